@@ -1,0 +1,282 @@
+"""Plain FP64 CPU oracle of the exact circulant-embedding sampler (Carron,
+Wolk & Szapudi 2014) -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library and its Python
+binding never import it; the two implementations share no code.
+
+The arithmetic lives in ``cf_oracle.c`` (plain C, binary64, compiled with
+``-ffp-contract=off``); this module only builds/loads it and marshals numpy
+arrays.  ``build()`` compiles it with gcc.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cf_oracle.c")
+_LIB = os.path.join(_HERE, "_cf_oracle.so")
+_lib = None
+
+XI_GAUSSIAN, XI_GEN_CAUCHY, XI_EXPONENTIAL, XI_TABLE = 0, 1, 2, 3
+BINS_LINEAR, BINS_LOG, BINS_EDGES = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``_cf_oracle.so`` (gcc, -O2, no FP contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(os.path.join(_HERE, "cf_oracle.h")))):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Report(C.Structure):
+    _fields_ = [("lambda_min", C.c_double), ("lambda_max", C.c_double), ("tau", C.c_double),
+                ("neg_mass", C.c_double), ("cov_error", C.c_double),
+                ("n_negative", C.c_int64), ("n_zeroed", C.c_int64),
+                ("clamped", C.c_int32), ("status", C.c_int32)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+
+
+def _lib_handle():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        lib.or_philox4x32_10.argtypes = [_P, _P, _P]
+        lib.or_log_unit.argtypes = [C.c_double]
+        lib.or_log_unit.restype = C.c_double
+        lib.or_logf_unit.argtypes = [C.c_float]
+        lib.or_logf_unit.restype = C.c_float
+        lib.or_cossin_2pi.argtypes = [C.c_double, _P, _P]
+        lib.or_cossin_2pif.argtypes = [C.c_float, _P, _P]
+        lib.or_draw_noise.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, C.c_int64, C.c_int64,
+                                      C.c_int32, _P]
+        lib.or_dft_naive.argtypes = [_P, _P, C.c_int64, C.c_int]
+        lib.or_fft_recursive.argtypes = [_P, C.c_int64, C.c_int]
+        lib.or_fft_nd.argtypes = [_P, C.c_int32, _P, C.c_int]
+        lib.or_embed_row.argtypes = [C.c_int32, _P, _P, C.c_int32, C.c_double, C.c_double,
+                                     C.c_double, _P, _P]
+        lib.or_eigenvalues.argtypes = [C.c_int32, _P, _P, _P]
+        lib.or_psd.argtypes = [C.c_int32, _P, _P, _P, C.c_int32, _P, _P, C.POINTER(Report)]
+        lib.or_sample.argtypes = [C.c_int32, _P, _P, C.c_uint64, C.c_uint64, C.c_int32,
+                                  C.c_int32, _P]
+        lib.or_sample_given_noise.argtypes = [C.c_int32, _P, _P, _P, _P]
+        lib.or_poisson_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        lib.or_poisson_uniform.restype = C.c_double
+        lib.or_poisson_icdf.argtypes = [C.c_double, C.c_double, _P]
+        lib.or_poisson_icdf.restype = C.c_int32
+        lib.or_lognormal_poisson.argtypes = [_P, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                             _P, C.c_uint64, C.c_uint64, _P, _P, _P]
+        lib.or_bin_edges.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _P, _P]
+        lib.or_power_spectrum.argtypes = [_P, C.c_int32, _P, C.c_double, C.c_int64, C.c_int32,
+                                          _P, _P, _P]
+        lib.or_counts_to_delta.argtypes = [_P, _P, C.c_int64, C.c_int64, _P]
+        lib.or_mean_cov.argtypes = [_P, C.c_int64, C.c_int32, _P, _P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dims(n):
+    n = [int(v) for v in n]
+    return np.asarray(n + [1] * (3 - len(n)), dtype=np.int64), len(n)
+
+
+# ---------------------------------------------------------------- generator
+def philox(ctr, key):
+    """Philox4x32-10 of one 4-word counter and 2-word key -> 4 uint32."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _lib_handle().or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def log_unit(u: float) -> float:
+    return _lib_handle().or_log_unit(float(u))
+
+
+def logf_unit(u) -> np.float32:
+    return np.float32(_lib_handle().or_logf_unit(float(u)))
+
+
+def cossin_2pi(u: float):
+    c, s = C.c_double(), C.c_double()
+    _lib_handle().or_cossin_2pi(float(u), C.byref(c), C.byref(s))
+    return c.value, s.value
+
+
+def cossin_2pif(u):
+    c, s = C.c_float(), C.c_float()
+    _lib_handle().or_cossin_2pif(float(u), C.byref(c), C.byref(s))
+    return np.float32(c.value), np.float32(s.value)
+
+
+def draw_noise(seed, r0, R, ncells, m_last, dtype):
+    """Complex noise [R][ncells] (complex128; dtype 1 values are exact binary32)."""
+    out = np.zeros((R, ncells, 2), dtype=np.float64)
+    _lib_handle().or_draw_noise(seed, r0, R, ncells, m_last, dtype, _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+# ---------------------------------------------------------------- transforms
+def dft_naive(x, sign):
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    out = np.zeros_like(x)
+    _lib_handle().or_dft_naive(_ptr(x), _ptr(out), x.size, sign)
+    return out
+
+
+def fft_recursive(x, sign):
+    a = np.array(x, dtype=np.complex128, copy=True)
+    _lib_handle().or_fft_recursive(_ptr(a), a.size, sign)
+    return a
+
+
+def fft_nd(x, sign):
+    a = np.array(x, dtype=np.complex128, copy=True, order="C")
+    dims = np.asarray(a.shape, dtype=np.int64)
+    _lib_handle().or_fft_nd(_ptr(a), a.ndim, _ptr(dims), sign)
+    return a
+
+
+# ---------------------------------------------------------------- embedding
+def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None):
+    dims, d = _dims(n)
+    cellv = np.ones(3) if cell is None else np.asarray(list(cell) + [1.0] * (3 - len(cell)))
+    M = [2 * int(v) for v in n]
+    c = np.zeros(int(np.prod(M)), dtype=np.float64)
+    tab = None if table is None else np.ascontiguousarray(table, dtype=np.float64).ravel()
+    _lib_handle().or_embed_row(d, _ptr(dims), _ptr(cellv), kind, amp, scale, beta, _ptr(tab),
+                               _ptr(c))
+    return c.reshape(M)
+
+
+def eigenvalues(n, c):
+    dims, d = _dims(n)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    lam = np.zeros(c.size, dtype=np.float64)
+    _lib_handle().or_eigenvalues(d, _ptr(dims), _ptr(c), _ptr(lam))
+    return lam.reshape(c.shape)
+
+
+def psd(n, c, lam, clamp=False):
+    dims, d = _dims(n)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    lp = np.zeros_like(lam)
+    s = np.zeros_like(lam)
+    rep = Report()
+    _lib_handle().or_psd(d, _ptr(dims), _ptr(c), _ptr(lam), int(bool(clamp)), _ptr(lp), _ptr(s),
+                         C.byref(rep))
+    return lp, s, rep.asdict()
+
+
+def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False):
+    """Steps a1-a3: first row c, eigenvalues lambda, lambda+, sqrt(lambda+), report."""
+    c = embed_row(n, kind, amp, scale, beta, cell, table)
+    lam = eigenvalues(n, c)
+    lp, s, rep = psd(n, c, lam, clamp)
+    return {"c": c, "lambda": lam, "lambda_plus": lp, "sqrt_lambda": s, "report": rep}
+
+
+# ---------------------------------------------------------------- sampling
+def sample(n, s, seed, r0, R, dtype):
+    """Fields [R][2][*n] (Re, Im) from sqrt(lambda+) s; dtype 0 f64 noise, 1 f32 noise."""
+    dims, d = _dims(n)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    out = np.zeros((R, 2) + tuple(int(v) for v in n), dtype=np.float64)
+    _lib_handle().or_sample(d, _ptr(dims), _ptr(s), seed, r0, R, dtype, _ptr(out))
+    return out
+
+
+def sample_given_noise(n, s, eps):
+    dims, d = _dims(n)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    e = np.ascontiguousarray(np.stack([np.real(eps), np.imag(eps)], axis=-1), dtype=np.float64)
+    w = np.zeros(tuple(int(v) for v in n) + (2,), dtype=np.float64)
+    _lib_handle().or_sample_given_noise(d, _ptr(dims), _ptr(s), _ptr(e), _ptr(w))
+    return w[..., 0] + 1j * w[..., 1]
+
+
+# ---------------------------------------------------------------- lognormal / Poisson
+def poisson_uniform(seed, cell, field):
+    return _lib_handle().or_poisson_uniform(seed, cell, field)
+
+
+def poisson_icdf(U, mu):
+    m = C.c_double()
+    n = _lib_handle().or_poisson_icdf(float(U), float(mu), C.byref(m))
+    return n, m.value
+
+
+def lognormal_poisson(G, sigma2, nbar, f=None, seed=0, field0=0):
+    """G: [nfields][cells] -> (delta, counts int32, margin)."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    nf, cells = G.shape[0], int(np.prod(G.shape[1:]))
+    fa = None if f is None else np.ascontiguousarray(f, dtype=np.float64).ravel()
+    delta = np.zeros_like(G)
+    counts = np.zeros(G.shape, dtype=np.int32)
+    margin = np.zeros_like(G)
+    _lib_handle().or_lognormal_poisson(_ptr(G), cells, nf, sigma2, nbar, _ptr(fa), seed, field0,
+                                       _ptr(delta), _ptr(counts), _ptr(margin))
+    return delta, counts, margin
+
+
+# ---------------------------------------------------------------- power spectrum
+def bin_edges(kind, nbins, kmin, kmax, edges=None):
+    e_in = None if edges is None else np.ascontiguousarray(edges, dtype=np.float64)
+    out = np.zeros(nbins + 1, dtype=np.float64)
+    _lib_handle().or_bin_edges(kind, nbins, kmin, kmax, _ptr(e_in), _ptr(out))
+    return out
+
+
+def power_spectrum(fields, n, edges, cell=1.0):
+    """fields [F][*n] -> (pk [F][nbins], nmodes [nbins])."""
+    dims, d = _dims(n)
+    fl = np.ascontiguousarray(fields, dtype=np.float64)
+    F = fl.shape[0]
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = edges.size - 1
+    pk = np.zeros((F, nb), dtype=np.float64)
+    nm = np.zeros(nb, dtype=np.int64)
+    _lib_handle().or_power_spectrum(_ptr(fl), d, _ptr(dims), cell, F, nb, _ptr(edges), _ptr(pk),
+                                    _ptr(nm))
+    return pk, nm
+
+
+def counts_to_delta(counts, f=None):
+    N = np.ascontiguousarray(counts, dtype=np.int32)
+    nf, cells = N.shape[0], int(np.prod(N.shape[1:]))
+    fa = None if f is None else np.ascontiguousarray(f, dtype=np.float64).ravel()
+    out = np.zeros(N.shape, dtype=np.float64)
+    _lib_handle().or_counts_to_delta(_ptr(N), _ptr(fa), cells, nf, _ptr(out))
+    return out
+
+
+def mean_cov(pk):
+    pk = np.ascontiguousarray(pk, dtype=np.float64)
+    F, nb = pk.shape
+    mean = np.zeros(nb)
+    cov = np.zeros((nb, nb))
+    _lib_handle().or_mean_cov(_ptr(pk), F, nb, _ptr(mean), _ptr(cov))
+    return mean, cov
