@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the exact survey-field sampler (one JSON line on stdout).
+
+A step is one pass of the whole hot path over one batch: circulant embedding
+with its binary64 eigenvalues and positivity check, 64 realizations of
+binary32 exact Gaussian fields with the fused lognormal + Poisson epilogue,
+and the 64-bin power spectra of the 128 Gaussian fields and of the 128 count
+maps with their mean and covariance (workload: 2D 512x512 survey in a
+1024x1024 periodic grid, xi = 0.8/(1+(r/8)^2)^0.4, nbar = 2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it runs under torch.distributed (one process per GPU); every rank
+samples its own realization range (replicas, weak scaling) and rank 0 prints.
+"--impl reference" times the CPU oracle on the same workload (bounded sample
+per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "cauchy2d_n512_f32"
+METRIC = "exact Gaussian/lognormal fields per sec (cells/s, % HBM roofline) vs plain FP64"
+UNIT = "cells/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-realizations", type=int, default=8)
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------- roofline
+def kernel_costs(wl, R, chunks):
+    """Algorithmic bytes per step of each kernel of the binary32 2D path.
+
+    sample_rows: writes the pruned intermediate R*M0*N1 complex64 and reads
+    sqrt(lambda) (M0*M1 float32) once per launch; icols_fields_lp: reads the
+    intermediate, writes 2 fields (float32) + 2 count maps (int32) per
+    realization; pk_rows: reads F fields (4 B/cell), writes F half spectra
+    n*(n/2+1) complex64; pk_cols: reads the half spectra."""
+    n0, n1 = wl.n
+    m0, m1 = wl.m
+    F = 2 * R
+    inter = R * m0 * n1 * 8
+    half = F * n0 * (n1 // 2 + 1) * 8
+    return {
+        "sample_rows_f32": inter + chunks * m0 * m1 * 4,
+        "icols_fields_lp_f32": inter + F * n0 * n1 * 8,
+        "pk_rows_f32": 2 * (F * n0 * n1 * 4 + half),   # Gaussian fields and count maps
+        "pk_cols_f32": 2 * half,
+    }
+
+
+def roofline(wl, R, timing, steps, hbm_peak, peak_kind):
+    per_kernel = {}
+    for name, (launches, ms) in timing.items():
+        base = name.split("<")[0]
+        per_kernel.setdefault(base, [0, 0.0])
+        per_kernel[base][0] += launches
+        per_kernel[base][1] += ms
+    launches_rows = per_kernel.get("sample_rows_f32", [steps, 0])[0]
+    chunks = max(1, launches_rows // max(steps, 1))
+    costs = kernel_costs(wl, R, chunks)
+    dom = max(per_kernel.items(), key=lambda kv: kv[1][1])[0]
+    if dom not in costs:
+        dom = max(costs, key=lambda k: per_kernel.get(k, [0, 0.0])[1])
+    launches, ms = per_kernel[dom]
+    bytes_per_launch = costs[dom] * steps / launches
+    avg_ms = ms / launches
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_source": peak_kind,
+            "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_ms, 5),
+            "launches": launches}, per_kernel
+
+
+# --------------------------------------------------------------------- CPU oracle
+def oracle_sample_run(wl, realizations, r0):
+    """The oracle as it stands on a bounded sample of the workload: embed,
+    `realizations` realizations (binary32 noise spec, binary64 arithmetic),
+    lognormal + Poisson, power spectra of fields and count maps, mean/cov."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    e = oracle.embed(list(wl.n), wl.xi_kind, wl.amp, wl.scale, wl.beta, clamp=wl.clamp)
+    fields = oracle.sample(wl.n, e["sqrt_lambda"], wl.seed, r0, realizations, 1 if wl.dtype == "f32" else 0)
+    F = 2 * realizations
+    G = fields.reshape(F, -1)
+    cells = F * wl.cells_per_field
+    if wl.nbar is not None:
+        _, counts, _ = oracle.lognormal_poisson(G, wl.sigma2, wl.nbar, seed=wl.seed + 1000, field0=2 * r0)
+    if wl.nbins:
+        edges = oracle.bin_edges(oracle.BINS_LINEAR, wl.nbins, 0.0, wl.n[0] / 2)
+        pk, _ = oracle.power_spectrum(fields.reshape((F,) + tuple(wl.n)), wl.n, edges)
+        oracle.mean_cov(pk)
+        if wl.nbar is not None:
+            dg = oracle.counts_to_delta(counts, None)
+            pkg, _ = oracle.power_spectrum(dg.reshape((F,) + tuple(wl.n)), wl.n, edges)
+            oracle.mean_cov(pkg)
+    dt = time.perf_counter() - t0
+    return cells, dt, np
+
+
+def cpu_baseline(wl, realizations):
+    import oracle
+    oracle.build()
+    cells, dt, _ = oracle_sample_run(wl, realizations, 0)
+    return {"value": cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d realization(s) (%d fields of %s) incl. embedding, lognormal+Poisson and spectra, "
+                      "single-threaded C oracle, %.1f s" % (realizations, 2 * realizations,
+                                                             "x".join(map(str, wl.n)), dt)}
+
+
+def run_reference(args):
+    from paper_1406_6072_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = W.CONFIGS[args.workload]
+    import oracle
+    oracle.build()
+    R = max(1, args.cpu_sample_realizations // 2)
+    if args.warmup > 0:
+        oracle_sample_run(wl, R, 0)  # loads the library and touches the code paths once
+    total_cells, total_t = 0, 0.0
+    for k in range(args.steps):
+        cells, dt, _ = oracle_sample_run(wl, R, (k + 1) * R)
+        total_cells += cells
+        total_t += dt
+    value = total_cells / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "text": wl.text,
+                                            "sample_realizations_per_step": R},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d realization(s) per step of %s" % (R, wl.name)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- our arm
+def e2e_run(pipe, wl, steps, warmup, rank):
+    """Same metric through the public API with host buffers: the xi table is
+    copied from pinned host memory each step, the fields, counts and spectra
+    are read back into pinned host memory each step."""
+    import numpy as np
+    import torch
+
+    import paper_1406_6072_gb300.cf as cf
+    m = wl.m
+    ax = [np.arange(v) for v in m]
+    lag = [np.where(a < n, a, a - 2 * n).astype(np.float64) * c for a, n, c in zip(ax, wl.n, wl.cell)]
+    r2 = lag[0][:, None] ** 2 + lag[1][None, :] ** 2
+    table = (wl.amp / (1.0 + r2 / wl.scale ** 2) ** wl.beta) if wl.xi_kind == 1 else None
+    if table is None:
+        return None
+    h_table = torch.from_numpy(np.ascontiguousarray(table)).pin_memory()
+    d_table = torch.empty_like(h_table, device=pipe.dev)
+    h_fields = torch.empty(pipe.fields.shape, dtype=pipe.fields.dtype).pin_memory()
+    h_counts = torch.empty(pipe.counts.shape, dtype=torch.int32).pin_memory()
+    outs = [pipe.pk, pipe.mean, pipe.cov, pipe.pkg, pipe.meang, pipe.covg]
+    h_outs = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+    s = pipe.stream
+    xi = cf.make_xi(cf.CF_XI_TABLE, table=d_table, table_on_device=1)
+
+    def one(k):
+        d_table.copy_(h_table, non_blocking=True)
+        pipe.embed(xi)
+        pipe.sample(r0=(rank * 100000 + k) * pipe.R)
+        pipe.spectra()
+        h_fields.copy_(pipe.fields, non_blocking=True)
+        h_counts.copy_(pipe.counts, non_blocking=True)
+        for h, d in zip(h_outs, outs):
+            h.copy_(d, non_blocking=True)
+
+    with torch.cuda.stream(s):
+        for k in range(warmup):
+            one(k)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for k in range(steps):
+            one(1000 + k)
+        e1.record(s)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h2d = h_table.numel() * 8
+    d2h = h_fields.numel() * h_fields.element_size() + h_counts.numel() * 4 + sum(h.numel() * 8 for h in h_outs)
+    return ms, h2d, d2h
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_1406_6072_gb300 import cf
+    from paper_1406_6072_gb300 import workloads as W
+    from paper_1406_6072_gb300.pipeline import FieldPipeline
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.CONFIGS[args.workload]
+    stream = torch.cuda.Stream(dev)
+    pipe = FieldPipeline(wl, dev, stream=stream)
+    R = pipe.R
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            pipe.step(r0=(rank * 100000 + k) * R)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        cf.cf_kernel_timing(1)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            pipe.step(r0=(rank * 100000 + args.warmup + k) * R)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        timing = cf.cf_kernel_timing_read()
+        cf.cf_kernel_timing(0)
+        clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    cells_all = pipe.cells_per_step * world
+    value = cells_all / (ms_max * 1e-3)
+    hbm_peak, peak_kind = measured_peaks()
+    roof, per_kernel = roofline(wl, R, timing, args.steps, hbm_peak, peak_kind)
+    launches = sum(v[0] for v in per_kernel.values())
+
+    e2e = None
+    if not args.no_e2e:
+        r = e2e_run(pipe, wl, max(3, args.steps // 2), 2, rank)
+        if r is not None:
+            e_ms, h2d, d2h = r
+            te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            if dist is not None:
+                dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e = {"value": cells_all / (float(te.item()) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h), "ms_per_step": float(te.item())}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_sample_realizations)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "text": wl.text, "realizations_per_step": R * world,
+                       "cells_per_step": cells_all, "realizations_per_s": R * world / (ms_max * 1e-3),
+                       "l2": "each step writes %d MiB of fields and counts (> 129 MB L2)"
+                             % (2 * pipe.cells_per_step * 4 >> 20),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "embed_report": pipe.emb.report,
+            "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(per_kernel.items())},
+        }
+        print(json.dumps(line))
+    pipe.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

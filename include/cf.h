@@ -1,0 +1,264 @@
+/*
+ * cf.h -- C ABI of the GB300 (sm_103a) exact survey-field sampler.
+ *
+ * Method: Carron, Wolk & Szapudi (2014), "On fast generation of cosmological
+ * random fields".  A stationary Gaussian field with covariance xi on a survey
+ * grid of n_i cells per axis is sampled exactly by embedding the grid in a
+ * periodic grid of M_i = 2 n_i cells (section 2, eq. (grid)), taking the DFT
+ * of the embedded correlation row (eq. (Specd)), drawing independent Fourier
+ * modes with variance lambda (eq. (Papos2)), inverse transforming and keeping
+ * the survey box (closing paragraph of section 2).  Section 3.1 exponentiates
+ * the field into a lognormal density and Poisson-samples galaxy counts (eqs.
+ * (Lncov), (sampling)); section 3.2 validates with the binned power spectrum
+ * (eq. (Def spec)).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every function returns a cf_status; CF_OK on success.  Nothing
+ *    throws across the ABI.  cf_last_error() returns a thread-local message
+ *    describing the most recent failure on the calling thread.
+ *  - Memory: unless stated otherwise, array arguments are DEVICE pointers of
+ *    the current CUDA device, owned by the caller; structs passed by pointer
+ *    are host memory.  The library owns cf_embedding and cf_server objects.
+ *  - Asynchrony: work is enqueued on the caller's stream and returns without
+ *    waiting, except cf_embed / cf_embed_from_lambda, which synchronise the
+ *    stream once to fill the report.  The first call on a device performs a
+ *    one-time set-up (twiddle tables) with a device synchronisation; make it
+ *    before any stream capture.
+ *  - Layouts: row-major (C order).  Complex values are interleaved (re, im).
+ *    Sampled fields are [R][2][n0][n1][n2]: field 2r is Re and 2r+1 is Im of
+ *    realization r0 + r (two independent exact fields per complex draw).
+ *  - Sizes: M_i = 2 n_i must be a power of two between 2 and 4096 (8192
+ *    cells along one axis at most are not supported: CF_ERR_UNSUPPORTED).
+ *  - Randomness: counter-based Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *    the 64-bit seed; any realization range [r0, r0+R) is reproducible on its
+ *    own.  The realization index r0+R-1 must fit in 32 bits.
+ */
+#ifndef CF_H
+#define CF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CF_API __attribute__((visibility("default")))
+#else
+#define CF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cf_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    CF_OK = 0,
+    CF_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad enum)  */
+    CF_ERR_NOT_PSD = 2,      /* an embedding eigenvalue < -tau and no clamping       */
+    CF_ERR_NOMEM = 3,        /* device or host allocation failed / workspace small   */
+    CF_ERR_UNSUPPORTED = 4,  /* size or mode not supported by this build             */
+    CF_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the detail)  */
+    CF_ERR_TIMEOUT = 6,      /* cf_serve_wait ran out of time                        */
+    CF_ERR_BUSY = 7,         /* server queue full / shutting down                    */
+    CF_ERR_NOT_FOUND = 8     /* unknown ticket                                       */
+} cf_status;
+
+typedef enum {
+    CF_F64 = 0,      /* binary64 noise, transforms and fields                         */
+    CF_F32 = 1,      /* binary32 noise, transforms and fields (eigenvalues stay FP64) */
+    CF_BF16_TC = 2,  /* reserved: tensor-core DFT stages, not in this build           */
+    CF_F16_TC = 3    /* reserved: tensor-core DFT stages, not in this build           */
+} cf_dtype;
+
+/* Survey grid (section 2, eq. (grid)): ndim in {1,2,3}; n[i] survey cells on
+ * axis i (unused axes ignored); cell[i] the physical cell side (the L/N of
+ * the paper), used for the lag r of xi and the volume of the power spectrum. */
+typedef struct {
+    int32_t ndim;
+    int32_t pad_;
+    int64_t n[3];
+    double cell[3];
+} cf_grid;
+
+typedef enum {
+    CF_XI_GAUSSIAN = 0,     /* amp * exp(-r^2 / (2 scale^2))                        */
+    CF_XI_GEN_CAUCHY = 1,   /* amp / (1 + (r/scale)^2)^beta                         */
+    CF_XI_EXPONENTIAL = 2,  /* amp * exp(-r / scale)                                */
+    CF_XI_TABLE = 3         /* caller's embedded first row c, M^d doubles           */
+} cf_xi_kind;
+
+/* Two-point function to embed.  For CF_XI_TABLE, table holds the embedded first
+ * row c(m) = xi(lag(m)) on the M^d periodic grid, row-major, with lag(m_i) =
+ * m_i for m_i < n_i and m_i - M_i otherwise; table_on_device says whether
+ * table is a device (1) or host (0) pointer.  Other kinds ignore table. */
+typedef struct {
+    int32_t kind;
+    int32_t table_on_device;
+    double amp;
+    double scale;
+    double beta;
+    const double* table;
+} cf_xi;
+
+/* cf_embed flags */
+#define CF_EMBED_CLAMP 1u        /* set eigenvalues < -tau to zero instead of failing */
+#define CF_EMBED_SKIP_ERROR 2u   /* with CF_EMBED_CLAMP: skip the covariance-error pass */
+
+/* Outcome of the positivity check (section 2, eq. (condition)).
+ * tau = 1e-12 lambda_max.  Eigenvalues in [-tau, tau] are set to zero (n_zeroed);
+ * eigenvalues below -tau are "negative" (n_negative, neg_mass = sum of |lambda|).
+ * exact = 1 when no eigenvalue was clamped: the realised covariance then equals
+ * xi on every survey lag to within tau.  When clamped, cov_error is the largest
+ * |IDFT(lambda+)/M^d - c| over survey lags (the realised covariance error). */
+typedef struct {
+    double lambda_min;
+    double lambda_max;
+    double tau;
+    double neg_mass;
+    double cov_error;
+    int64_t n_negative;
+    int64_t n_zeroed;
+    int32_t clamped;
+    int32_t exact;
+} cf_embed_report;
+
+typedef struct cf_embedding cf_embedding;
+
+/* Steps a1-a3 (section 2, eqs. (grid), (Specd), (condition)): builds the
+ * embedded row c on the device, computes lambda = DFT(c) in binary64 (the cell
+ * volume of eq. (Specd) is absorbed: lambda_k = sum_m c_m e^{-2 pi i k.m/M}),
+ * checks positivity, and keeps lambda, sqrt(lambda+) on the device.
+ * Synchronises stream s once to fill *rep (may be NULL).  On CF_ERR_NOT_PSD
+ * *out is NULL and *rep still describes the spectrum. */
+CF_API cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags, cf_stream_t s,
+                   cf_embedding** out, cf_embed_report* rep);
+
+/* As cf_embed, with the spectrum lambda (M^d doubles, device) given instead of
+ * xi (e.g. the periodic-box spectrum of section 3.3, eq. (Periodicboxmodes)).
+ * The covariance-error pass compares against IDFT(lambda) itself. */
+CF_API cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
+                               cf_stream_t s, cf_embedding** out, cf_embed_report* rep);
+
+CF_API cf_status cf_embedding_free(cf_embedding* e);
+
+/* Copies of the embedding's arrays into caller device memory (M^d doubles),
+ * enqueued on s: the raw eigenvalues lambda and sqrt(lambda+). */
+CF_API cf_status cf_embedding_lambda(const cf_embedding* e, double* dst, cf_stream_t s);
+CF_API cf_status cf_embedding_sqrt_lambda(const cf_embedding* e, double* dst, cf_stream_t s);
+/* Grid and report of an embedding (host structs). */
+CF_API cf_status cf_embedding_info(const cf_embedding* e, cf_grid* g, cf_embed_report* rep);
+
+/* Step b1 alone (section 2, eq. (Papos2): independent zero-mean Gaussian
+ * modes).  Writes the complex standard-normal noise of cells [0, ncells) of
+ * realizations [r0, r0+R) to out: [R][ncells] complex of dtype dt (float2 or
+ * double2).  m_last is the size of the last embedding axis (the binary32
+ * specification pairs column c with c + m_last/2); ncells must be a multiple
+ * of m_last.  Bit-exact reference for the noise fused into cf_sample. */
+CF_API cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_t ncells, int64_t m_last,
+                        cf_dtype dt, void* out, cf_stream_t s);
+
+/* Workspace (bytes, device) that cf_sample / cf_sample_lp need for R
+ * realizations; realizations are processed in chunks sized so that the
+ * intermediate of a chunk stays in L2, so the size saturates for large R. */
+CF_API cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, cf_dtype dt, size_t* bytes);
+
+/* Steps b1-b4 (section 2, eq. (Papos2) and the closing paragraph): for each
+ * realization r in [r0, r0+R), draws eps_k (Philox stream 0), scales it by
+ * sqrt(lambda+_k), computes W_m = M^{-d/2} sum_k sqrt(lambda_k) eps_k
+ * e^{+2 pi i k.m/M} for survey cells m (pruned axis-by-axis inverse FFT), and
+ * writes fields_out [R][2][n...] (float for CF_F32, double for CF_F64):
+ * Re W then Im W.  ws: device workspace of at least cf_sample_workspace_size
+ * bytes (fewer bytes -> smaller chunks; below one realization -> CF_ERR_NOMEM). */
+CF_API cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, cf_dtype dt,
+                    void* fields_out, void* ws, size_t ws_bytes, cf_stream_t s);
+
+/* Lognormal + Poisson parameters (section 3.1, eqs. (Lncov), (sampling)). */
+typedef struct {
+    double sigma2;          /* variance of G: rho = exp(G - sigma2/2), delta = rho - 1 */
+    double nbar;            /* Poisson intensity of a cell with f = 1                 */
+    const float* f;         /* device [cells] unmasked fraction f_i, or NULL (f = 1)  */
+    uint64_t seed;          /* key of Philox stream 1 (the Poisson uniforms)          */
+    float* delta_out;       /* device [nfields][cells] or NULL                        */
+    int32_t* counts_out;    /* device [nfields][cells], required                      */
+} cf_lp_params;
+
+/* cf_sample with steps c1-c2 fused into the last inverse-FFT pass: writes the
+ * fields (if fields_out is not NULL) and the lognormal delta / Poisson counts
+ * of every field, with field index 2(r0+r) + {0,1}.  Binary32 only. */
+CF_API cf_status cf_sample_lp(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, cf_dtype dt,
+                       void* fields_out, const cf_lp_params* lp, void* ws, size_t ws_bytes,
+                       cf_stream_t s);
+
+/* Steps c1-c2 standalone (section 3.1): for fields j in [0, nfields) with
+ * global index field0 + j and cells i in [0, cells_per_field):
+ *   rho = exp(G - sigma2/2); delta = rho - 1; mu = nbar f_i rho;
+ *   count = min{ k >= 0 : U < F(k; mu) }, F the Poisson CDF, U in [0,1) from
+ *   Philox key seed, counter (i_lo, i_hi, (field0+j) >> 1, 1), words (0,1) for
+ *   even and (2,3) for odd fields, U = ((a>>5) 2^26 + (b>>6)) 2^-53.
+ * G: [nfields][cells] of dtype dt; f_or_null: [cells] float or NULL;
+ * delta_out_or_null: [nfields][cells] float; counts_out: [nfields][cells] int32. */
+CF_API cf_status cf_lognormal_poisson(const void* G, cf_dtype dt, int64_t cells_per_field,
+                               int64_t nfields, double sigma2, double nbar,
+                               const float* f_or_null, uint64_t seed, uint64_t field0,
+                               float* delta_out_or_null, int32_t* counts_out, cf_stream_t s);
+
+typedef enum { CF_BINS_LINEAR = 0, CF_BINS_LOG = 1, CF_BINS_EDGES = 2 } cf_bins_kind;
+
+/* Bins of |n| = sqrt(sum_i n_i^2), n_i in (-n/2, n/2] the mode index in
+ * fundamental units.  Bin b is [e_b, e_{b+1}).  LINEAR: e_b = kmin + b (kmax -
+ * kmin)/nbins; LOG: e_b = kmin exp(b ln(kmax/kmin)/nbins) (the paper's 20
+ * ln-spaced bins); EDGES: host array edges[nbins+1], increasing.  kmax <= 0
+ * means n/2.  The DC mode is never binned. */
+typedef struct {
+    int32_t nbins;
+    int32_t kind;
+    double kmin;
+    double kmax;
+    const double* edges;
+} cf_bins;
+
+/* Workspace bytes for cf_power_spectrum / cf_power_spectrum_counts. */
+CF_API cf_status cf_power_spectrum_workspace_size(const cf_grid* g, int64_t nfields, const cf_bins* b,
+                                           cf_dtype dt, size_t* bytes);
+
+/* Step d1 (section 3.2, eq. (Def spec)): for each real field phi of fields
+ * [nfields][n...] (float for CF_F32, double for CF_F64):
+ *   pk_out[f][b] = cell^d / (prod n_i * N_b) * sum_{|n| in bin b} |DFT(phi)_n|^2
+ * over all modes of the full grid (both +n and -n); nmodes_out[b] = N_b
+ * (int64).  ndim must be 2 or 3 with the same power-of-two n on all axes.  If mean_or_null / cov_or_null are
+ * given, the mean over fields [nbins] and the unbiased (1/(F-1)) covariance
+ * [nbins][nbins] are written too (section 3.2, "prediction and covariance from
+ * a very large number of simulations").  Outputs are device doubles/int64. */
+CF_API cf_status cf_power_spectrum(const void* fields, cf_dtype dt, const cf_grid* g, int64_t nfields,
+                            const cf_bins* bins, double* pk_out, int64_t* nmodes_out,
+                            double* mean_or_null, double* cov_or_null, void* ws,
+                            size_t ws_bytes, cf_stream_t s);
+
+/* Step d1 on count maps (section 3.2, eq. (Estim) and the map before it):
+ * each count field N [nfields][n...] (int32) becomes
+ * delta_g = (N/f - Nhat)/Nhat where f != 0 (0 elsewhere), Nhat = N_tot / sum f,
+ * and its spectrum is computed as in cf_power_spectrum (binary32 transforms). */
+CF_API cf_status cf_power_spectrum_counts(const int32_t* counts, const float* f_or_null, const cf_grid* g,
+                                   int64_t nfields, const cf_bins* bins, double* pk_out,
+                                   int64_t* nmodes_out, double* mean_or_null, double* cov_or_null,
+                                   void* ws, size_t ws_bytes, cf_stream_t s);
+
+/* Kernel timing (tracing).  cf_kernel_timing(1) clears the accumulators and
+ * makes every subsequent library launch record a CUDA event pair on its own
+ * stream; cf_kernel_timing(0) stops recording.  cf_kernel_timing_read waits
+ * for the recorded events and writes a JSON object
+ * {"<kernel>": [launches, total_ms], ...} into json (capacity cap bytes,
+ * NUL-terminated); *needed receives the full length.  Timing adds one event
+ * pair per launch; leave it off outside measurements. */
+CF_API cf_status cf_kernel_timing(int32_t enable);
+CF_API cf_status cf_kernel_timing_read(char* json, size_t cap, size_t* needed);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+CF_API const char* cf_last_error(void);
+/* Library version string. */
+CF_API const char* cf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CF_H */

@@ -1,0 +1,309 @@
+"""Thin Python binding of the C ABI in ``include/cf.h`` (``libcf.so``).
+
+Argument marshalling only: every function has the name of its C entry point,
+takes torch CUDA tensors (or raw integer device pointers) for device arrays
+and a stream (default: torch's current stream), and raises :class:`CfError`
+on a non-OK status.  All computation happens in the CUDA library; if the
+library has not been built this module fails on import.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libcf.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_1406_6072_gb300._build): " + LIB_PATH)
+
+_lib = C.CDLL(LIB_PATH)
+
+# ----------------------------------------------------------------- constants
+CF_OK, CF_ERR_ARG, CF_ERR_NOT_PSD, CF_ERR_NOMEM, CF_ERR_UNSUPPORTED, CF_ERR_CUDA = 0, 1, 2, 3, 4, 5
+CF_ERR_TIMEOUT, CF_ERR_BUSY, CF_ERR_NOT_FOUND = 6, 7, 8
+STATUS_NAMES = {0: "CF_OK", 1: "CF_ERR_ARG", 2: "CF_ERR_NOT_PSD", 3: "CF_ERR_NOMEM",
+                4: "CF_ERR_UNSUPPORTED", 5: "CF_ERR_CUDA", 6: "CF_ERR_TIMEOUT", 7: "CF_ERR_BUSY",
+                8: "CF_ERR_NOT_FOUND"}
+CF_F64, CF_F32, CF_BF16_TC, CF_F16_TC = 0, 1, 2, 3
+CF_XI_GAUSSIAN, CF_XI_GEN_CAUCHY, CF_XI_EXPONENTIAL, CF_XI_TABLE = 0, 1, 2, 3
+CF_EMBED_CLAMP, CF_EMBED_SKIP_ERROR = 1, 2
+CF_BINS_LINEAR, CF_BINS_LOG, CF_BINS_EDGES = 0, 1, 2
+
+
+class CfError(RuntimeError):
+    def __init__(self, status, func, message):
+        self.status = status
+        super().__init__("%s returned %s: %s" % (func, STATUS_NAMES.get(status, status), message))
+
+
+# ----------------------------------------------------------------- structs
+class cf_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("pad_", C.c_int32), ("n", C.c_int64 * 3), ("cell", C.c_double * 3)]
+
+
+class cf_xi(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("table_on_device", C.c_int32), ("amp", C.c_double),
+                ("scale", C.c_double), ("beta", C.c_double), ("table", C.c_void_p)]
+
+
+class cf_embed_report(C.Structure):
+    _fields_ = [("lambda_min", C.c_double), ("lambda_max", C.c_double), ("tau", C.c_double),
+                ("neg_mass", C.c_double), ("cov_error", C.c_double), ("n_negative", C.c_int64),
+                ("n_zeroed", C.c_int64), ("clamped", C.c_int32), ("exact", C.c_int32)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cf_lp_params(C.Structure):
+    _fields_ = [("sigma2", C.c_double), ("nbar", C.c_double), ("f", C.c_void_p), ("seed", C.c_uint64),
+                ("delta_out", C.c_void_p), ("counts_out", C.c_void_p)]
+
+
+class cf_bins(C.Structure):
+    _fields_ = [("nbins", C.c_int32), ("kind", C.c_int32), ("kmin", C.c_double), ("kmax", C.c_double),
+                ("edges", C.c_void_p)]
+
+
+_P = C.c_void_p
+_S = C.c_void_p  # cudaStream_t
+_sigs = {
+    "cf_embed": [C.POINTER(cf_grid), C.POINTER(cf_xi), C.c_uint32, _S, C.POINTER(_P), C.POINTER(cf_embed_report)],
+    "cf_embed_from_lambda": [C.POINTER(cf_grid), _P, C.c_uint32, _S, C.POINTER(_P), C.POINTER(cf_embed_report)],
+    "cf_embedding_free": [_P],
+    "cf_embedding_lambda": [_P, _P, _S],
+    "cf_embedding_sqrt_lambda": [_P, _P, _S],
+    "cf_embedding_info": [_P, C.POINTER(cf_grid), C.POINTER(cf_embed_report)],
+    "cf_draw_noise": [C.c_uint64, C.c_uint64, C.c_int32, C.c_int64, C.c_int64, C.c_int32, _P, _S],
+    "cf_sample_workspace_size": [_P, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
+    "cf_sample": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, _P, C.c_size_t, _S],
+    "cf_sample_lp": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, C.POINTER(cf_lp_params), _P,
+                     C.c_size_t, _S],
+    "cf_lognormal_poisson": [_P, C.c_int32, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, C.c_uint64,
+                             C.c_uint64, _P, _P, _S],
+    "cf_power_spectrum_workspace_size": [C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), C.c_int32,
+                                         C.POINTER(C.c_size_t)],
+    "cf_power_spectrum": [_P, C.c_int32, C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), _P, _P, _P, _P, _P,
+                          C.c_size_t, _S],
+    "cf_power_spectrum_counts": [_P, _P, C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), _P, _P, _P, _P, _P,
+                                 C.c_size_t, _S],
+}
+for _name, _args in _sigs.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = C.c_int
+_lib.cf_kernel_timing.argtypes = [C.c_int32]
+_lib.cf_kernel_timing.restype = C.c_int
+_lib.cf_kernel_timing_read.argtypes = [C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+_lib.cf_kernel_timing_read.restype = C.c_int
+_lib.cf_last_error.restype = C.c_char_p
+_lib.cf_last_error.argtypes = []
+_lib.cf_version.restype = C.c_char_p
+_lib.cf_version.argtypes = []
+
+
+def _check(status, func):
+    if status != CF_OK:
+        raise CfError(status, func, _lib.cf_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor / integer / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_grid(n, cell=None):
+    g = cf_grid()
+    n = list(n)
+    g.ndim = len(n)
+    for a in range(3):
+        g.n[a] = int(n[a]) if a < len(n) else 1
+        g.cell[a] = float(cell[a]) if cell is not None and a < len(cell) else 1.0
+    return g
+
+
+def make_xi(kind, amp=1.0, scale=1.0, beta=0.0, table=None, table_on_device=None):
+    x = cf_xi()
+    x.kind = int(kind)
+    x.amp, x.scale, x.beta = float(amp), float(scale), float(beta)
+    if table is not None:
+        x.table = _ptr(table)
+        x.table_on_device = int(table_on_device if table_on_device is not None
+                                else getattr(table, "is_cuda", False))
+    return x
+
+
+def make_bins(nbins, kind=CF_BINS_LINEAR, kmin=0.0, kmax=0.0, edges=None):
+    b = cf_bins()
+    b.nbins, b.kind, b.kmin, b.kmax = int(nbins), int(kind), float(kmin), float(kmax)
+    b._edges_keep = None
+    if edges is not None:
+        arr = np.ascontiguousarray(edges, dtype=np.float64)
+        b._edges_keep = arr
+        b.edges = arr.ctypes.data
+    return b
+
+
+# ----------------------------------------------------------------- entry points
+class Embedding:
+    """Owns a cf_embedding handle (freed on close/garbage collection)."""
+
+    def __init__(self, handle, report):
+        self.handle = handle
+        self.report = report
+
+    def close(self):
+        if self.handle:
+            _lib.cf_embedding_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cf_embed(grid, xi, flags=0, stream=None):
+    h = _P()
+    rep = cf_embed_report()
+    st = _lib.cf_embed(C.byref(grid), C.byref(xi), flags, _stream(stream), C.byref(h), C.byref(rep))
+    if st == CF_ERR_NOT_PSD:
+        err = CfError(st, "cf_embed", _lib.cf_last_error().decode())
+        err.report = rep.asdict()
+        raise err
+    _check(st, "cf_embed")
+    return Embedding(h.value, rep.asdict())
+
+
+def cf_embed_from_lambda(grid, lam, flags=0, stream=None):
+    h = _P()
+    rep = cf_embed_report()
+    st = _lib.cf_embed_from_lambda(C.byref(grid), _ptr(lam), flags, _stream(stream), C.byref(h), C.byref(rep))
+    if st == CF_ERR_NOT_PSD:
+        err = CfError(st, "cf_embed_from_lambda", _lib.cf_last_error().decode())
+        err.report = rep.asdict()
+        raise err
+    _check(st, "cf_embed_from_lambda")
+    return Embedding(h.value, rep.asdict())
+
+
+def cf_embedding_free(emb):
+    emb.close()
+
+
+def cf_embedding_lambda(emb, dst, stream=None):
+    _check(_lib.cf_embedding_lambda(emb.handle, _ptr(dst), _stream(stream)), "cf_embedding_lambda")
+
+
+def cf_embedding_sqrt_lambda(emb, dst, stream=None):
+    _check(_lib.cf_embedding_sqrt_lambda(emb.handle, _ptr(dst), _stream(stream)), "cf_embedding_sqrt_lambda")
+
+
+def cf_embedding_info(emb):
+    g = cf_grid()
+    rep = cf_embed_report()
+    _check(_lib.cf_embedding_info(emb.handle, C.byref(g), C.byref(rep)), "cf_embedding_info")
+    return g, rep.asdict()
+
+
+def cf_draw_noise(seed, r0, R, ncells, m_last, dtype, out, stream=None):
+    _check(_lib.cf_draw_noise(seed, r0, R, ncells, m_last, dtype, _ptr(out), _stream(stream)), "cf_draw_noise")
+
+
+def cf_sample_workspace_size(emb, R, dtype):
+    n = C.c_size_t()
+    _check(_lib.cf_sample_workspace_size(emb.handle, R, dtype, C.byref(n)), "cf_sample_workspace_size")
+    return n.value
+
+
+def cf_sample(emb, seed, r0, R, dtype, fields_out, ws, ws_bytes, stream=None):
+    _check(_lib.cf_sample(emb.handle, seed, r0, R, dtype, _ptr(fields_out), _ptr(ws), ws_bytes, _stream(stream)),
+           "cf_sample")
+
+
+def make_lp(sigma2, nbar, counts_out, seed, f=None, delta_out=None):
+    p = cf_lp_params()
+    p.sigma2, p.nbar, p.seed = float(sigma2), float(nbar), int(seed)
+    p.f, p.delta_out, p.counts_out = _ptr(f), _ptr(delta_out), _ptr(counts_out)
+    return p
+
+
+def cf_sample_lp(emb, seed, r0, R, dtype, fields_out, lp, ws, ws_bytes, stream=None):
+    _check(_lib.cf_sample_lp(emb.handle, seed, r0, R, dtype, _ptr(fields_out), C.byref(lp), _ptr(ws), ws_bytes,
+                             _stream(stream)), "cf_sample_lp")
+
+
+def cf_lognormal_poisson(G, dtype, cells_per_field, nfields, sigma2, nbar, f, seed, field0, delta_out, counts_out,
+                         stream=None):
+    _check(_lib.cf_lognormal_poisson(_ptr(G), dtype, cells_per_field, nfields, sigma2, nbar, _ptr(f), seed, field0,
+                                     _ptr(delta_out), _ptr(counts_out), _stream(stream)), "cf_lognormal_poisson")
+
+
+def cf_power_spectrum_workspace_size(grid, nfields, bins, dtype):
+    n = C.c_size_t()
+    _check(_lib.cf_power_spectrum_workspace_size(C.byref(grid), nfields, C.byref(bins), dtype, C.byref(n)),
+           "cf_power_spectrum_workspace_size")
+    return n.value
+
+
+def cf_power_spectrum(fields, dtype, grid, nfields, bins, pk_out, nmodes_out, mean=None, cov=None, ws=None,
+                      ws_bytes=0, stream=None):
+    _check(_lib.cf_power_spectrum(_ptr(fields), dtype, C.byref(grid), nfields, C.byref(bins), _ptr(pk_out),
+                                  _ptr(nmodes_out), _ptr(mean), _ptr(cov), _ptr(ws), ws_bytes, _stream(stream)),
+           "cf_power_spectrum")
+
+
+def cf_power_spectrum_counts(counts, f, grid, nfields, bins, pk_out, nmodes_out, mean=None, cov=None, ws=None,
+                             ws_bytes=0, stream=None):
+    _check(_lib.cf_power_spectrum_counts(_ptr(counts), _ptr(f), C.byref(grid), nfields, C.byref(bins),
+                                         _ptr(pk_out), _ptr(nmodes_out), _ptr(mean), _ptr(cov), _ptr(ws), ws_bytes,
+                                         _stream(stream)), "cf_power_spectrum_counts")
+
+
+def cf_kernel_timing(enable):
+    _check(_lib.cf_kernel_timing(int(bool(enable))), "cf_kernel_timing")
+
+
+def cf_kernel_timing_read():
+    """{kernel: (launches, total_ms)} accumulated since cf_kernel_timing(1)."""
+    import json
+    need = C.c_size_t()
+    _lib.cf_kernel_timing_read(None, 0, C.byref(need))
+    buf = C.create_string_buffer(need.value + 64)
+    _check(_lib.cf_kernel_timing_read(buf, len(buf), C.byref(need)), "cf_kernel_timing_read")
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def cf_last_error():
+    return _lib.cf_last_error().decode(errors="replace")
+
+
+def cf_version():
+    return _lib.cf_version().decode()
+
+
+def raw_lib():
+    """The loaded ctypes library (for ABI tests)."""
+    return _lib

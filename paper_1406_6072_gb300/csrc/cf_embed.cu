@@ -1,0 +1,378 @@
+// cf_embed.cu -- steps a1-a3: circulant embedding of the two-point function,
+// binary64 eigenvalues and the positivity check (section 2, eqs. (grid),
+// (Specd), (condition)).
+#include <math.h>
+
+#include "cf_kernels.cuh"
+
+namespace cf {
+
+// a1: first row of the circulant, c(m) = xi(|lag(m)|), lag(m_i) = m_i for
+// m_i < n_i and m_i - M_i otherwise (the grid of eq. (grid) runs -n..n-1).
+__global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, double beta,
+                           double* __restrict__ c, C2<double>* __restrict__ z) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.mtotal;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx;
+        double r2 = 0.0;
+        for (int a = g.ndim - 1; a >= 0; --a) {
+            const long long m = rem % g.m[a];
+            rem /= g.m[a];
+            const long long lag = m < g.n[a] ? m : m - g.m[a];
+            const double x = (double)lag * g.cell[a];
+            r2 += x * x;
+        }
+        double v;
+        if (kind == CF_XI_GAUSSIAN)
+            v = amp * exp(-r2 / (2.0 * scale * scale));
+        else if (kind == CF_XI_GEN_CAUCHY)
+            v = amp * pow(1.0 + r2 / (scale * scale), -beta);
+        else
+            v = amp * exp(-sqrt(r2) / scale);
+        c[idx] = v;
+        z[idx] = mk(v, 0.0);
+    }
+}
+
+__global__ void k_real_to_complex(const double* __restrict__ a, double* __restrict__ c_copy,
+                                  C2<double>* __restrict__ z, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = a[i];
+        if (c_copy) c_copy[i] = v;
+        z[i] = mk(v, 0.0);
+    }
+}
+
+__global__ void k_take_real(const C2<double>* __restrict__ z, double scale, double* __restrict__ out,
+                            long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = z[i].x * scale;
+}
+
+struct EmbedStats {
+    double lmin, lmax, tau, neg_mass, cov_error;
+    unsigned long long n_negative, n_zeroed;
+};
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+// block-wide reduction helpers (kRedThreads threads)
+__device__ __forceinline__ double block_min(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) { return -block_min(-v, sh); }
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_minmax_partial(const double* __restrict__ lam, long long total, double* __restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    double mn = INFINITY, mx = -INFINITY;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        mn = fmin(mn, l);
+        mx = fmax(mx, l);
+    }
+    mn = block_min(mn, sh);
+    mx = block_max(mx, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = mn;
+        part[2 * blockIdx.x + 1] = mx;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_minmax_final(const double* __restrict__ part, int nparts, EmbedStats* st) {
+    __shared__ double sh[kRedThreads];
+    double mn = INFINITY, mx = -INFINITY;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        mn = fmin(mn, part[2 * i]);
+        mx = fmax(mx, part[2 * i + 1]);
+    }
+    mn = block_min(mn, sh);
+    mx = block_max(mx, sh);
+    if (threadIdx.x == 0) {
+        st->lmin = mn;
+        st->lmax = mx;
+        st->tau = 1e-12 * mx;
+        st->neg_mass = 0.0;
+        st->cov_error = 0.0;
+        st->n_negative = 0;
+        st->n_zeroed = 0;
+    }
+}
+
+// a3: lambda+ = lambda if lambda > tau; 0 if |lambda| <= tau (zeroed); 0 if
+// lambda < -tau (negative: counted, its |lambda| summed); s = sqrt(lambda+).
+__global__ void __launch_bounds__(kRedThreads)
+    k_threshold(const double* __restrict__ lam, long long total, const EmbedStats* __restrict__ st,
+                double norm, double* __restrict__ s64, float* __restrict__ s32,
+                double* __restrict__ lam_plus_or_null, double* __restrict__ part,
+                unsigned long long* __restrict__ counts) {
+    __shared__ double sh[kRedThreads];
+    const double tau = st->tau;
+    double neg = 0.0;
+    unsigned long long nneg = 0, nzero = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        double lp;
+        if (l > tau) {
+            lp = l;
+        } else if (l >= -tau) {
+            lp = 0.0;
+            ++nzero;
+        } else {
+            lp = 0.0;
+            ++nneg;
+            neg += -l;
+        }
+        const double sv = sqrt(lp) * norm;
+        s64[i] = sv;
+        s32[i] = (float)sv;
+        if (lam_plus_or_null) lam_plus_or_null[i] = lp;
+    }
+    neg = block_sum(neg, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = neg;
+    if (nneg) atomicAdd(&counts[0], nneg);
+    if (nzero) atomicAdd(&counts[1], nzero);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_threshold_final(const double* __restrict__ part, int nparts, const unsigned long long* counts,
+                      EmbedStats* st) {
+    __shared__ double sh[kRedThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        st->neg_mass = s;
+        st->n_negative = counts[0];
+        st->n_zeroed = counts[1];
+    }
+}
+
+// realised covariance error max |Re z/M^d - c| over survey lags (no index == n)
+__global__ void __launch_bounds__(kRedThreads)
+    k_cov_error_partial(const C2<double>* __restrict__ z, const double* __restrict__ c, GridInfo g,
+                        double inv_total, double* __restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    double mx = 0.0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.mtotal;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx;
+        bool survey = true;
+        for (int a = g.ndim - 1; a >= 0; --a) {
+            const long long m = rem % g.m[a];
+            rem /= g.m[a];
+            if (m == g.n[a]) survey = false;
+        }
+        if (survey) mx = fmax(mx, fabs(z[idx].x * inv_total - c[idx]));
+    }
+    mx = block_max(mx, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = mx;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_cov_error_final(const double* __restrict__ part, int nparts, EmbedStats* st) {
+    __shared__ double sh[kRedThreads];
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) mx = fmax(mx, part[i]);
+    mx = block_max(mx, sh);
+    if (threadIdx.x == 0) st->cov_error = mx;
+}
+
+// lambda+ as a complex array (for the realised-covariance pass)
+__global__ void k_lambda_plus_complex(const double* __restrict__ lam, double tau,
+                                      C2<double>* __restrict__ z, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        z[i] = mk(l > tau ? l : 0.0, 0.0);
+    }
+}
+
+// Device buffers of one embedding computation.
+struct EmbedScratch {
+    C2<double>* z = nullptr;
+    double* c = nullptr;
+    double* part = nullptr;
+    EmbedStats* st = nullptr;
+    unsigned long long* counts = nullptr;
+    cudaStream_t s = nullptr;
+    ~EmbedScratch() {
+        if (z) cudaFreeAsync(z, s);
+        if (c) cudaFreeAsync(c, s);
+        if (part) cudaFreeAsync(part, s);
+        if (st) cudaFreeAsync(st, s);
+        if (counts) cudaFreeAsync(counts, s);
+    }
+};
+
+// Common tail: z holds lambda (complex, Re used), c the embedded row (target
+// covariance).  Runs a3 and builds the embedding.
+static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t flags,
+                                  cf_embedding** out, cf_embed_report* rep) {
+    cudaStream_t s = sc.s;
+    const long long total = gi.mtotal;
+    const int blocks = grid_blocks(total, kRedThreads, kRedBlocks);
+    cf_embedding* e = new cf_embedding();
+    e->grid = gi;
+    CF_CUDA(cudaGetDevice(&e->device));
+    auto cleanup = [&]() { cf_embedding_free(e); };
+    if (cudaMallocAsync((void**)&e->lambda, sizeof(double) * total, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&e->s64, sizeof(double) * total, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&e->s32, sizeof(float) * total, s) != cudaSuccess) {
+        cleanup();
+        return fail(CF_ERR_NOMEM, "device allocation of the embedding (%lld cells) failed", total);
+    }
+    ScopedKernelTimer kt(s, "embed_psd");
+    k_take_real<<<blocks, kRedThreads, 0, s>>>(sc.z, 1.0, e->lambda, total);
+    k_minmax_partial<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.part);
+    k_minmax_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
+    CF_CUDA(cudaMemsetAsync(sc.counts, 0, 2 * sizeof(unsigned long long), s));
+    const bool want_error = (flags & CF_EMBED_CLAMP) && !(flags & CF_EMBED_SKIP_ERROR);
+    k_threshold<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.st, 1.0 / sqrt((double)total), e->s64,
+                                               e->s32, nullptr, sc.part, sc.counts);
+    k_threshold_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.counts, sc.st);
+    CF_CHECK_LAUNCH();
+    EmbedStats st{};
+    CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
+    CF_CUDA(cudaStreamSynchronize(s));
+    cf_embed_report r{};
+    r.lambda_min = st.lmin;
+    r.lambda_max = st.lmax;
+    r.tau = st.tau;
+    r.neg_mass = st.neg_mass;
+    r.n_negative = (int64_t)st.n_negative;
+    r.n_zeroed = (int64_t)st.n_zeroed;
+    r.clamped = 0;
+    r.exact = 1;
+    e->tau = st.tau;
+    if (!(st.lmax > 0.0)) {
+        r.exact = 0;
+        if (rep) *rep = r;
+        cleanup();
+        return fail(CF_ERR_NOT_PSD, "largest eigenvalue %.3e is not positive", st.lmax);
+    }
+    if (st.n_negative > 0) {
+        if (!(flags & CF_EMBED_CLAMP)) {
+            r.exact = 0;
+            if (rep) *rep = r;
+            cleanup();
+            return fail(CF_ERR_NOT_PSD,
+                        "%llu eigenvalues below -tau (lambda_min/lambda_max = %.3e); set CF_EMBED_CLAMP",
+                        st.n_negative, st.lmin / st.lmax);
+        }
+        r.clamped = 1;
+        r.exact = 0;
+        if (want_error) {
+            // realised covariance = IDFT(lambda+)/M^d
+            k_lambda_plus_complex<<<blocks, kRedThreads, 0, s>>>(e->lambda, st.tau, sc.z, total);
+            CF_CHECK_LAUNCH();
+            CF_TRY((fft_nd_inplace<double, +1>(sc.z, gi, s)));
+            k_cov_error_partial<<<blocks, kRedThreads, 0, s>>>(sc.z, sc.c, gi, 1.0 / (double)total, sc.part);
+            k_cov_error_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
+            CF_CHECK_LAUNCH();
+            CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
+            CF_CUDA(cudaStreamSynchronize(s));
+            r.cov_error = st.cov_error;
+        }
+    }
+    e->report = r;
+    if (rep) *rep = r;
+    *out = e;
+    return CF_OK;
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+
+static cf_status alloc_scratch(EmbedScratch& sc, long long total) {
+    cudaStream_t s = sc.s;
+    if (cudaMallocAsync((void**)&sc.z, sizeof(C2<double>) * total, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&sc.c, sizeof(double) * total, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&sc.part, sizeof(double) * kRedBlocks * 2, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&sc.st, sizeof(EmbedStats), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&sc.counts, sizeof(unsigned long long) * 2, s) != cudaSuccess)
+        return fail(CF_ERR_NOMEM, "device allocation for the embedding of %lld cells failed", total);
+    return CF_OK;
+}
+
+extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags, cf_stream_t stream,
+                              cf_embedding** out, cf_embed_report* rep) {
+    clear_error();
+    if (!out) return fail(CF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!xi) return fail(CF_ERR_ARG, "xi is NULL");
+    GridInfo gi;
+    CF_TRY(check_grid(g, &gi));
+    if (xi->kind < CF_XI_GAUSSIAN || xi->kind > CF_XI_TABLE) return fail(CF_ERR_ARG, "unknown xi kind %d", xi->kind);
+    if (xi->kind == CF_XI_TABLE && !xi->table) return fail(CF_ERR_ARG, "CF_XI_TABLE needs a table");
+    if (xi->kind != CF_XI_TABLE && !(xi->scale > 0.0)) return fail(CF_ERR_ARG, "xi scale must be > 0");
+    CF_TRY(ensure_device_init());
+    EmbedScratch sc;
+    sc.s = (cudaStream_t)stream;
+    CF_TRY(alloc_scratch(sc, gi.mtotal));
+    const int blocks = grid_blocks(gi.mtotal, kRedThreads, kRedBlocks);
+    if (xi->kind == CF_XI_TABLE) {
+        if (xi->table_on_device) {
+            k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(xi->table, sc.c, sc.z, gi.mtotal);
+        } else {
+            CF_CUDA(cudaMemcpyAsync(sc.c, xi->table, sizeof(double) * gi.mtotal, cudaMemcpyHostToDevice, sc.s));
+            k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(sc.c, nullptr, sc.z, gi.mtotal);
+        }
+    } else {
+        ScopedKernelTimer kt(sc.s, "embed_fill");
+        k_fill_row<<<blocks, kRedThreads, 0, sc.s>>>(gi, xi->kind, xi->amp, xi->scale, xi->beta, sc.c, sc.z);
+    }
+    CF_CHECK_LAUNCH();
+    CF_TRY((fft_nd_inplace<double, -1>(sc.z, gi, sc.s)));
+    return finish_embedding(gi, sc, flags, out, rep);
+}
+
+extern "C" cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
+                                          cf_stream_t stream, cf_embedding** out, cf_embed_report* rep) {
+    clear_error();
+    if (!out) return fail(CF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!lambda) return fail(CF_ERR_ARG, "lambda is NULL");
+    GridInfo gi;
+    CF_TRY(check_grid(g, &gi));
+    CF_TRY(ensure_device_init());
+    EmbedScratch sc;
+    sc.s = (cudaStream_t)stream;
+    CF_TRY(alloc_scratch(sc, gi.mtotal));
+    const int blocks = grid_blocks(gi.mtotal, kRedThreads, kRedBlocks);
+    // target covariance c = IDFT(lambda)/M^d, for the error pass
+    k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(lambda, nullptr, sc.z, gi.mtotal);
+    CF_CHECK_LAUNCH();
+    CF_TRY((fft_nd_inplace<double, +1>(sc.z, gi, sc.s)));
+    k_take_real<<<blocks, kRedThreads, 0, sc.s>>>(sc.z, 1.0 / (double)gi.mtotal, sc.c, gi.mtotal);
+    k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(lambda, nullptr, sc.z, gi.mtotal);
+    CF_CHECK_LAUNCH();
+    return finish_embedding(gi, sc, flags, out, rep);
+}

@@ -1,0 +1,207 @@
+// cf_fft.cuh -- CTA-level line FFTs for sm_103a.
+//
+// A CTA transforms several lines of length L (a power of two, 2..4096) at
+// once.  Each line is handled by TL = L/E threads that hold E points each in
+// registers (E = 16 in binary32, 8 in binary64).  The transform is a Stockham
+// autosort FFT: every stage applies radix-R butterflies (R = E, the last stage
+// R = L / E^k) entirely in registers, and consecutive stages exchange data
+// through shared memory (one write + one read per stage boundary), padded by
+// one slot every E points so that the stride-R accesses of the early stages
+// hit distinct banks.  The first stage's inputs come from the caller
+// (generated noise or global loads) and the last stage's outputs go to a
+// caller functor (global stores with cropping, or a fused epilogue), so a
+// transform costs (#stages - 1) shared-memory round trips and no global
+// traffic beyond its input and output.
+#pragma once
+#include "cf_device.cuh"
+
+namespace cf {
+
+constexpr int TWN = 8192;  // twiddle table length: w[j] = exp(+2 pi i j / TWN)
+
+template <typename T>
+struct FftE;
+template <>
+struct FftE<float> {
+    static constexpr int value = 16;
+};
+template <>
+struct FftE<double> {
+    static constexpr int value = 8;
+};
+
+template <typename T, int L>
+struct LineGeom {
+    static constexpr int E = L < FftE<T>::value ? L : FftE<T>::value;  // points per thread
+    static constexpr int TL = L / E;                                   // threads per line
+    static constexpr int PADDED = L + L / E;                           // padded line length
+};
+
+// padded shared-memory slot of point p
+template <int E>
+__device__ __forceinline__ int padp(int p) { return p + p / E; }
+
+// Lines stored one after the other (row tiles).
+template <int E, int STRIDE>
+struct RowLayout {
+    __device__ __forceinline__ int operator()(int line, int p) const { return line * STRIDE + padp<E>(p); }
+};
+// Lines interleaved point-major (column tiles of C lines).
+template <int E, int C>
+struct ColLayout {
+    __device__ __forceinline__ int operator()(int line, int p) const { return padp<E>(p) * C + line; }
+};
+
+// ---------------------------------------------------------------- radix kernels
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft2(C2<T>& a, C2<T>& b) {
+    const C2<T> t = a;
+    a = t + b;
+    b = t - b;
+}
+
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3) {
+    const C2<T> t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = mul_si<SIGN>(a1 - a3);
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = t1 + t3;
+    a3 = t1 - t3;
+}
+
+// multiply by exp(SIGN i theta) given (cos theta, sin theta)
+template <int SIGN, typename T>
+__device__ __forceinline__ C2<T> rot(C2<T> a, T c, T s) {
+    return cmul(a, mk(c, SIGN > 0 ? s : -s));
+}
+
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft8(C2<T>* v) {
+    dft4<SIGN>(v[0], v[2], v[4], v[6]);
+    dft4<SIGN>(v[1], v[3], v[5], v[7]);
+    const T h = (T)0.70710678118654752440;
+    const C2<T> o0 = v[1];
+    const C2<T> o1 = rot<SIGN>(v[3], h, h);
+    const C2<T> o2 = mul_si<SIGN>(v[5]);
+    const C2<T> o3 = rot<SIGN>(v[7], -h, h);
+    const C2<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    v[0] = e0 + o0;
+    v[4] = e0 - o0;
+    v[1] = e1 + o1;
+    v[5] = e1 - o1;
+    v[2] = e2 + o2;
+    v[6] = e2 - o2;
+    v[3] = e3 + o3;
+    v[7] = e3 - o3;
+}
+
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft16(C2<T>* v) {
+    // four length-4 DFTs over n1 (stride 4), twiddles w16^{n2 k1}, four more over n2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<SIGN>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+    const T h = (T)0.70710678118654752440;
+    v[5] = rot<SIGN>(v[5], c1, s1);      // n2=1,k1=1: w^1
+    v[9] = rot<SIGN>(v[9], h, h);        // n2=1,k1=2: w^2
+    v[13] = rot<SIGN>(v[13], s1, c1);    // n2=1,k1=3: w^3
+    v[6] = rot<SIGN>(v[6], h, h);        // n2=2,k1=1: w^2
+    v[10] = mul_si<SIGN>(v[10]);         // n2=2,k1=2: w^4
+    v[14] = rot<SIGN>(v[14], -h, h);     // n2=2,k1=3: w^6
+    v[7] = rot<SIGN>(v[7], s1, c1);      // n2=3,k1=1: w^3
+    v[11] = rot<SIGN>(v[11], -h, h);     // n2=3,k1=2: w^6
+    v[15] = rot<SIGN>(v[15], -c1, -s1);  // n2=3,k1=3: w^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4x4 block
+    C2<T> t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+template <int R, int SIGN, typename T>
+__device__ __forceinline__ void dftR(C2<T>* v) {
+    if constexpr (R == 2) {
+        dft2<SIGN>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4<SIGN>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        dft8<SIGN>(v);
+    } else if constexpr (R == 16) {
+        dft16<SIGN>(v);
+    }
+}
+
+template <int SIGN, typename T>
+__device__ __forceinline__ C2<T> twiddle(const C2<T>* __restrict__ tw, int idx) {
+    const C2<T> w = tw[idx];
+    return SIGN > 0 ? w : mk(w.x, -w.y);
+}
+
+// ---------------------------------------------------------------- Stockham stages
+// v holds this thread's inputs of the stage with sub-transform size NS:
+// butterfly b (jb = j + b*TL) takes points jb + q*(L/R), q < R, in v[b*R + q].
+// KEEP: only outputs with point index < KEEP are produced (KEEP = L or L/2).
+// out(line, point, value) receives each kept output of the last stage.
+template <typename T, int L, int E, int SIGN, int KEEP, int NS, class Lay, class Out>
+__device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, int j, C2<T> (&v)[E],
+                                          const C2<T>* __restrict__ tw, Out& out) {
+    constexpr int R = (E < L / NS) ? E : (L / NS);
+    constexpr int TL = L / E;
+    constexpr int B = E / R;
+    constexpr int STRIDE = L / R;
+    if constexpr (NS > 1) {
+        constexpr int TWS = TWN / (NS * R);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int k = (j + b * TL) & (NS - 1);
+#pragma unroll
+            for (int q = 1; q < R; ++q)
+                v[b * R + q] = cmul(v[b * R + q], twiddle<SIGN>(tw, (q * k * TWS) & (TWN - 1)));
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) dftR<R, SIGN>(&v[b * R]);
+    if constexpr (NS * R == L) {
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+                if (q * STRIDE < KEEP) out(line, j + b * TL + q * STRIDE, v[b * R + q]);
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int jb = j + b * TL;
+            const int base = (jb / NS) * (NS * R) + (jb & (NS - 1));
+#pragma unroll
+            for (int q = 0; q < R; ++q) sm[lay(line, base + q * NS)] = v[b * R + q];
+        }
+        __syncthreads();
+        constexpr int NS2 = NS * R;
+        constexpr int R2 = (E < L / NS2) ? E : (L / NS2);
+        constexpr int B2 = E / R2;
+        constexpr int STRIDE2 = L / R2;
+#pragma unroll
+        for (int b = 0; b < B2; ++b)
+#pragma unroll
+            for (int q = 0; q < R2; ++q) v[b * R2 + q] = sm[lay(line, j + b * TL + q * STRIDE2)];
+        fft_stage<T, L, E, SIGN, KEEP, NS2>(sm, lay, line, j, v, tw, out);
+    }
+}
+
+// Full transform of a line whose first-stage inputs v[q] = x[j + q*L/E] are
+// already in registers.  Every thread of the CTA must call this (it contains
+// __syncthreads); threads without a valid line pass dummy data.
+template <typename T, int L, int SIGN, int KEEP, class Lay, class Out>
+__device__ __forceinline__ void line_fft(C2<T>* sm, const Lay& lay, int line, int j,
+                                         C2<T> (&v)[LineGeom<T, L>::E], const C2<T>* __restrict__ tw,
+                                         Out& out) {
+    fft_stage<T, L, LineGeom<T, L>::E, SIGN, KEEP, 1>(sm, lay, line, j, v, tw, out);
+}
+
+}  // namespace cf

@@ -1,0 +1,91 @@
+// cf_internal.h -- host-side declarations shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "../../include/cf.h"
+#include "cf_device.cuh"
+
+namespace cf {
+
+// thread-local error message; returns st for tail calls
+cf_status fail(cf_status st, const char* fmt, ...);
+void clear_error();
+
+#define CF_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::cf::fail(CF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CF_CHECK_LAUNCH()                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess)                                                             \
+            return ::cf::fail(CF_ERR_CUDA, "kernel launch failed at %s:%d: %s", __FILE__,  \
+                              __LINE__, cudaGetErrorString(e_));                           \
+    } while (0)
+
+#define CF_TRY(expr)                       \
+    do {                                   \
+        cf_status st_ = (expr);            \
+        if (st_ != CF_OK) return st_;      \
+    } while (0)
+
+// One-time per-device set-up (twiddle tables).  Synchronises the device the
+// first time it runs on a device.
+cf_status ensure_device_init();
+const C2<float>* twiddles_f32();   // current device, TWN entries exp(+2 pi i j/TWN)
+const C2<double>* twiddles_f64();
+
+inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int log2i(long long v) {
+    int r = 0;
+    while ((1ll << r) < v) ++r;
+    return r;
+}
+
+constexpr long long kMaxLine = 4096;  // longest supported transform line
+
+// Per-launch CUDA-event timing (see cf_kernel_timing).  Constructed right
+// before a launch and destroyed right after it on the same stream.
+class ScopedKernelTimer {
+  public:
+    ScopedKernelTimer(cudaStream_t s, const char* name, long long variant = -1);
+    ~ScopedKernelTimer();
+    ScopedKernelTimer(const ScopedKernelTimer&) = delete;
+    ScopedKernelTimer& operator=(const ScopedKernelTimer&) = delete;
+
+  private:
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    char name_[96];
+};
+
+// Validates a survey grid for the sampler; fills M and totals.
+struct GridInfo {
+    int ndim;
+    long long n[3];
+    long long m[3];
+    double cell[3];
+    long long ncell;   // prod n
+    long long mtotal;  // prod m
+};
+cf_status check_grid(const cf_grid* g, GridInfo* gi);
+
+}  // namespace cf
+
+struct cf_embedding {
+    cf::GridInfo grid;
+    double* lambda = nullptr;    // raw eigenvalues [mtotal]
+    double* s64 = nullptr;       // sqrt(lambda+) * mtotal^{-1/2} [mtotal]
+    float* s32 = nullptr;        // binary32 copy of s64 [mtotal]
+    double tau = 0.0;
+    cf_embed_report report{};
+    int device = 0;
+};

@@ -1,0 +1,227 @@
+// cf_kernels.cuh -- transform-pass kernels shared by the embedding, the
+// sampler and the power spectrum, and the compile-time dispatch over the line
+// length.
+#pragma once
+#include <stdio.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "cf_fft.cuh"
+#include "cf_internal.h"
+
+namespace cf {
+
+// --------------------------------------------------------------------------
+// Fused field epilogue of the last inverse-transform pass: split W into the
+// Re/Im fields and (binary32) apply the lognormal transform and the Poisson
+// draw of section 3.1 to both fields of the survey cell.
+// --------------------------------------------------------------------------
+template <typename T>
+struct FieldEpi {
+    T* fields;          // [chunk][2][cells] or null
+    int32_t* counts;    // [chunk][2][cells] or null (no lognormal/Poisson step)
+    float* delta;       // [chunk][2][cells] or null
+    const float* f;     // [cells] or null (f = 1)
+    double half_sigma2;
+    float half_sigma2_f;
+    double nbar;
+    uint32_t pkey0, pkey1;
+    uint32_t r0;        // global index of the chunk's first realization
+    long long cells;
+
+    __device__ __forceinline__ void operator()(int rl, long long cell, C2<T> w) const {
+        const size_t base = (size_t)rl * 2 * (size_t)cells + (size_t)cell;
+        if (fields) {
+            fields[base] = w.x;
+            fields[base + cells] = w.y;
+        }
+        if (counts) {
+            const float g0 = (float)w.x, g1 = (float)w.y;
+            const uint4 x = poisson_words((unsigned long long)cell, r0 + (uint32_t)rl, pkey0, pkey1);
+            const float fi = f ? f[cell] : 1.0f;
+            counts[base] = poisson_count_fast(g0, half_sigma2, half_sigma2_f, nbar, fi, bits53(x.x, x.y));
+            counts[base + cells] =
+                poisson_count_fast(g1, half_sigma2, half_sigma2_f, nbar, fi, bits53(x.z, x.w));
+            if (delta) {
+                delta[base] = expf(g0 - half_sigma2_f) - 1.0f;
+                delta[base + cells] = expf(g1 - half_sigma2_f) - 1.0f;
+            }
+        }
+    }
+};
+
+// --------------------------------------------------------------------------
+// Column pass: FFT along the middle axis of in[outer][L][inner] for a tile of
+// C consecutive inner indices per CTA.  mode 0: complex output
+// out[outer][KEEP][inner] (in place allowed when KEEP == L); mode 1: field
+// epilogue with realization = outer index and cell = point*inner + i.
+// --------------------------------------------------------------------------
+template <typename T, int L>
+struct ColsCfg {
+    using G = LineGeom<T, L>;
+    static constexpr int C = G::TL >= 256 ? 1 : ((256 / G::TL) > 32 ? 32 : (256 / G::TL));
+    static constexpr int THREADS = C * G::TL;
+    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)C * (size_t)G::PADDED;
+};
+
+template <typename T, int L, int SIGN, int KEEP_HALF>
+__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS)
+    k_cols(const C2<T>* in, long long inner, C2<T>* out, int mode, FieldEpi<T> epi,
+           const C2<T>* __restrict__ tw) {
+    using Cfg = ColsCfg<T, L>;
+    using G = typename Cfg::G;
+    constexpr int KEEP = KEEP_HALF ? L / 2 : L;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
+    const int ln = threadIdx.x % Cfg::C;
+    const int j = threadIdx.x / Cfg::C;
+    const long long i = (long long)blockIdx.x * Cfg::C + ln;
+    const long long o = blockIdx.y;
+    const bool valid = i < inner;
+    const C2<T>* src = in + (size_t)o * L * (size_t)inner + (size_t)(valid ? i : 0);
+    C2<T> v[G::E];
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)inner];
+    auto sink = [&](int, int p, C2<T> val) {
+        if (!valid) return;
+        if (mode == 0)
+            out[((size_t)o * KEEP + p) * (size_t)inner + i] = val;
+        else
+            epi((int)o, (long long)p * inner + i, val);
+    };
+    line_fft<T, L, SIGN, KEEP>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+}
+
+// --------------------------------------------------------------------------
+// Row pass on contiguous lines: in-place complex FFT of rows of length L.
+// --------------------------------------------------------------------------
+template <typename T, int L>
+struct RowsCfg {
+    using G = LineGeom<T, L>;
+    static constexpr int ROWS = G::TL >= 256 ? 1 : 256 / G::TL;
+    static constexpr int THREADS = ROWS * G::TL;
+    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
+};
+
+template <typename T, int L, int SIGN>
+__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS)
+    k_rows_c2c(C2<T>* data, long long nrows, const C2<T>* __restrict__ tw) {
+    using Cfg = RowsCfg<T, L>;
+    using G = typename Cfg::G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
+    const int line = threadIdx.x / G::TL;
+    const int j = threadIdx.x % G::TL;
+    const long long row = (long long)blockIdx.x * Cfg::ROWS + line;
+    const bool valid = row < nrows;
+    C2<T>* base = data + (size_t)(valid ? row : 0) * L;
+    C2<T> v[G::E];
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) v[q] = base[j + q * (L / G::E)];
+    auto sink = [&](int, int p, C2<T> val) {
+        if (valid) base[p] = val;
+    };
+    line_fft<T, L, SIGN, L>(sm, RowLayout<G::E, G::PADDED>(), line, j, v, tw, sink);
+}
+
+// --------------------------------------------------------------------------
+// Launch helpers.
+// --------------------------------------------------------------------------
+template <class K>
+inline cf_status prepare_smem(K kernel, size_t smem) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return fail(CF_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    }
+    return CF_OK;
+}
+
+// Calls f(std::integral_constant<int, L>{}) for the runtime line length L.
+template <class F>
+inline cf_status dispatch_line(long long L, F&& f) {
+    switch (L) {
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    case 64: return f(std::integral_constant<int, 64>{});
+    case 128: return f(std::integral_constant<int, 128>{});
+    case 256: return f(std::integral_constant<int, 256>{});
+    case 512: return f(std::integral_constant<int, 512>{});
+    case 1024: return f(std::integral_constant<int, 1024>{});
+    case 2048: return f(std::integral_constant<int, 2048>{});
+    case 4096: return f(std::integral_constant<int, 4096>{});
+    default: return fail(CF_ERR_UNSUPPORTED, "transform length %lld not supported", L);
+    }
+}
+
+template <typename T>
+inline const C2<T>* twiddles();
+template <>
+inline const C2<float>* twiddles<float>() { return twiddles_f32(); }
+template <>
+inline const C2<double>* twiddles<double>() { return twiddles_f64(); }
+
+// Column pass launch over in[outer][L][inner].
+template <typename T, int SIGN, int KEEP_HALF>
+inline cf_status launch_cols(long long L, const C2<T>* in, long long outer, long long inner, C2<T>* out,
+                             int mode, const FieldEpi<T>& epi, cudaStream_t s) {
+    if (outer > 65535) return fail(CF_ERR_UNSUPPORTED, "column pass with %lld outer slices", outer);
+    return dispatch_line(L, [&](auto Lc) -> cf_status {
+        constexpr int LL = decltype(Lc)::value;
+        using Cfg = ColsCfg<T, LL>;
+        auto kern = k_cols<T, LL, SIGN, KEEP_HALF>;
+        CF_TRY(prepare_smem(kern, Cfg::SMEM));
+        dim3 grid((unsigned)((inner + Cfg::C - 1) / Cfg::C), (unsigned)outer);
+        const char* name = SIGN > 0 ? (mode == 1 ? (epi.counts ? "icols_fields_lp" : "icols_fields") : "icols")
+                                    : "fcols";
+        char full[64];
+        snprintf(full, sizeof full, "%s_%s", name, sizeof(T) == 4 ? "f32" : "f64");
+        ScopedKernelTimer kt(s, full, LL);
+        kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(in, inner, out, mode, epi, twiddles<T>());
+        CF_CHECK_LAUNCH();
+        return CF_OK;
+    });
+}
+
+template <typename T, int SIGN>
+inline cf_status launch_rows_c2c(long long L, C2<T>* data, long long nrows, cudaStream_t s) {
+    return dispatch_line(L, [&](auto Lc) -> cf_status {
+        constexpr int LL = decltype(Lc)::value;
+        using Cfg = RowsCfg<T, LL>;
+        auto kern = k_rows_c2c<T, LL, SIGN>;
+        CF_TRY(prepare_smem(kern, Cfg::SMEM));
+        dim3 grid((unsigned)((nrows + Cfg::ROWS - 1) / Cfg::ROWS));
+        ScopedKernelTimer kt(s, SIGN > 0 ? (sizeof(T) == 4 ? "irows_f32" : "irows_f64")
+                                         : (sizeof(T) == 4 ? "frows_f32" : "frows_f64"), LL);
+        kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(data, nrows, twiddles<T>());
+        CF_CHECK_LAUNCH();
+        return CF_OK;
+    });
+}
+
+// In-place N-D complex transform (unnormalised) of data[m0][m1][m2].
+template <typename T, int SIGN>
+inline cf_status fft_nd_inplace(C2<T>* data, const GridInfo& g, cudaStream_t s) {
+    const int d = g.ndim;
+    long long total = g.mtotal;
+    CF_TRY((launch_rows_c2c<T, SIGN>(g.m[d - 1], data, total / g.m[d - 1], s)));
+    for (int a = d - 2; a >= 0; --a) {
+        long long inner = 1, outer = 1;
+        for (int b = a + 1; b < d; ++b) inner *= g.m[b];
+        for (int b = 0; b < a; ++b) outer *= g.m[b];
+        FieldEpi<T> none{};
+        CF_TRY((launch_cols<T, SIGN, 0>(g.m[a], data, outer, inner, data, 0, none, s)));
+    }
+    return CF_OK;
+}
+
+inline int grid_blocks(long long n, int threads, int cap = 152 * 16) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b > cap ? cap : b);
+}
+
+}  // namespace cf

@@ -1,0 +1,447 @@
+// cf_pk.cu -- step d1: binned power spectrum of real fields or count maps
+// (section 3.2, eqs. (Def spec), (Estim)) with its mean and covariance over
+// realizations.
+//
+// Two real fields are transformed at once as z = a + i b along the last axis;
+// the row pass separates A = (Z_k + conj Z_{-k})/2 and B = (Z_k - conj Z_{-k})/2i
+// into half spectra (k_last in [0, n/2]).  The remaining axes are complex
+// column passes; the last one squares, weights (2 for 0 < k_last < n/2, the
+// mirror mode -k) and bins in shared memory before one atomic add per bin.
+#include <math.h>
+
+#include "cf_kernels.cuh"
+
+namespace cf {
+
+constexpr int kMaxBins = 512;
+
+struct Edges {
+    double e[kMaxBins + 1];
+};
+
+enum { PK_FLOAT = 0, PK_DOUBLE = 1, PK_COUNTS = 2 };
+
+__global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int* __restrict__ bin_of) {
+    for (long long k2 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k2 <= k2max;
+         k2 += (long long)gridDim.x * blockDim.x) {
+        int b = -1;
+        if (k2 > 0) {
+            const double kn = sqrt((double)k2);
+            if (kn >= ed.e[0] && kn < ed.e[nbins]) {
+                b = 0;
+                while (!(kn < ed.e[b + 1])) ++b;
+            }
+        }
+        bin_of[k2] = b;
+    }
+}
+
+__device__ __forceinline__ long long signed_mode(long long i, long long n) { return i <= n / 2 ? i : i - n; }
+
+__global__ void k_pk_nmodes(GridInfo g, const int* __restrict__ bin_of, long long k2max,
+                            unsigned long long* __restrict__ nmodes) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ncell;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx, k2 = 0;
+        for (int a = g.ndim - 1; a >= 0; --a) {
+            const long long i = rem % g.n[a];
+            rem /= g.n[a];
+            const long long sn = signed_mode(i, g.n[a]);
+            k2 += sn * sn;
+        }
+        const int b = k2 <= k2max ? bin_of[k2] : -1;
+        if (b >= 0) atomicAdd(&nmodes[b], 1ull);
+    }
+}
+
+__global__ void k_count_totals(const int32_t* __restrict__ counts, long long cells, const float* __restrict__ f,
+                               unsigned long long* __restrict__ ntot, double* __restrict__ fsum) {
+    const int field = blockIdx.y;
+    unsigned long long acc = 0;
+    double facc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells;
+         i += (long long)gridDim.x * blockDim.x) {
+        acc += (unsigned long long)(long long)counts[(size_t)field * cells + i];
+        if (field == 0) facc += f ? (double)f[i] : 1.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        facc += __shfl_down_sync(0xffffffffu, facc, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (acc) atomicAdd(&ntot[field], acc);
+        if (field == 0 && facc != 0.0) atomicAdd(fsum, facc);
+    }
+}
+
+__global__ void k_nhat(const unsigned long long* __restrict__ ntot, const double* __restrict__ fsum, int nfields,
+                       double* __restrict__ nhat) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nfields) nhat[i] = fsum[0] > 0.0 ? (double)ntot[i] / fsum[0] : 0.0;
+}
+
+// Pass 1: pairs of real fields along the last axis -> two half spectra.
+template <typename T, int L>
+struct PkRowsCfg {
+    using G = LineGeom<T, L>;
+    static constexpr int ROWS = G::TL >= 256 ? 1 : 256 / G::TL;
+    static constexpr int THREADS = ROWS * G::TL;
+    static constexpr size_t SMEM = 2 * sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
+};
+
+template <typename T, int L>
+__global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS)
+    k_pk_rows(const void* __restrict__ fields, int kind, const float* __restrict__ f, const double* __restrict__ nhat,
+              long long rows, long long cells, long long nfields, long long f0, C2<T>* __restrict__ out,
+              const C2<T>* __restrict__ tw) {
+    using Cfg = PkRowsCfg<T, L>;
+    using G = typename Cfg::G;
+    constexpr int E = G::E;
+    constexpr int STEP = L / E;
+    constexpr int H = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
+    C2<T>* sm2 = sm + (size_t)Cfg::ROWS * G::PADDED;
+    const int line = threadIdx.x / G::TL;
+    const int j = threadIdx.x % G::TL;
+    const long long row = (long long)blockIdx.x * Cfg::ROWS + line;
+    const bool valid = row < rows;
+    const long long rw = valid ? row : 0;
+    const long long fa = f0 + 2ll * blockIdx.y;  // global field index of A
+    const long long fb = fa + 1;
+    const bool hasb = fb < nfields;
+    T nha = 0, nhb = 0;
+    if (kind == PK_COUNTS) {
+        nha = (T)nhat[fa];
+        nhb = hasb ? (T)nhat[fb] : (T)0;
+    }
+    auto value = [&](long long fld, T nh, long long p) -> T {
+        const size_t at = (size_t)fld * cells + (size_t)rw * L + p;
+        if (kind == PK_FLOAT) return (T)((const float*)fields)[at];
+        if (kind == PK_DOUBLE) return (T)((const double*)fields)[at];
+        const long long cell = rw * L + p;
+        const T fi = f ? (T)f[cell] : (T)1;
+        const T N = (T)((const int32_t*)fields)[at];
+        return (fi != (T)0 && nh > (T)0) ? (N / fi - nh) / nh : (T)0;
+    };
+    C2<T> v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const long long p = j + q * STEP;
+        v[q] = mk(value(fa, nha, p), hasb ? value(fb, nhb, p) : (T)0);
+    }
+    RowLayout<E, G::PADDED> lay;
+    auto sink = [&](int ln, int p, C2<T> val) { sm2[lay(ln, p)] = val; };
+    line_fft<T, L, -1, L>(sm, lay, line, j, v, tw, sink);
+    __syncthreads();
+    if (!valid) return;
+    const long long la = fa - f0, lb = fb - f0;
+    C2<T>* oa = out + ((size_t)la * rows + row) * H;
+    C2<T>* ob = out + ((size_t)lb * rows + row) * H;
+    const T half = (T)0.5;
+    for (int k = j; k < H; k += G::TL) {
+        const C2<T> zk = sm2[lay(line, k & (L - 1))];
+        const C2<T> zm = sm2[lay(line, (L - k) & (L - 1))];
+        oa[k] = mk(half * (zk.x + zm.x), half * (zk.y - zm.y));
+        if (hasb) ob[k] = mk(half * (zk.y + zm.y), half * (zm.x - zk.x));
+    }
+}
+
+// Last pass: FFT along axis 0, |X|^2 with mirror weights, binned.
+template <typename T, int L>
+__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS)
+    k_pk_cols(const C2<T>* __restrict__ in, long long inner, long long H, long long n_mid, long long n_last,
+              const int* __restrict__ bin_of, long long k2max, int nbins, double* __restrict__ acc, long long f0,
+              const C2<T>* __restrict__ tw) {
+    using Cfg = ColsCfg<T, L>;
+    using G = typename Cfg::G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
+    T* sbin = reinterpret_cast<T*>(sm + (size_t)Cfg::C * G::PADDED);
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sbin[b] = (T)0;
+    __syncthreads();
+    const int ln = threadIdx.x % Cfg::C;
+    const int j = threadIdx.x / Cfg::C;
+    const long long i = (long long)blockIdx.x * Cfg::C + ln;
+    const long long o = blockIdx.y;
+    const bool valid = i < inner;
+    const C2<T>* src = in + (size_t)o * L * (size_t)inner + (size_t)(valid ? i : 0);
+    C2<T> v[G::E];
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)inner];
+    const long long il = i % H;          // k_last index in [0, n_last/2]
+    const long long imid = i / H;        // middle-axis index (3D) or 0
+    const long long smid = signed_mode(imid, n_mid);
+    const T w = (il == 0 || 2 * il == n_last) ? (T)1 : (T)2;
+    auto sink = [&](int, int p, C2<T> val) {
+        if (!valid) return;
+        const long long s0 = signed_mode(p, L);
+        const long long k2 = s0 * s0 + smid * smid + il * il;
+        const int b = k2 <= k2max ? bin_of[k2] : -1;
+        if (b >= 0) atomicAdd(&sbin[b], w * (val.x * val.x + val.y * val.y));
+    };
+    line_fft<T, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const T s = sbin[b];
+        if (s != (T)0) atomicAdd(&acc[(size_t)(f0 + o) * nbins + b], (double)s);
+    }
+}
+
+__global__ void k_pk_finalize(const double* __restrict__ acc, const unsigned long long* __restrict__ nmodes,
+                              long long nfields, int nbins, double volfac, double* __restrict__ pk,
+                              int64_t* __restrict__ nmodes_out) {
+    const long long total = nfields * nbins;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx % nbins);
+        const unsigned long long nm = nmodes[b];
+        pk[idx] = nm ? volfac * acc[idx] / (double)nm : 0.0;
+        if (idx < nbins && nmodes_out) nmodes_out[idx] = (int64_t)nmodes[idx];
+    }
+}
+
+__global__ void k_pk_mean(const double* __restrict__ pk, long long nfields, int nbins, double* __restrict__ mean) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    double s = 0.0;
+    for (long long f = 0; f < nfields; ++f) s += pk[f * nbins + b];
+    mean[b] = nfields > 0 ? s / (double)nfields : 0.0;
+}
+
+__global__ void k_pk_cov(const double* __restrict__ pk, const double* __restrict__ mean, long long nfields, int nbins,
+                         double* __restrict__ cov) {
+    const int a = blockIdx.x;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        double s = 0.0;
+        for (long long f = 0; f < nfields; ++f) s += (pk[f * nbins + a] - mean[a]) * (pk[f * nbins + b] - mean[b]);
+        cov[(size_t)a * nbins + b] = nfields > 1 ? s / (double)(nfields - 1) : 0.0;
+    }
+}
+
+// ----------------------------------------------------------------- host side
+struct PkPlan {
+    GridInfo g;         // survey grid (n used as the transform sizes)
+    int nbins;
+    Edges edges;
+    long long k2max;
+    long long H;        // n_last/2 + 1
+    long long rows;     // prod of leading axes
+    size_t elem;
+    long long chunk;    // fields per chunk (even)
+    size_t off_bin, off_nmodes, off_acc, off_nhat, off_fsum, off_ntot, off_half, off_half2, total;
+};
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins* b, size_t elem, PkPlan* P) {
+    if (!grid) return fail(CF_ERR_ARG, "grid is NULL");
+    if (!b) return fail(CF_ERR_ARG, "bins is NULL");
+    if (grid->ndim < 2 || grid->ndim > 3)
+        return fail(grid->ndim == 1 ? CF_ERR_UNSUPPORTED : CF_ERR_ARG, "power spectrum needs ndim 2 or 3");
+    GridInfo& g = P->g;
+    g.ndim = grid->ndim;
+    g.ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a < g.ndim) {
+            g.n[a] = grid->n[a];
+            g.cell[a] = grid->cell[a];
+            if (g.n[a] < 2 || !is_pow2(g.n[a]) || g.n[a] > kMaxLine)
+                return fail(CF_ERR_UNSUPPORTED, "power spectrum needs power-of-two sizes 2..%lld (n[%d] = %lld)",
+                            kMaxLine, a, g.n[a]);
+            if (g.n[a] != grid->n[0]) return fail(CF_ERR_UNSUPPORTED, "power spectrum needs equal sizes on all axes");
+            if (!(g.cell[a] > 0.0)) return fail(CF_ERR_ARG, "cell must be > 0");
+        } else {
+            g.n[a] = 1;
+            g.cell[a] = 1.0;
+        }
+        g.m[a] = g.n[a];
+        g.ncell *= g.n[a];
+    }
+    g.mtotal = g.ncell;
+    if (b->nbins < 1 || b->nbins > kMaxBins) return fail(CF_ERR_ARG, "nbins must be 1..%d", kMaxBins);
+    P->nbins = b->nbins;
+    const double kmax = b->kmax > 0.0 ? b->kmax : (double)(g.n[0] / 2);
+    const double kmin = b->kmin;
+    for (int i = 0; i <= b->nbins; ++i) {
+        if (b->kind == CF_BINS_LINEAR)
+            P->edges.e[i] = kmin + (double)i * ((kmax - kmin) / (double)b->nbins);
+        else if (b->kind == CF_BINS_LOG) {
+            if (!(kmin > 0.0)) return fail(CF_ERR_ARG, "log bins need kmin > 0");
+            P->edges.e[i] = kmin * exp((double)i * (log(kmax / kmin) / (double)b->nbins));
+        } else if (b->kind == CF_BINS_EDGES) {
+            if (!b->edges) return fail(CF_ERR_ARG, "CF_BINS_EDGES needs edges");
+            P->edges.e[i] = b->edges[i];
+        } else
+            return fail(CF_ERR_ARG, "unknown bins kind %d", b->kind);
+        if (i > 0 && !(P->edges.e[i] > P->edges.e[i - 1])) return fail(CF_ERR_ARG, "bin edges must increase");
+    }
+    P->k2max = 0;
+    for (int a = 0; a < g.ndim; ++a) P->k2max += (g.n[a] / 2) * (g.n[a] / 2);
+    const long long nl = g.n[g.ndim - 1];
+    P->H = nl / 2 + 1;
+    P->rows = g.ncell / nl;
+    P->elem = elem;
+    const size_t per_field = elem * (size_t)P->rows * (size_t)P->H;
+    long long chunk = (long long)((48ull << 20) / (per_field ? per_field : 1));
+    if (chunk < 2) chunk = 2;
+    chunk &= ~1ll;
+    if (chunk > 65534) chunk = 65534;
+    const long long nf_even = (nfields + 1) & ~1ll;
+    if (chunk > nf_even) chunk = nf_even < 2 ? 2 : nf_even;
+    P->chunk = chunk;
+    size_t o = 0;
+    P->off_bin = o;
+    o = align256(o + sizeof(int) * (size_t)(P->k2max + 1));
+    P->off_nmodes = o;
+    o = align256(o + sizeof(unsigned long long) * P->nbins);
+    P->off_acc = o;
+    o = align256(o + sizeof(double) * (size_t)nfields * P->nbins);
+    P->off_nhat = o;
+    o = align256(o + sizeof(double) * (size_t)nfields);
+    P->off_fsum = o;
+    o = align256(o + sizeof(double));
+    P->off_ntot = o;
+    o = align256(o + sizeof(unsigned long long) * (size_t)nfields);
+    P->off_half = o;
+    o = align256(o + per_field * (size_t)chunk);
+    P->off_half2 = o;  // unused (3D passes run in place)
+    P->total = o;
+    return CF_OK;
+}
+
+template <typename T, int L>
+static cf_status launch_pk_rows(const void* fields, int kind, const float* f, const double* nhat, const PkPlan& P,
+                                long long nfields, long long f0, long long nchunk, C2<T>* out, cudaStream_t s) {
+    using Cfg = PkRowsCfg<T, L>;
+    auto kern = k_pk_rows<T, L>;
+    CF_TRY(prepare_smem(kern, Cfg::SMEM));
+    dim3 grid((unsigned)((P.rows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)((nchunk + 1) / 2));
+    ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_rows_f32" : "pk_rows_f64", L);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(fields, kind, f, nhat, P.rows, P.g.ncell, nfields, f0, out,
+                                               twiddles<T>());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+template <typename T, int L>
+static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mid, const PkPlan& P, const int* bin_of,
+                                double* acc, long long f0, long long nchunk, cudaStream_t s) {
+    using Cfg = ColsCfg<T, L>;
+    auto kern = k_pk_cols<T, L>;
+    const size_t smem = Cfg::SMEM + sizeof(T) * (size_t)P.nbins;
+    CF_TRY(prepare_smem(kern, smem));
+    dim3 grid((unsigned)((inner + Cfg::C - 1) / Cfg::C), (unsigned)nchunk);
+    ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_cols_f32" : "pk_cols_f64", L);
+    kern<<<grid, Cfg::THREADS, smem, s>>>(in, inner, P.H, n_mid, P.g.n[P.g.ndim - 1], bin_of, P.k2max, P.nbins, acc,
+                                          f0, twiddles<T>());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+template <typename T>
+static cf_status pk_impl(const void* fields, int kind, const float* f, const PkPlan& P, long long nfields,
+                         double* pk_out, int64_t* nmodes_out, double* mean, double* cov, char* ws, cudaStream_t s) {
+    const GridInfo& g = P.g;
+    int* bin_of = (int*)(ws + P.off_bin);
+    unsigned long long* nmodes = (unsigned long long*)(ws + P.off_nmodes);
+    double* acc = (double*)(ws + P.off_acc);
+    double* nhat = (double*)(ws + P.off_nhat);
+    double* fsum = (double*)(ws + P.off_fsum);
+    unsigned long long* ntot = (unsigned long long*)(ws + P.off_ntot);
+    C2<T>* half = (C2<T>*)(ws + P.off_half);
+    {
+    ScopedKernelTimer kt(s, "pk_setup");
+    k_pk_bintable<<<grid_blocks(P.k2max + 1, 256, 1024), 256, 0, s>>>(P.edges, P.nbins, P.k2max, bin_of);
+    CF_CUDA(cudaMemsetAsync(nmodes, 0, sizeof(unsigned long long) * P.nbins, s));
+    CF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nfields * P.nbins, s));
+    k_pk_nmodes<<<grid_blocks(g.ncell, 256, 1024), 256, 0, s>>>(g, bin_of, P.k2max, nmodes);
+    }
+    CF_CHECK_LAUNCH();
+    if (kind == PK_COUNTS) {
+        CF_CUDA(cudaMemsetAsync(ntot, 0, sizeof(unsigned long long) * (size_t)nfields, s));
+        CF_CUDA(cudaMemsetAsync(fsum, 0, sizeof(double), s));
+        dim3 grid((unsigned)grid_blocks(g.ncell, 256, 64), (unsigned)nfields);
+        ScopedKernelTimer kt(s, "pk_count_totals");
+        k_count_totals<<<grid, 256, 0, s>>>((const int32_t*)fields, g.ncell, f, ntot, fsum);
+        k_nhat<<<(unsigned)((nfields + 255) / 256), 256, 0, s>>>(ntot, fsum, (int)nfields, nhat);
+        CF_CHECK_LAUNCH();
+    }
+    const int d = g.ndim;
+    const long long nl = g.n[d - 1];
+    for (long long f0 = 0; f0 < nfields; f0 += P.chunk) {
+        const long long nc = (nfields - f0) < P.chunk ? (nfields - f0) : P.chunk;
+        CF_TRY(dispatch_line(nl, [&](auto Lc) -> cf_status {
+            return launch_pk_rows<T, decltype(Lc)::value>(fields, kind, f, nhat, P, nfields, f0, nc, half, s);
+        }));
+        if (d == 3) {
+            FieldEpi<T> none{};
+            CF_TRY((launch_cols<T, -1, 0>(g.n[1], half, nc * g.n[0], P.H, half, 0, none, s)));
+        }
+        const long long inner = (d == 3 ? g.n[1] : 1) * P.H;
+        const long long n_mid = d == 3 ? g.n[1] : 1;
+        CF_TRY(dispatch_line(g.n[0], [&](auto Lc) -> cf_status {
+            return launch_pk_cols<T, decltype(Lc)::value>(half, inner, n_mid, P, bin_of, acc, f0, nc, s);
+        }));
+    }
+    double volfac = 1.0;
+    for (int a = 0; a < d; ++a) volfac *= g.cell[a] / (double)g.n[a];
+    ScopedKernelTimer kt(s, "pk_finalize");
+    k_pk_finalize<<<grid_blocks(nfields * P.nbins, 256, 1024), 256, 0, s>>>(acc, nmodes, nfields, P.nbins, volfac,
+                                                                            pk_out, nmodes_out);
+    if (mean || cov) {
+        double* mu = mean ? mean : acc;  // acc is free after finalize when mean is not wanted
+        k_pk_mean<<<(P.nbins + 127) / 128, 128, 0, s>>>(pk_out, nfields, P.nbins, mu);
+        if (cov) k_pk_cov<<<P.nbins, 128, 0, s>>>(pk_out, mu, nfields, P.nbins, cov);
+    }
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+extern "C" cf_status cf_power_spectrum_workspace_size(const cf_grid* g, int64_t nfields, const cf_bins* b, cf_dtype dt,
+                                                      size_t* bytes) {
+    clear_error();
+    if (!bytes) return fail(CF_ERR_ARG, "bytes is NULL");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
+    PkPlan P;
+    CF_TRY(make_plan(g, nfields, b, dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>), &P));
+    *bytes = P.total;
+    return CF_OK;
+}
+
+static cf_status pk_common(const void* fields, int kind, cf_dtype dt, const float* f, const cf_grid* g, int64_t nfields,
+                           const cf_bins* bins, double* pk_out, int64_t* nmodes_out, double* mean, double* cov,
+                           void* ws, size_t ws_bytes, cf_stream_t s) {
+    clear_error();
+    if (!fields || !pk_out) return fail(CF_ERR_ARG, "fields and pk_out are required");
+    if (nfields < 1) return fail(CF_ERR_ARG, "nfields must be >= 1");
+    if (nfields > 65535) return fail(CF_ERR_UNSUPPORTED, "at most 65535 fields per call");
+    const size_t elem = dt == CF_F64 ? sizeof(C2<double>) : sizeof(C2<float>);
+    PkPlan P;
+    CF_TRY(make_plan(g, nfields, bins, elem, &P));
+    if (!ws || ws_bytes < P.total) return fail(CF_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, P.total);
+    CF_TRY(ensure_device_init());
+    if (dt == CF_F64)
+        return pk_impl<double>(fields, kind, f, P, nfields, pk_out, nmodes_out, mean, cov, (char*)ws, (cudaStream_t)s);
+    return pk_impl<float>(fields, kind, f, P, nfields, pk_out, nmodes_out, mean, cov, (char*)ws, (cudaStream_t)s);
+}
+
+extern "C" cf_status cf_power_spectrum(const void* fields, cf_dtype dt, const cf_grid* g, int64_t nfields,
+                                       const cf_bins* bins, double* pk_out, int64_t* nmodes_out, double* mean_or_null,
+                                       double* cov_or_null, void* ws, size_t ws_bytes, cf_stream_t s) {
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
+    return pk_common(fields, dt == CF_F32 ? PK_FLOAT : PK_DOUBLE, dt, nullptr, g, nfields, bins, pk_out, nmodes_out,
+                     mean_or_null, cov_or_null, ws, ws_bytes, s);
+}
+
+extern "C" cf_status cf_power_spectrum_counts(const int32_t* counts, const float* f_or_null, const cf_grid* g,
+                                              int64_t nfields, const cf_bins* bins, double* pk_out,
+                                              int64_t* nmodes_out, double* mean_or_null, double* cov_or_null,
+                                              void* ws, size_t ws_bytes, cf_stream_t s) {
+    return pk_common(counts, PK_COUNTS, CF_F32, f_or_null, g, nfields, bins, pk_out, nmodes_out, mean_or_null,
+                     cov_or_null, ws, ws_bytes, s);
+}

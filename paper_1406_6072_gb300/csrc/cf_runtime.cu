@@ -1,0 +1,256 @@
+// cf_runtime.cu -- error state, per-device set-up (twiddle tables), grid
+// validation and embedding accessors.
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "cf_fft.cuh"
+#include "cf_internal.h"
+
+namespace cf {
+
+static thread_local std::string g_last_error;
+
+cf_status fail(cf_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+// Twiddle tables, one copy per device that loads the library.
+__device__ C2<float> g_tw32[TWN];
+__device__ C2<double> g_tw64[TWN];
+
+__global__ void k_init_twiddles(C2<float>* tw32, C2<double>* tw64) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= TWN) return;
+    double s, c;
+    sincospi(2.0 * (double)j / (double)TWN, &s, &c);
+    tw64[j] = mk(c, s);
+    tw32[j] = mk((float)c, (float)s);
+}
+
+static constexpr int kMaxDevices = 64;
+static std::mutex g_init_mu;
+static bool g_inited[kMaxDevices];
+static C2<float>* g_tw32_ptr[kMaxDevices];
+static C2<double>* g_tw64_ptr[kMaxDevices];
+
+static int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+cf_status ensure_device_init() {
+    int dev = 0;
+    CF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(CF_ERR_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (g_inited[dev]) return CF_OK;
+    void* p32 = nullptr;
+    void* p64 = nullptr;
+    CF_CUDA(cudaGetSymbolAddress(&p32, g_tw32));
+    CF_CUDA(cudaGetSymbolAddress(&p64, g_tw64));
+    k_init_twiddles<<<(TWN + 255) / 256, 256>>>((C2<float>*)p32, (C2<double>*)p64);
+    CF_CHECK_LAUNCH();
+    CF_CUDA(cudaDeviceSynchronize());
+    g_tw32_ptr[dev] = (C2<float>*)p32;
+    g_tw64_ptr[dev] = (C2<double>*)p64;
+    g_inited[dev] = true;
+    return CF_OK;
+}
+
+const C2<float>* twiddles_f32() { return g_tw32_ptr[current_device()]; }
+const C2<double>* twiddles_f64() { return g_tw64_ptr[current_device()]; }
+
+cf_status check_grid(const cf_grid* g, GridInfo* gi) {
+    if (!g) return fail(CF_ERR_ARG, "grid is NULL");
+    if (g->ndim < 1 || g->ndim > 3) return fail(CF_ERR_ARG, "ndim must be 1, 2 or 3 (got %d)", g->ndim);
+    gi->ndim = g->ndim;
+    gi->ncell = 1;
+    gi->mtotal = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (a < g->ndim) {
+            const long long n = (long long)g->n[a];
+            if (n < 1) return fail(CF_ERR_ARG, "n[%d] = %lld must be >= 1", a, n);
+            const long long m = 2 * n;
+            if (!is_pow2(m) || m > kMaxLine)
+                return fail(CF_ERR_UNSUPPORTED, "embedding size 2*n[%d] = %lld must be a power of two <= %lld",
+                            a, m, kMaxLine);
+            const double c = g->cell[a];
+            if (!(c > 0.0)) return fail(CF_ERR_ARG, "cell[%d] must be > 0", a);
+            gi->n[a] = n;
+            gi->m[a] = m;
+            gi->cell[a] = c;
+            gi->ncell *= n;
+            gi->mtotal *= m;
+        } else {
+            gi->n[a] = 1;
+            gi->m[a] = 1;
+            gi->cell[a] = 1.0;
+        }
+    }
+    return CF_OK;
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+extern "C" const char* cf_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* cf_version(void) { return "cf 0.1 (sm_103a)"; }
+
+extern "C" cf_status cf_embedding_free(cf_embedding* e) {
+    if (!e) return CF_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(e->device);
+    cudaFree(e->lambda);
+    cudaFree(e->s64);
+    cudaFree(e->s32);
+    cudaSetDevice(prev);
+    delete e;
+    return CF_OK;
+}
+
+extern "C" cf_status cf_embedding_lambda(const cf_embedding* e, double* dst, cf_stream_t s) {
+    if (!e || !dst) return fail(CF_ERR_ARG, "NULL argument");
+    CF_CUDA(cudaMemcpyAsync(dst, e->lambda, sizeof(double) * (size_t)e->grid.mtotal,
+                            cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+    return CF_OK;
+}
+
+__global__ void k_sqrt_lambda_plus(const double* __restrict__ lam, double tau, double* __restrict__ dst,
+                                   long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        dst[i] = l > tau ? sqrt(l) : 0.0;
+    }
+}
+
+extern "C" cf_status cf_embedding_sqrt_lambda(const cf_embedding* e, double* dst, cf_stream_t s) {
+    if (!e || !dst) return fail(CF_ERR_ARG, "NULL argument");
+    const long long total = e->grid.mtotal;
+    const int blocks = (int)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256);
+    k_sqrt_lambda_plus<<<blocks, 256, 0, (cudaStream_t)s>>>(e->lambda, e->tau, dst, total);
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+extern "C" cf_status cf_embedding_info(const cf_embedding* e, cf_grid* g, cf_embed_report* rep) {
+    if (!e) return fail(CF_ERR_ARG, "NULL embedding");
+    if (g) {
+        g->ndim = e->grid.ndim;
+        g->pad_ = 0;
+        for (int a = 0; a < 3; ++a) {
+            g->n[a] = e->grid.n[a];
+            g->cell[a] = e->grid.cell[a];
+        }
+    }
+    if (rep) *rep = e->report;
+    return CF_OK;
+}
+
+// ----------------------------------------------------------------- kernel timing
+#include <map>
+#include <vector>
+
+namespace cf {
+namespace {
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+std::map<std::string, std::pair<long long, double>> g_acc;
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+ScopedKernelTimer::ScopedKernelTimer(cudaStream_t s, const char* name, long long variant) : s_(s) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (!g_timing) return;
+    if (variant >= 0)
+        snprintf(name_, sizeof name_, "%s<%lld>", name, variant);
+    else
+        snprintf(name_, sizeof name_, "%s", name);
+    a_ = take_event();
+    b_ = take_event();
+    cudaEventRecord(a_, s_);
+}
+
+ScopedKernelTimer::~ScopedKernelTimer() {
+    if (!a_) return;
+    cudaEventRecord(b_, s_);
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_pending.push_back({name_, a_, b_});
+}
+
+static void drain_pending() {
+    for (auto& p : g_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        auto& acc = g_acc[p.name];
+        acc.first += 1;
+        acc.second += ms;
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+}  // namespace cf
+
+extern "C" cf_status cf_kernel_timing(int32_t enable) {
+    std::lock_guard<std::mutex> lk(cf::g_tmu);
+    cf::drain_pending();
+    if (enable) cf::g_acc.clear();
+    cf::g_timing = enable != 0;
+    return CF_OK;
+}
+
+extern "C" cf_status cf_kernel_timing_read(char* json, size_t cap, size_t* needed) {
+    std::lock_guard<std::mutex> lk(cf::g_tmu);
+    cf::drain_pending();
+    std::string out = "{";
+    bool first = true;
+    for (auto& kv : cf::g_acc) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
+                 kv.second.second);
+        out += buf;
+        first = false;
+    }
+    out += "}";
+    if (needed) *needed = out.size() + 1;
+    if (json && cap > 0) {
+        size_t n = out.size() < cap - 1 ? out.size() : cap - 1;
+        memcpy(json, out.data(), n);
+        json[n] = 0;
+    }
+    return CF_OK;
+}

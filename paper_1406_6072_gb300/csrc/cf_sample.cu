@@ -1,0 +1,261 @@
+// cf_sample.cu -- steps b1-b4 (and c1-c2 fused): per-realization exact
+// Gaussian fields by the pruned inverse transform of scaled complex noise
+// (section 2, eq. (Papos2) and the closing paragraph), plus the stand-alone
+// noise draw.
+#include "cf_kernels.cuh"
+
+#include <stdlib.h>
+
+namespace cf {
+
+// --------------------------------------------------------------------------
+// Pass 1: rows along the last axis.  Each thread draws the noise of its E
+// first-stage points (Philox stream 0), scales it by sqrt(lambda+)/sqrt(M^d),
+// runs the inverse line transform, and keeps the first L/2 outputs (the
+// survey half).  Output: complex intermediate [chunk][nrows][L/2], or for a
+// one-dimensional grid the fields (and counts) directly.
+// --------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS)
+    k_sample_rows(const T* __restrict__ s, T amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
+                  long long nrows, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
+                  const C2<T>* __restrict__ tw) {
+    using Cfg = RowsCfg<T, L>;
+    using G = typename Cfg::G;
+    constexpr int E = G::E;
+    constexpr int STEP = L / E;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
+    const int line = threadIdx.x / G::TL;
+    const int j = threadIdx.x % G::TL;
+    const long long row = (long long)blockIdx.x * Cfg::ROWS + line;
+    const int rl = blockIdx.y;
+    const uint32_t r = r0 + (uint32_t)rl;
+    const bool valid = row < nrows;
+    const long long rw = valid ? row : 0;
+    const T* srow = s + (size_t)rw * L;
+    C2<T> v[E];
+    if constexpr (sizeof(T) == 4) {
+        // binary32: columns c and c + L/2 share one Philox call (pair index
+        // row*L/2 + c); first-stage points j + q*STEP and j + (q + E/2)*STEP
+        // are exactly such a pair.
+#pragma unroll
+        for (int q = 0; q < E / 2; ++q) {
+            const int col = j + q * STEP;
+            C2<float> lo, hi;
+            noise_pair_f32((unsigned long long)rw * (L / 2) + col, r, key0, key1, lo, hi);
+            v[q] = cscale(lo, srow[col] * amp_scale);
+            v[q + E / 2] = cscale(hi, srow[col + L / 2] * amp_scale);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int col = j + q * STEP;
+            const C2<double> e = noise_f64((unsigned long long)rw * L + col, r, key0, key1);
+            v[q] = cscale(e, srow[col] * amp_scale);
+        }
+    }
+    auto sink = [&](int, int p, C2<T> val) {
+        if (!valid) return;
+        if (mode == 0)
+            out[((size_t)rl * nrows + row) * (L / 2) + p] = val;
+        else
+            epi(rl, (long long)row * (L / 2) + p, val);
+    };
+    line_fft<T, L, +1, L / 2>(sm, RowLayout<E, G::PADDED>(), line, j, v, tw, sink);
+}
+
+template <typename T>
+static cf_status launch_sample_rows(long long L, const T* s, T amp_scale, uint64_t seed, uint32_t r0,
+                                    int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
+                                    cudaStream_t st) {
+    return dispatch_line(L, [&](auto Lc) -> cf_status {
+        constexpr int LL = decltype(Lc)::value;
+        using Cfg = RowsCfg<T, LL>;
+        auto kern = k_sample_rows<T, LL>;
+        CF_TRY(prepare_smem(kern, Cfg::SMEM));
+        dim3 grid((unsigned)((nrows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)chunk);
+        ScopedKernelTimer kt(st, sizeof(T) == 4 ? "sample_rows_f32" : "sample_rows_f64", LL);
+        kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
+                                                     nrows, out, mode, epi, twiddles<T>());
+        CF_CHECK_LAUNCH();
+        return CF_OK;
+    });
+}
+
+// Intermediate bytes of one realization.
+static size_t per_realization_bytes(const GridInfo& g, size_t elem) {
+    if (g.ndim == 1) return 0;
+    if (g.ndim == 2) return elem * (size_t)g.m[0] * (size_t)g.n[1];
+    return elem * ((size_t)g.m[0] * g.m[1] * g.n[2] + (size_t)g.m[0] * g.n[1] * g.n[2]);
+}
+
+// Target bytes of one chunk's intermediates (kept L2-resident between passes).
+static size_t chunk_target_bytes() {
+    static size_t v = [] {
+        const char* e = getenv("CF_CHUNK_MB");
+        long mb = e ? atol(e) : 48;
+        if (mb < 1) mb = 1;
+        return (size_t)mb << 20;
+    }();
+    return v;
+}
+
+static int pick_chunk(const GridInfo& g, size_t elem, int R, size_t ws_bytes) {
+    const size_t per = per_realization_bytes(g, elem);
+    if (per == 0) return R < 65535 ? R : 65535;  // grid.y bound
+    size_t c = chunk_target_bytes() / per;
+    if (c < 1) c = 1;
+    if (c > (size_t)R) c = (size_t)R;
+    if (c > 65535) c = 65535;
+    const size_t by_ws = ws_bytes / per;
+    if (c > by_ws) c = by_ws;
+    return (int)c;
+}
+
+template <typename T>
+static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, int R, void* fields,
+                             const cf_lp_params* lp, void* ws, size_t ws_bytes, double amp_scale,
+                             cudaStream_t st) {
+    const GridInfo& g = e->grid;
+    const size_t elem = sizeof(C2<T>);
+    const int chunk = pick_chunk(g, elem, R, ws_bytes);
+    if (chunk < 1) return fail(CF_ERR_NOMEM, "workspace of %zu bytes holds no realization (%zu needed)", ws_bytes,
+                               per_realization_bytes(g, elem));
+    const T* s = sizeof(T) == 4 ? (const T*)(const void*)e->s32 : (const T*)(const void*)e->s64;
+    const long long cells = g.ncell;
+    const int d = g.ndim;
+    C2<T>* buf1 = (C2<T>*)ws;
+    C2<T>* buf2 = nullptr;
+    if (d == 3) buf2 = buf1 + (size_t)chunk * g.m[0] * g.m[1] * g.n[2];
+    for (int c0 = 0; c0 < R; c0 += chunk) {
+        const int nr = (R - c0) < chunk ? (R - c0) : chunk;
+        FieldEpi<T> epi{};
+        epi.fields = fields ? (T*)fields + (size_t)c0 * 2 * cells : nullptr;
+        epi.cells = cells;
+        epi.r0 = (uint32_t)(r0 + (uint64_t)c0);
+        if (lp) {
+            epi.counts = lp->counts_out + (size_t)c0 * 2 * cells;
+            epi.delta = lp->delta_out ? lp->delta_out + (size_t)c0 * 2 * cells : nullptr;
+            epi.f = lp->f;
+            epi.half_sigma2 = 0.5 * lp->sigma2;
+            epi.half_sigma2_f = (float)(0.5 * lp->sigma2);
+            epi.nbar = lp->nbar;
+            epi.pkey0 = (uint32_t)lp->seed;
+            epi.pkey1 = (uint32_t)(lp->seed >> 32);
+        }
+        const uint32_t rr0 = (uint32_t)(r0 + (uint64_t)c0);
+        const long long Ml = g.m[d - 1];
+        const long long nrows = g.mtotal / Ml;
+        if (d == 1) {
+            CF_TRY(launch_sample_rows<T>(Ml, s, (T)amp_scale, seed, rr0, nr, nrows, nullptr, 1, epi, st));
+        } else if (d == 2) {
+            CF_TRY(launch_sample_rows<T>(Ml, s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
+            // pass 2: columns of [chunk][M0][N1], keep N0, fields epilogue
+            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st)));
+        } else {
+            CF_TRY(launch_sample_rows<T>(Ml, s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
+            // pass 2: axis 1 of [chunk*M0][M1][N2] -> [chunk*M0][N1][N2]
+            CF_TRY((launch_cols<T, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st)));
+            // pass 3: axis 0 of [chunk][M0][N1*N2] -> fields
+            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st)));
+        }
+    }
+    return CF_OK;
+}
+
+static cf_status check_sample_args(const cf_embedding* e, uint64_t r0, int32_t R, cf_dtype dt) {
+    if (!e) return fail(CF_ERR_ARG, "embedding is NULL");
+    if (R < 0) return fail(CF_ERR_ARG, "R must be >= 0");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
+    return CF_OK;
+}
+
+// ----------------------------------------------------------------- noise draw
+__global__ void k_noise_f32(uint32_t key0, uint32_t key1, uint32_t r0, long long ncells, long long m_last,
+                            C2<float>* __restrict__ out) {
+    const long long half = m_last / 2;
+    const long long npairs = ncells / 2;
+    const uint32_t r = r0 + blockIdx.y;
+    C2<float>* o = out + (size_t)blockIdx.y * ncells;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npairs;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long row = p / half, c = p % half;
+        C2<float> lo, hi;
+        noise_pair_f32((unsigned long long)p, r, key0, key1, lo, hi);
+        o[row * m_last + c] = lo;
+        o[row * m_last + c + half] = hi;
+    }
+}
+
+__global__ void k_noise_f64(uint32_t key0, uint32_t key1, uint32_t r0, long long ncells, C2<double>* __restrict__ out) {
+    const uint32_t r = r0 + blockIdx.y;
+    C2<double>* o = out + (size_t)blockIdx.y * ncells;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells;
+         k += (long long)gridDim.x * blockDim.x)
+        o[k] = noise_f64((unsigned long long)k, r, key0, key1);
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+extern "C" cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, cf_dtype dt, size_t* bytes) {
+    clear_error();
+    if (!e || !bytes) return fail(CF_ERR_ARG, "NULL argument");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    const size_t elem = dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>);
+    const size_t per = per_realization_bytes(e->grid, elem);
+    int chunk = pick_chunk(e->grid, elem, R < 1 ? 1 : R, (size_t)-1);
+    *bytes = per * (size_t)(chunk < 1 ? 1 : chunk);
+    return CF_OK;
+}
+
+extern "C" cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, cf_dtype dt,
+                               void* fields_out, void* ws, size_t ws_bytes, cf_stream_t s) {
+    clear_error();
+    CF_TRY(check_sample_args(e, r0, R, dt));
+    if (!fields_out) return fail(CF_ERR_ARG, "fields_out is NULL");
+    if (R == 0) return CF_OK;
+    CF_TRY(ensure_device_init());
+    if (dt == CF_F32) return sample_impl<float>(e, seed, r0, R, fields_out, nullptr, ws, ws_bytes, 1.0, (cudaStream_t)s);
+    return sample_impl<double>(e, seed, r0, R, fields_out, nullptr, ws, ws_bytes, 1.0, (cudaStream_t)s);
+}
+
+extern "C" cf_status cf_sample_lp(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, cf_dtype dt,
+                                  void* fields_out, const cf_lp_params* lp, void* ws, size_t ws_bytes,
+                                  cf_stream_t s) {
+    clear_error();
+    CF_TRY(check_sample_args(e, r0, R, dt));
+    if (dt != CF_F32) return fail(CF_ERR_UNSUPPORTED, "the fused lognormal/Poisson epilogue is binary32 only");
+    if (!lp || !lp->counts_out) return fail(CF_ERR_ARG, "lp and lp->counts_out are required");
+    if (!(lp->nbar >= 0.0)) return fail(CF_ERR_ARG, "nbar must be >= 0");
+    if (R == 0) return CF_OK;
+    CF_TRY(ensure_device_init());
+    return sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, (cudaStream_t)s);
+}
+
+extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_t ncells, int64_t m_last,
+                                   cf_dtype dt, void* out, cf_stream_t s) {
+    clear_error();
+    if (!out) return fail(CF_ERR_ARG, "out is NULL");
+    if (R < 0 || ncells < 0) return fail(CF_ERR_ARG, "negative size");
+    if (R > 65535) return fail(CF_ERR_UNSUPPORTED, "at most 65535 realizations per call");
+    if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
+    if (R == 0 || ncells == 0) return CF_OK;
+    const dim3 grid((unsigned)grid_blocks(dt == CF_F32 ? ncells / 2 : ncells, 256, 2048), (unsigned)R);
+    ScopedKernelTimer kt((cudaStream_t)s, dt == CF_F32 ? "noise_f32" : "noise_f64");
+    if (dt == CF_F32) {
+        if (m_last < 2 || (m_last & 1) || ncells % m_last) return fail(CF_ERR_ARG, "m_last must be even and divide ncells");
+        k_noise_f32<<<grid, 256, 0, (cudaStream_t)s>>>((uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)r0, ncells,
+                                                      m_last, (C2<float>*)out);
+    } else if (dt == CF_F64) {
+        k_noise_f64<<<grid, 256, 0, (cudaStream_t)s>>>((uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)r0, ncells,
+                                                      (C2<double>*)out);
+    } else {
+        return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    }
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}

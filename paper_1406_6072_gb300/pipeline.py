@@ -1,0 +1,91 @@
+"""One pass of the whole hot path over a workload, through the C ABI.
+
+A step is: embed (a1-a3) -> sample with the fused lognormal/Poisson epilogue
+(b1-b4, c1-c2) -> power spectra of the Gaussian fields and of the count maps
+with mean and covariance (d1).  Device buffers are allocated once with torch;
+every computation is a call into libcf.so on one stream.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import cf
+from .workloads import Workload
+
+
+class FieldPipeline:
+    def __init__(self, wl: Workload, device="cuda:0", stream=None, R=None, with_pk=True):
+        self.wl = wl
+        self.dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        self.R = wl.R if R is None else R
+        self.dtype = cf.CF_F32 if wl.dtype == "f32" else cf.CF_F64
+        self.tdtype = torch.float32 if wl.dtype == "f32" else torch.float64
+        self.grid = cf.make_grid(wl.n, wl.cell[: wl.ndim])
+        self.xi = cf.make_xi(wl.xi_kind, wl.amp, wl.scale, wl.beta)
+        self.flags = cf.CF_EMBED_CLAMP if wl.clamp else 0
+        self.with_lp = wl.nbar is not None and self.dtype == cf.CF_F32
+        self.with_pk = with_pk and wl.nbins is not None
+        F = 2 * self.R
+        shape = (self.R, 2) + tuple(wl.n)
+        self.fields = torch.empty(shape, dtype=self.tdtype, device=self.dev)
+        self.counts = torch.empty(shape, dtype=torch.int32, device=self.dev) if self.with_lp else None
+        self.emb = None
+        self.ws = None
+        self.ws_bytes = 0
+        if self.with_pk:
+            self.bins = cf.make_bins(wl.nbins)
+            self.pk_ws_bytes = cf.cf_power_spectrum_workspace_size(self.grid, F, self.bins, self.dtype)
+            self.pk_ws = torch.empty(self.pk_ws_bytes, dtype=torch.uint8, device=self.dev)
+            self.pk = torch.empty((F, wl.nbins), dtype=torch.float64, device=self.dev)
+            self.nmodes = torch.empty(wl.nbins, dtype=torch.int64, device=self.dev)
+            self.mean = torch.empty(wl.nbins, dtype=torch.float64, device=self.dev)
+            self.cov = torch.empty((wl.nbins, wl.nbins), dtype=torch.float64, device=self.dev)
+            if self.with_lp:
+                self.pkg = torch.empty_like(self.pk)
+                self.meang = torch.empty_like(self.mean)
+                self.covg = torch.empty_like(self.cov)
+
+    def embed(self, xi=None):
+        if self.emb is not None:
+            self.emb.close()
+        self.emb = cf.cf_embed(self.grid, xi or self.xi, self.flags, self.stream)
+        need = cf.cf_sample_workspace_size(self.emb, self.R, self.dtype)
+        if self.ws is None or need > self.ws_bytes:
+            self.ws_bytes = need
+            self.ws = torch.empty(max(need, 1), dtype=torch.uint8, device=self.dev)
+        return self.emb.report
+
+    def sample(self, r0=0):
+        wl = self.wl
+        if self.with_lp:
+            lp = cf.make_lp(wl.sigma2, wl.nbar, self.counts, wl.seed + 1000)
+            cf.cf_sample_lp(self.emb, wl.seed, r0, self.R, self.dtype, self.fields, lp, self.ws, self.ws_bytes,
+                            self.stream)
+        else:
+            cf.cf_sample(self.emb, wl.seed, r0, self.R, self.dtype, self.fields, self.ws, self.ws_bytes, self.stream)
+
+    def spectra(self):
+        if not self.with_pk:
+            return
+        F = 2 * self.R
+        cf.cf_power_spectrum(self.fields, self.dtype, self.grid, F, self.bins, self.pk, self.nmodes, self.mean,
+                             self.cov, self.pk_ws, self.pk_ws_bytes, self.stream)
+        if self.with_lp:
+            cf.cf_power_spectrum_counts(self.counts, None, self.grid, F, self.bins, self.pkg, self.nmodes,
+                                        self.meang, self.covg, self.pk_ws, self.pk_ws_bytes, self.stream)
+
+    def step(self, r0=0):
+        """Embed + sample (+ lognormal/Poisson) + spectra for realizations [r0, r0+R)."""
+        self.embed()
+        self.sample(r0)
+        self.spectra()
+
+    @property
+    def cells_per_step(self):
+        return 2 * self.R * self.wl.cells_per_field
+
+    def close(self):
+        if self.emb is not None:
+            self.emb.close()
+            self.emb = None
