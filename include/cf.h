@@ -21,9 +21,12 @@
  *    are host memory.  The library owns cf_embedding and cf_server objects.
  *  - Asynchrony: work is enqueued on the caller's stream and returns without
  *    waiting, except cf_embed / cf_embed_from_lambda, which synchronise the
- *    stream once to fill the report.  The first call on a device performs a
- *    one-time set-up (twiddle tables) with a device synchronisation; make it
- *    before any stream capture.
+ *    stream to fill the report (once, or twice when the clamped covariance
+ *    error is computed), and cf_embedding_free, which waits for the device.
+ *    The first call on a device performs a one-time set-up (twiddle tables)
+ *    with a device synchronisation; make it before any stream capture.
+ *  - Device: calls run on the device of the stream passed (the legacy
+ *    default stream, NULL, means the calling thread's current device).
  *  - Layouts: row-major (C order).  Complex values are interleaved (re, im).
  *    Sampled fields are [R][2][n0][n1][n2]: field 2r is Re and 2r+1 is Im of
  *    realization r0 + r (two independent exact fields per complex draw).
@@ -139,6 +142,8 @@ CF_API cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags, cf_
 CF_API cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
                                cf_stream_t s, cf_embedding** out, cf_embed_report* rep);
 
+/* Frees an embedding.  Waits until the device is idle first, because work
+ * enqueued on any stream may still read sqrt(lambda). */
 CF_API cf_status cf_embedding_free(cf_embedding* e);
 
 /* Copies of the embedding's arrays into caller device memory (M^d doubles),

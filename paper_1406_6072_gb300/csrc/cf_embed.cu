@@ -241,9 +241,10 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
     e->grid = gi;
     CF_CUDA(cudaGetDevice(&e->device));
     auto cleanup = [&]() { cf_embedding_free(e); };
-    if (cudaMallocAsync((void**)&e->lambda, sizeof(double) * total, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&e->s64, sizeof(double) * total, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&e->s32, sizeof(float) * total, s) != cudaSuccess) {
+    // persistent arrays: plain allocations (freed with a device synchronisation)
+    if (cudaMalloc((void**)&e->lambda, sizeof(double) * total) != cudaSuccess ||
+        cudaMalloc((void**)&e->s64, sizeof(double) * total) != cudaSuccess ||
+        cudaMalloc((void**)&e->s32, sizeof(float) * total) != cudaSuccess) {
         cleanup();
         return fail(CF_ERR_NOMEM, "device allocation of the embedding (%lld cells) failed", total);
     }
@@ -333,7 +334,7 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
     if (xi->kind < CF_XI_GAUSSIAN || xi->kind > CF_XI_TABLE) return fail(CF_ERR_ARG, "unknown xi kind %d", xi->kind);
     if (xi->kind == CF_XI_TABLE && !xi->table) return fail(CF_ERR_ARG, "CF_XI_TABLE needs a table");
     if (xi->kind != CF_XI_TABLE && !(xi->scale > 0.0)) return fail(CF_ERR_ARG, "xi scale must be > 0");
-    CF_TRY(ensure_device_init());
+    CF_TRY(enter((cudaStream_t)stream));
     EmbedScratch sc;
     sc.s = (cudaStream_t)stream;
     CF_TRY(alloc_scratch(sc, gi.mtotal));
@@ -362,7 +363,7 @@ extern "C" cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda
     if (!lambda) return fail(CF_ERR_ARG, "lambda is NULL");
     GridInfo gi;
     CF_TRY(check_grid(g, &gi));
-    CF_TRY(ensure_device_init());
+    CF_TRY(enter((cudaStream_t)stream));
     EmbedScratch sc;
     sc.s = (cudaStream_t)stream;
     CF_TRY(alloc_scratch(sc, gi.mtotal));

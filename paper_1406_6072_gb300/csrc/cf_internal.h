@@ -23,9 +23,13 @@ void clear_error();
             return ::cf::fail(CF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// After a launch: reports launch errors; with CF_SYNC_CHECK=1 in the
+// environment also waits for the device and reports execution errors at the
+// launch that caused them (a debugging aid; off by default).
 #define CF_CHECK_LAUNCH()                                                                  \
     do {                                                                                   \
         cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ == cudaSuccess && ::cf::sync_check_enabled()) e_ = cudaDeviceSynchronize(); \
         if (e_ != cudaSuccess)                                                             \
             return ::cf::fail(CF_ERR_CUDA, "kernel launch failed at %s:%d: %s", __FILE__,  \
                               __LINE__, cudaGetErrorString(e_));                           \
@@ -37,9 +41,14 @@ void clear_error();
         if (st_ != CF_OK) return st_;      \
     } while (0)
 
+bool sync_check_enabled();
+
 // One-time per-device set-up (twiddle tables).  Synchronises the device the
 // first time it runs on a device.
 cf_status ensure_device_init();
+// Entry-point prologue: makes the device of stream s current (the legacy
+// default stream keeps the current device) and runs the one-time set-up.
+cf_status enter(cudaStream_t s);
 const C2<float>* twiddles_f32();   // current device, TWN entries exp(+2 pi i j/TWN)
 const C2<double>* twiddles_f64();
 

@@ -48,6 +48,7 @@ extern "C" cf_status cf_lognormal_poisson(const void* G, cf_dtype dt, int64_t ce
     if (((field0 + (uint64_t)nfields) >> 1) > 0xffffffffull) return fail(CF_ERR_ARG, "field index exceeds 33 bits");
     const long long total = (long long)cells_per_field * nfields;
     if (total == 0) return CF_OK;
+    CF_TRY(enter((cudaStream_t)s));
     const int blocks = grid_blocks(total, 256, 152 * 32);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     ScopedKernelTimer kt((cudaStream_t)s, dt == CF_F32 ? "lognormal_poisson_f32" : "lognormal_poisson_f64");

@@ -424,7 +424,7 @@ static cf_status pk_common(const void* fields, int kind, cf_dtype dt, const floa
     PkPlan P;
     CF_TRY(make_plan(g, nfields, bins, elem, &P));
     if (!ws || ws_bytes < P.total) return fail(CF_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, P.total);
-    CF_TRY(ensure_device_init());
+    CF_TRY(enter((cudaStream_t)s));
     if (dt == CF_F64)
         return pk_impl<double>(fields, kind, f, P, nfields, pk_out, nmodes_out, mean, cov, (char*)ws, (cudaStream_t)s);
     return pk_impl<float>(fields, kind, f, P, nfields, pk_out, nmodes_out, mean, cov, (char*)ws, (cudaStream_t)s);

@@ -1,6 +1,7 @@
 // cf_runtime.cu -- error state, per-device set-up (twiddle tables), grid
 // validation and embedding accessors.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -69,6 +70,26 @@ cf_status ensure_device_init() {
     return CF_OK;
 }
 
+bool sync_check_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("CF_SYNC_CHECK");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+cf_status enter(cudaStream_t s) {
+    if (s) {
+        int dev = -1;
+        cudaError_t e = cudaStreamGetDevice(s, &dev);
+        if (e != cudaSuccess) return fail(CF_ERR_CUDA, "cudaStreamGetDevice: %s", cudaGetErrorString(e));
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != dev) CF_CUDA(cudaSetDevice(dev));
+    }
+    return ensure_device_init();
+}
+
 const C2<float>* twiddles_f32() { return g_tw32_ptr[current_device()]; }
 const C2<double>* twiddles_f64() { return g_tw64_ptr[current_device()]; }
 
@@ -115,6 +136,8 @@ extern "C" cf_status cf_embedding_free(cf_embedding* e) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(e->device);
+    // enqueued work on any stream may still read the embedding
+    cudaDeviceSynchronize();
     cudaFree(e->lambda);
     cudaFree(e->s64);
     cudaFree(e->s32);

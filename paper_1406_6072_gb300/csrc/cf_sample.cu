@@ -218,7 +218,7 @@ extern "C" cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0
     CF_TRY(check_sample_args(e, r0, R, dt));
     if (!fields_out) return fail(CF_ERR_ARG, "fields_out is NULL");
     if (R == 0) return CF_OK;
-    CF_TRY(ensure_device_init());
+    CF_TRY(enter((cudaStream_t)s));
     if (dt == CF_F32) return sample_impl<float>(e, seed, r0, R, fields_out, nullptr, ws, ws_bytes, 1.0, (cudaStream_t)s);
     return sample_impl<double>(e, seed, r0, R, fields_out, nullptr, ws, ws_bytes, 1.0, (cudaStream_t)s);
 }
@@ -232,7 +232,7 @@ extern "C" cf_status cf_sample_lp(const cf_embedding* e, uint64_t seed, uint64_t
     if (!lp || !lp->counts_out) return fail(CF_ERR_ARG, "lp and lp->counts_out are required");
     if (!(lp->nbar >= 0.0)) return fail(CF_ERR_ARG, "nbar must be >= 0");
     if (R == 0) return CF_OK;
-    CF_TRY(ensure_device_init());
+    CF_TRY(enter((cudaStream_t)s));
     return sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, (cudaStream_t)s);
 }
 
@@ -244,6 +244,7 @@ extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_
     if (R > 65535) return fail(CF_ERR_UNSUPPORTED, "at most 65535 realizations per call");
     if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
     if (R == 0 || ncells == 0) return CF_OK;
+    CF_TRY(enter((cudaStream_t)s));
     const dim3 grid((unsigned)grid_blocks(dt == CF_F32 ? ncells / 2 : ncells, 256, 2048), (unsigned)R);
     ScopedKernelTimer kt((cudaStream_t)s, dt == CF_F32 ? "noise_f32" : "noise_f64");
     if (dt == CF_F32) {
