@@ -243,12 +243,14 @@ extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_
     if (R < 0 || ncells < 0) return fail(CF_ERR_ARG, "negative size");
     if (R > 65535) return fail(CF_ERR_UNSUPPORTED, "at most 65535 realizations per call");
     if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    if (dt == CF_F32 && (m_last < 2 || (m_last & 1) || ncells % m_last))
+        return fail(CF_ERR_ARG, "m_last must be even and divide ncells");
     if (R == 0 || ncells == 0) return CF_OK;
     CF_TRY(enter((cudaStream_t)s));
     const dim3 grid((unsigned)grid_blocks(dt == CF_F32 ? ncells / 2 : ncells, 256, 2048), (unsigned)R);
     ScopedKernelTimer kt((cudaStream_t)s, dt == CF_F32 ? "noise_f32" : "noise_f64");
     if (dt == CF_F32) {
-        if (m_last < 2 || (m_last & 1) || ncells % m_last) return fail(CF_ERR_ARG, "m_last must be even and divide ncells");
         k_noise_f32<<<grid, 256, 0, (cudaStream_t)s>>>((uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)r0, ncells,
                                                       m_last, (C2<float>*)out);
     } else if (dt == CF_F64) {
