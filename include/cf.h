@@ -22,7 +22,7 @@
  *  - Asynchrony: work is enqueued on the caller's stream and returns without
  *    waiting, except cf_embed / cf_embed_from_lambda, which synchronise the
  *    stream to fill the report (once, or twice when the clamped covariance
- *    error is computed), and cf_embedding_free, which waits for the device.
+ *    error is computed).
  *    The first call on a device performs a one-time set-up (twiddle tables)
  *    with a device synchronisation; make it before any stream capture.
  *  - Device: calls run on the device of the stream passed (the legacy
@@ -142,8 +142,9 @@ CF_API cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags, cf_
 CF_API cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
                                cf_stream_t s, cf_embedding** out, cf_embed_report* rep);
 
-/* Frees an embedding.  Waits until the device is idle first, because work
- * enqueued on any stream may still read sqrt(lambda). */
+/* Frees an embedding without waiting on the host: the memory is released on
+ * a library-owned stream after the last work that any library call enqueued
+ * on it (on any stream) has finished. */
 CF_API cf_status cf_embedding_free(cf_embedding* e);
 
 /* Copies of the embedding's arrays into caller device memory (M^d doubles),

@@ -32,13 +32,19 @@ def _newest_header():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, jobs: int | None = None, defines=(),
+          out: str | None = None, build_dir: str | None = None) -> str:
+    """Compiles csrc/ into LIB (or `out`); `defines` are extra -D macros
+    (build-time tunables such as CF_E32 or CF_ROWS_MINB) compiled into a
+    separate object directory."""
+    lib = out or LIB
+    bdir = build_dir or BUILD
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_time = _newest_header()
     objs, todo = [], []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
         if (not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_time)
                 or ptxas_info):
@@ -46,8 +52,8 @@ def build(verbose: bool = False, ptxas_info: bool = False, jobs: int | None = No
 
     def compile_one(item):
         src, obj = item
-        cmd = [_nvcc()] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + \
-            ["-c", src, "-o", obj]
+        cmd = [_nvcc()] + ARCH + NVCC_FLAGS + ["-D" + d for d in defines] + \
+            (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -59,14 +65,14 @@ def build(verbose: bool = False, ptxas_info: bool = False, jobs: int | None = No
             for src, err in ex.map(compile_one, todo):
                 if verbose or ptxas_info:
                     sys.stderr.write("== %s\n%s" % (os.path.basename(src), err))
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if todo or not os.path.exists(lib):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

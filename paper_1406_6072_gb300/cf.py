@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcf.so")
+# CF_LIBRARY may name another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("CF_LIBRARY") or os.path.join(_HERE, "libcf.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libcf.so is not built (run __graft_entry__.build() or "

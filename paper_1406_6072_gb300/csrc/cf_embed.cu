@@ -9,17 +9,20 @@ namespace cf {
 
 // a1: first row of the circulant, c(m) = xi(|lag(m)|), lag(m_i) = m_i for
 // m_i < n_i and m_i - M_i otherwise (the grid of eq. (grid) runs -n..n-1).
+// xi depends on |lag_i| only, so one thread evaluates xi once per point of
+// [0, n_0] x ... and writes it to the 2^d mirror positions m_i = l_i and
+// M_i - l_i (one position when l_i is 0 or n_i).
 __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, double beta,
                            double* __restrict__ c, C2<double>* __restrict__ z) {
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.mtotal;
-         idx += (long long)gridDim.x * blockDim.x) {
-        long long rem = idx;
+    const long long q0 = g.n[0] + 1, q1 = g.ndim > 1 ? g.n[1] + 1 : 1, q2 = g.ndim > 2 ? g.n[2] + 1 : 1;
+    const long long total = q0 * q1 * q2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long l2 = t % q2, l1 = (t / q2) % q1, l0 = t / (q1 * q2);
+        const long long l[3] = {l0, l1, l2};
         double r2 = 0.0;
-        for (int a = g.ndim - 1; a >= 0; --a) {
-            const long long m = rem % g.m[a];
-            rem /= g.m[a];
-            const long long lag = m < g.n[a] ? m : m - g.m[a];
-            const double x = (double)lag * g.cell[a];
+        for (int a = 0; a < g.ndim; ++a) {
+            const double x = (double)l[a] * g.cell[a];
             r2 += x * x;
         }
         double v;
@@ -29,8 +32,23 @@ __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, doubl
             v = amp * pow(1.0 + r2 / (scale * scale), -beta);
         else
             v = amp * exp(-sqrt(r2) / scale);
-        c[idx] = v;
-        z[idx] = mk(v, 0.0);
+        // mirror positions
+        const int na = g.ndim;
+        const int nm0 = (l0 == 0 || l0 == g.n[0]) ? 1 : 2;
+        const int nm1 = (na < 2 || l1 == 0 || l1 == g.n[1]) ? 1 : 2;
+        const int nm2 = (na < 3 || l2 == 0 || l2 == g.n[2]) ? 1 : 2;
+        for (int a0 = 0; a0 < nm0; ++a0) {
+            const long long m0 = a0 ? g.m[0] - l0 : l0;
+            for (int a1 = 0; a1 < nm1; ++a1) {
+                const long long m1 = a1 ? g.m[1] - l1 : l1;
+                for (int a2 = 0; a2 < nm2; ++a2) {
+                    const long long m2 = a2 ? g.m[2] - l2 : l2;
+                    const long long idx = (m0 * g.m[1] + m1) * g.m[2] + m2;
+                    c[idx] = v;
+                    z[idx] = mk(v, 0.0);
+                }
+            }
+        }
     }
 }
 
@@ -125,10 +143,12 @@ __global__ void __launch_bounds__(kRedThreads)
 
 // a3: lambda+ = lambda if lambda > tau; 0 if |lambda| <= tau (zeroed); 0 if
 // lambda < -tau (negative: counted, its |lambda| summed); s = sqrt(lambda+).
+// The binary32 amplitude sqrt(lambda+ / M^d) is formed in binary32 from the
+// exactly scaled binary64 value (M^d is a power of two); the binary64
+// amplitude is built only when a binary64 sampler needs it (k_s64).
 __global__ void __launch_bounds__(kRedThreads)
     k_threshold(const double* __restrict__ lam, long long total, const EmbedStats* __restrict__ st,
-                double norm, double* __restrict__ s64, float* __restrict__ s32,
-                double* __restrict__ lam_plus_or_null, double* __restrict__ part,
+                double inv_total, float* __restrict__ s32, double* __restrict__ part,
                 unsigned long long* __restrict__ counts) {
     __shared__ double sh[kRedThreads];
     const double tau = st->tau;
@@ -148,10 +168,7 @@ __global__ void __launch_bounds__(kRedThreads)
             ++nneg;
             neg += -l;
         }
-        const double sv = sqrt(lp) * norm;
-        s64[i] = sv;
-        s32[i] = (float)sv;
-        if (lam_plus_or_null) lam_plus_or_null[i] = lp;
+        s32[i] = sqrtf((float)(lp * inv_total));
     }
     neg = block_sum(neg, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = neg;
@@ -240,23 +257,25 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
     cf_embedding* e = new cf_embedding();
     e->grid = gi;
     CF_CUDA(cudaGetDevice(&e->device));
+    e->alloc_stream = s;
     auto cleanup = [&]() { cf_embedding_free(e); };
-    // persistent arrays: plain allocations (freed with a device synchronisation)
-    if (cudaMalloc((void**)&e->lambda, sizeof(double) * total) != cudaSuccess ||
-        cudaMalloc((void**)&e->s64, sizeof(double) * total) != cudaSuccess ||
-        cudaMalloc((void**)&e->s32, sizeof(float) * total) != cudaSuccess) {
+    // persistent arrays: stream-ordered allocations, released after their last use
+    if (cudaMallocAsync((void**)&e->lambda, sizeof(double) * total, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&e->s32, sizeof(float) * total, s) != cudaSuccess) {
         cleanup();
         return fail(CF_ERR_NOMEM, "device allocation of the embedding (%lld cells) failed", total);
     }
+    const bool want_error = (flags & CF_EMBED_CLAMP) && !(flags & CF_EMBED_SKIP_ERROR);
+    {
     ScopedKernelTimer kt(s, "embed_psd");
     k_take_real<<<blocks, kRedThreads, 0, s>>>(sc.z, 1.0, e->lambda, total);
     k_minmax_partial<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.part);
     k_minmax_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
     CF_CUDA(cudaMemsetAsync(sc.counts, 0, 2 * sizeof(unsigned long long), s));
-    const bool want_error = (flags & CF_EMBED_CLAMP) && !(flags & CF_EMBED_SKIP_ERROR);
-    k_threshold<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.st, 1.0 / sqrt((double)total), e->s64,
-                                               e->s32, nullptr, sc.part, sc.counts);
+    k_threshold<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.st, 1.0 / (double)total, e->s32, sc.part,
+                                               sc.counts);
     k_threshold_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.counts, sc.st);
+    }
     CF_CHECK_LAUNCH();
     EmbedStats st{};
     CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
@@ -290,11 +309,17 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
         r.exact = 0;
         if (want_error) {
             // realised covariance = IDFT(lambda+)/M^d
-            k_lambda_plus_complex<<<blocks, kRedThreads, 0, s>>>(e->lambda, st.tau, sc.z, total);
+            {
+                ScopedKernelTimer kt(s, "embed_cov_error");
+                k_lambda_plus_complex<<<blocks, kRedThreads, 0, s>>>(e->lambda, st.tau, sc.z, total);
+            }
             CF_CHECK_LAUNCH();
             CF_TRY((fft_nd_inplace<double, +1>(sc.z, gi, s)));
-            k_cov_error_partial<<<blocks, kRedThreads, 0, s>>>(sc.z, sc.c, gi, 1.0 / (double)total, sc.part);
-            k_cov_error_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
+            {
+                ScopedKernelTimer kt(s, "embed_cov_error");
+                k_cov_error_partial<<<blocks, kRedThreads, 0, s>>>(sc.z, sc.c, gi, 1.0 / (double)total, sc.part);
+                k_cov_error_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
+            }
             CF_CHECK_LAUNCH();
             CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
             CF_CUDA(cudaStreamSynchronize(s));
@@ -303,6 +328,7 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
     }
     e->report = r;
     if (rep) *rep = r;
+    record_use(e, s);
     *out = e;
     return CF_OK;
 }

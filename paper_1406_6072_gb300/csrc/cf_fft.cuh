@@ -19,15 +19,23 @@ namespace cf {
 
 constexpr int TWN = 8192;  // twiddle table length: w[j] = exp(+2 pi i j / TWN)
 
+// Points held per thread (build-time tunables; powers of two, 2..16).
+#ifndef CF_E32
+#define CF_E32 16
+#endif
+#ifndef CF_E64
+#define CF_E64 8
+#endif
+
 template <typename T>
 struct FftE;
 template <>
 struct FftE<float> {
-    static constexpr int value = 16;
+    static constexpr int value = CF_E32;
 };
 template <>
 struct FftE<double> {
-    static constexpr int value = 8;
+    static constexpr int value = CF_E64;
 };
 
 template <typename T, int L>
@@ -147,7 +155,9 @@ __device__ __forceinline__ C2<T> twiddle(const C2<T>* __restrict__ tw, int idx) 
 // butterfly b (jb = j + b*TL) takes points jb + q*(L/R), q < R, in v[b*R + q].
 // KEEP: only outputs with point index < KEEP are produced (KEEP = L or L/2).
 // out(line, point, value) receives each kept output of the last stage.
-template <typename T, int L, int E, int SIGN, int KEEP, int NS, class Lay, class Out>
+// SYNC_OUT: barrier before the last stage emits its outputs, so that out()
+// may write into the exchange buffer sm itself.
+template <typename T, int L, int E, int SIGN, int KEEP, int NS, bool SYNC_OUT, class Lay, class Out>
 __device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, int j, C2<T> (&v)[E],
                                           const C2<T>* __restrict__ tw, Out& out) {
     constexpr int R = (E < L / NS) ? E : (L / NS);
@@ -167,6 +177,7 @@ __device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, i
 #pragma unroll
     for (int b = 0; b < B; ++b) dftR<R, SIGN>(&v[b * R]);
     if constexpr (NS * R == L) {
+        if constexpr (SYNC_OUT) __syncthreads();
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
@@ -190,18 +201,18 @@ __device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, i
         for (int b = 0; b < B2; ++b)
 #pragma unroll
             for (int q = 0; q < R2; ++q) v[b * R2 + q] = sm[lay(line, j + b * TL + q * STRIDE2)];
-        fft_stage<T, L, E, SIGN, KEEP, NS2>(sm, lay, line, j, v, tw, out);
+        fft_stage<T, L, E, SIGN, KEEP, NS2, SYNC_OUT>(sm, lay, line, j, v, tw, out);
     }
 }
 
 // Full transform of a line whose first-stage inputs v[q] = x[j + q*L/E] are
 // already in registers.  Every thread of the CTA must call this (it contains
 // __syncthreads); threads without a valid line pass dummy data.
-template <typename T, int L, int SIGN, int KEEP, class Lay, class Out>
+template <typename T, int L, int SIGN, int KEEP, class Lay, class Out, bool SYNC_OUT = false>
 __device__ __forceinline__ void line_fft(C2<T>* sm, const Lay& lay, int line, int j,
                                          C2<T> (&v)[LineGeom<T, L>::E], const C2<T>* __restrict__ tw,
                                          Out& out) {
-    fft_stage<T, L, LineGeom<T, L>::E, SIGN, KEEP, 1>(sm, lay, line, j, v, tw, out);
+    fft_stage<T, L, LineGeom<T, L>::E, SIGN, KEEP, 1, SYNC_OUT>(sm, lay, line, j, v, tw, out);
 }
 
 }  // namespace cf

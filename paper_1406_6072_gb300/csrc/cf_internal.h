@@ -6,6 +6,9 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "../../include/cf.h"
 #include "cf_device.cuh"
@@ -92,9 +95,19 @@ cf_status check_grid(const cf_grid* g, GridInfo* gi);
 struct cf_embedding {
     cf::GridInfo grid;
     double* lambda = nullptr;    // raw eigenvalues [mtotal]
-    double* s64 = nullptr;       // sqrt(lambda+) * mtotal^{-1/2} [mtotal]
-    float* s32 = nullptr;        // binary32 copy of s64 [mtotal]
+    double* s64 = nullptr;       // sqrt(lambda+ / mtotal) [mtotal], built on first binary64 use
+    float* s32 = nullptr;        // sqrt(lambda+ / mtotal) in binary32 [mtotal]
     double tau = 0.0;
     cf_embed_report report{};
     int device = 0;
+    cudaStream_t alloc_stream = nullptr;
+    std::mutex mu;                                           // guards s64 and uses
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;  // last use per stream
 };
+
+namespace cf {
+// Records that work enqueued on stream s reads embedding e (the free waits for it).
+void record_use(cf_embedding* e, cudaStream_t s);
+// Builds e->s64 (on stream s) if it does not exist yet.
+cf_status ensure_s64(cf_embedding* e, cudaStream_t s);
+}  // namespace cf

@@ -57,16 +57,33 @@ struct FieldEpi {
 // out[outer][KEEP][inner] (in place allowed when KEEP == L); mode 1: field
 // epilogue with realization = outer index and cell = point*inner + i.
 // --------------------------------------------------------------------------
+// Build-time tunables of the CTA shapes: threads per CTA and the minimum
+// number of resident CTAs per SM given to the register allocator.
+#ifndef CF_COLS_THREADS
+#define CF_COLS_THREADS 256
+#endif
+#ifndef CF_COLS_MINB
+#define CF_COLS_MINB 1
+#endif
+#ifndef CF_ROWS_THREADS
+#define CF_ROWS_THREADS 256
+#endif
+#ifndef CF_ROWS_MINB
+#define CF_ROWS_MINB 1
+#endif
+
 template <typename T, int L>
 struct ColsCfg {
     using G = LineGeom<T, L>;
-    static constexpr int C = G::TL >= 256 ? 1 : ((256 / G::TL) > 32 ? 32 : (256 / G::TL));
+    static constexpr int C =
+        G::TL >= CF_COLS_THREADS ? 1 : ((CF_COLS_THREADS / G::TL) > 32 ? 32 : (CF_COLS_THREADS / G::TL));
     static constexpr int THREADS = C * G::TL;
+    static constexpr int MINB = THREADS * CF_COLS_MINB <= 2048 ? CF_COLS_MINB : 1;
     static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)C * (size_t)G::PADDED;
 };
 
 template <typename T, int L, int SIGN, int KEEP_HALF>
-__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
     k_cols(const C2<T>* in, long long inner, C2<T>* out, int mode, FieldEpi<T> epi,
            const C2<T>* __restrict__ tw) {
     using Cfg = ColsCfg<T, L>;
@@ -99,13 +116,14 @@ __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS)
 template <typename T, int L>
 struct RowsCfg {
     using G = LineGeom<T, L>;
-    static constexpr int ROWS = G::TL >= 256 ? 1 : 256 / G::TL;
+    static constexpr int ROWS = G::TL >= CF_ROWS_THREADS ? 1 : CF_ROWS_THREADS / G::TL;
     static constexpr int THREADS = ROWS * G::TL;
+    static constexpr int MINB = THREADS * CF_ROWS_MINB <= 2048 ? CF_ROWS_MINB : 1;
     static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
 };
 
 template <typename T, int L, int SIGN>
-__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS, RowsCfg<T, L>::MINB)
     k_rows_c2c(C2<T>* data, long long nrows, const C2<T>* __restrict__ tw) {
     using Cfg = RowsCfg<T, L>;
     using G = typename Cfg::G;

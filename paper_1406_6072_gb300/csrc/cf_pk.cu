@@ -7,6 +7,13 @@
 // into half spectra (k_last in [0, n/2]).  The remaining axes are complex
 // column passes; the last one squares, weights (2 for 0 < k_last < n/2, the
 // mirror mode -k) and bins in shared memory before one atomic add per bin.
+//
+// Count maps: delta_g = X/Nhat - I with X = N/f on unmasked cells (0
+// elsewhere) and I the unmasked-cell indicator, so for k != 0
+// |DFT delta_g|^2 = |DFT X|^2/Nhat^2 - 2 Re(DFT X conj DFT I)/Nhat + |DFT I|^2.
+// The transform runs on X (no pre-pass for Nhat): the row pass accumulates
+// N_tot per field, the binning pass accumulates |DFT X|^2 and the cross term
+// against the mask spectrum DFT I, and the final pass combines them.
 #include <math.h>
 
 #include "cf_kernels.cuh"
@@ -19,7 +26,7 @@ struct Edges {
     double e[kMaxBins + 1];
 };
 
-enum { PK_FLOAT = 0, PK_DOUBLE = 1, PK_COUNTS = 2 };
+enum { PK_FLOAT = 0, PK_DOUBLE = 1, PK_COUNTS = 2, PK_MASK = 3 };
 
 __global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int* __restrict__ bin_of) {
     for (long long k2 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k2 <= k2max;
@@ -38,62 +45,21 @@ __global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int* __restr
 
 __device__ __forceinline__ long long signed_mode(long long i, long long n) { return i <= n / 2 ? i : i - n; }
 
-__global__ void k_pk_nmodes(GridInfo g, const int* __restrict__ bin_of, long long k2max,
-                            unsigned long long* __restrict__ nmodes) {
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.ncell;
-         idx += (long long)gridDim.x * blockDim.x) {
-        long long rem = idx, k2 = 0;
-        for (int a = g.ndim - 1; a >= 0; --a) {
-            const long long i = rem % g.n[a];
-            rem /= g.n[a];
-            const long long sn = signed_mode(i, g.n[a]);
-            k2 += sn * sn;
-        }
-        const int b = k2 <= k2max ? bin_of[k2] : -1;
-        if (b >= 0) atomicAdd(&nmodes[b], 1ull);
-    }
-}
-
-__global__ void k_count_totals(const int32_t* __restrict__ counts, long long cells, const float* __restrict__ f,
-                               unsigned long long* __restrict__ ntot, double* __restrict__ fsum) {
-    const int field = blockIdx.y;
-    unsigned long long acc = 0;
-    double facc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cells;
-         i += (long long)gridDim.x * blockDim.x) {
-        acc += (unsigned long long)(long long)counts[(size_t)field * cells + i];
-        if (field == 0) facc += f ? (double)f[i] : 1.0;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        acc += __shfl_down_sync(0xffffffffu, acc, o);
-        facc += __shfl_down_sync(0xffffffffu, facc, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (acc) atomicAdd(&ntot[field], acc);
-        if (field == 0 && facc != 0.0) atomicAdd(fsum, facc);
-    }
-}
-
-__global__ void k_nhat(const unsigned long long* __restrict__ ntot, const double* __restrict__ fsum, int nfields,
-                       double* __restrict__ nhat) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nfields) nhat[i] = fsum[0] > 0.0 ? (double)ntot[i] / fsum[0] : 0.0;
-}
-
 // Pass 1: pairs of real fields along the last axis -> two half spectra.
 template <typename T, int L>
 struct PkRowsCfg {
     using G = LineGeom<T, L>;
-    static constexpr int ROWS = G::TL >= 256 ? 1 : 256 / G::TL;
+    static constexpr int ROWS = G::TL >= CF_ROWS_THREADS ? 1 : CF_ROWS_THREADS / G::TL;
     static constexpr int THREADS = ROWS * G::TL;
-    static constexpr size_t SMEM = 2 * sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
+    static constexpr int MINB = THREADS * CF_ROWS_MINB <= 2048 ? CF_ROWS_MINB : 1;
+    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
 };
 
 template <typename T, int L>
-__global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS)
-    k_pk_rows(const void* __restrict__ fields, int kind, const float* __restrict__ f, const double* __restrict__ nhat,
-              long long rows, long long cells, long long nfields, long long f0, C2<T>* __restrict__ out,
-              const C2<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MINB)
+    k_pk_rows(const void* __restrict__ fields, int kind, const float* __restrict__ f,
+              unsigned long long* __restrict__ ntot, double* __restrict__ fsum, long long rows, long long cells,
+              long long nfields, long long f0, C2<T>* __restrict__ out, const C2<T>* __restrict__ tw) {
     using Cfg = PkRowsCfg<T, L>;
     using G = typename Cfg::G;
     constexpr int E = G::E;
@@ -101,7 +67,6 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS)
     constexpr int H = L / 2 + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
-    C2<T>* sm2 = sm + (size_t)Cfg::ROWS * G::PADDED;
     const int line = threadIdx.x / G::TL;
     const int j = threadIdx.x % G::TL;
     const long long row = (long long)blockIdx.x * Cfg::ROWS + line;
@@ -109,30 +74,52 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS)
     const long long rw = valid ? row : 0;
     const long long fa = f0 + 2ll * blockIdx.y;  // global field index of A
     const long long fb = fa + 1;
-    const bool hasb = fb < nfields;
-    T nha = 0, nhb = 0;
-    if (kind == PK_COUNTS) {
-        nha = (T)nhat[fa];
-        nhb = hasb ? (T)nhat[fb] : (T)0;
-    }
-    auto value = [&](long long fld, T nh, long long p) -> T {
+    const bool hasb = kind != PK_MASK && fb < nfields;
+    // X = N/f (0 where f = 0) for count maps; the indicator of f != 0 for the mask
+    unsigned long long na = 0, nb = 0;
+    double fs = 0.0;
+    auto value = [&](long long fld, long long p, unsigned long long& ncount) -> T {
         const size_t at = (size_t)fld * cells + (size_t)rw * L + p;
         if (kind == PK_FLOAT) return (T)((const float*)fields)[at];
         if (kind == PK_DOUBLE) return (T)((const double*)fields)[at];
         const long long cell = rw * L + p;
-        const T fi = f ? (T)f[cell] : (T)1;
-        const T N = (T)((const int32_t*)fields)[at];
-        return (fi != (T)0 && nh > (T)0) ? (N / fi - nh) / nh : (T)0;
+        if (kind == PK_MASK) {
+            const float fi = f[cell];
+            if (valid) fs += (double)fi;
+            return fi != 0.0f ? (T)1 : (T)0;
+        }
+        const int32_t N = ((const int32_t*)fields)[at];
+        if (valid) ncount += (unsigned long long)(long long)N;
+        if (!f) return (T)N;
+        const T fi = (T)f[cell];
+        return fi != (T)0 ? (T)N / fi : (T)0;
     };
     C2<T> v[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
         const long long p = j + q * STEP;
-        v[q] = mk(value(fa, nha, p), hasb ? value(fb, nhb, p) : (T)0);
+        const T va = value(fa, p, na);
+        v[q] = mk(va, hasb ? value(fb, p, nb) : (T)0);
+    }
+    if (kind == PK_COUNTS || kind == PK_MASK) {
+        for (int o = 16; o > 0; o >>= 1) {
+            na += __shfl_down_sync(0xffffffffu, na, o);
+            nb += __shfl_down_sync(0xffffffffu, nb, o);
+            fs += __shfl_down_sync(0xffffffffu, fs, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (kind == PK_COUNTS) {
+                if (na) atomicAdd(&ntot[fa], na);
+                if (nb) atomicAdd(&ntot[fb], nb);
+            } else if (fs != 0.0) {
+                atomicAdd(fsum, fs);
+            }
+        }
     }
     RowLayout<E, G::PADDED> lay;
-    auto sink = [&](int ln, int p, C2<T> val) { sm2[lay(ln, p)] = val; };
-    line_fft<T, L, -1, L>(sm, lay, line, j, v, tw, sink);
+    // the spectrum of the line goes back into the exchange buffer
+    auto sink = [&](int ln, int p, C2<T> val) { sm[lay(ln, p)] = val; };
+    line_fft<T, L, -1, L, RowLayout<E, G::PADDED>, decltype(sink), true>(sm, lay, line, j, v, tw, sink);
     __syncthreads();
     if (!valid) return;
     const long long la = fa - f0, lb = fb - f0;
@@ -140,25 +127,38 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS)
     C2<T>* ob = out + ((size_t)lb * rows + row) * H;
     const T half = (T)0.5;
     for (int k = j; k < H; k += G::TL) {
-        const C2<T> zk = sm2[lay(line, k & (L - 1))];
-        const C2<T> zm = sm2[lay(line, (L - k) & (L - 1))];
+        const C2<T> zk = sm[lay(line, k & (L - 1))];
+        const C2<T> zm = sm[lay(line, (L - k) & (L - 1))];
         oa[k] = mk(half * (zk.x + zm.x), half * (zk.y - zm.y));
         if (hasb) ob[k] = mk(half * (zk.y + zm.y), half * (zm.x - zk.x));
     }
 }
 
-// Last pass: FFT along axis 0, |X|^2 with mirror weights, binned.
+// Last pass: FFT along axis 0, |X|^2 with mirror weights, binned.  With a
+// mask spectrum (count maps on a masked survey) the cross term
+// Re(X conj I) is binned as well.  The first field of a call also counts the
+// modes per bin and, with a mask, bins |I|^2.
 template <typename T, int L>
-__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
     k_pk_cols(const C2<T>* __restrict__ in, long long inner, long long H, long long n_mid, long long n_last,
-              const int* __restrict__ bin_of, long long k2max, int nbins, double* __restrict__ acc, long long f0,
-              const C2<T>* __restrict__ tw) {
+              const int* __restrict__ bin_of, long long k2max, int nbins, double* __restrict__ acc,
+              double* __restrict__ acc_cross, const C2<T>* __restrict__ mask_spec, unsigned long long* __restrict__ nmodes,
+              double* __restrict__ mask_power, long long f0, const C2<T>* __restrict__ tw) {
     using Cfg = ColsCfg<T, L>;
     using G = typename Cfg::G;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
     T* sbin = reinterpret_cast<T*>(sm + (size_t)Cfg::C * G::PADDED);
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sbin[b] = (T)0;
+    T* scross = sbin + nbins;
+    T* smask = scross + nbins;
+    unsigned int* scount = reinterpret_cast<unsigned int*>(smask + nbins);
+    const bool first = (f0 == 0 && blockIdx.y == 0);
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        sbin[b] = (T)0;
+        scross[b] = (T)0;
+        smask[b] = (T)0;
+        scount[b] = 0u;
+    }
     __syncthreads();
     const int ln = threadIdx.x % Cfg::C;
     const int j = threadIdx.x / Cfg::C;
@@ -172,50 +172,99 @@ __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS)
     const long long il = i % H;          // k_last index in [0, n_last/2]
     const long long imid = i / H;        // middle-axis index (3D) or 0
     const long long smid = signed_mode(imid, n_mid);
-    const T w = (il == 0 || 2 * il == n_last) ? (T)1 : (T)2;
+    const int wi = (il == 0 || 2 * il == n_last) ? 1 : 2;
+    const T w = (T)wi;
     auto sink = [&](int, int p, C2<T> val) {
         if (!valid) return;
         const long long s0 = signed_mode(p, L);
         const long long k2 = s0 * s0 + smid * smid + il * il;
         const int b = k2 <= k2max ? bin_of[k2] : -1;
-        if (b >= 0) atomicAdd(&sbin[b], w * (val.x * val.x + val.y * val.y));
+        if (b < 0) return;
+        atomicAdd(&sbin[b], w * (val.x * val.x + val.y * val.y));
+        if (mask_spec) {
+            const C2<T> mb = mask_spec[(size_t)p * inner + i];
+            atomicAdd(&scross[b], w * (val.x * mb.x + val.y * mb.y));
+            if (first) atomicAdd(&smask[b], w * (mb.x * mb.x + mb.y * mb.y));
+        }
+        if (first) atomicAdd(&scount[b], (unsigned int)wi);
     };
     line_fft<T, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-        const T s = sbin[b];
-        if (s != (T)0) atomicAdd(&acc[(size_t)(f0 + o) * nbins + b], (double)s);
+        const size_t at = (size_t)(f0 + o) * nbins + b;
+        if (sbin[b] != (T)0) atomicAdd(&acc[at], (double)sbin[b]);
+        if (mask_spec && scross[b] != (T)0) atomicAdd(&acc_cross[at], (double)scross[b]);
+        if (first) {
+            if (scount[b]) atomicAdd(&nmodes[b], (unsigned long long)scount[b]);
+            if (mask_spec && smask[b] != (T)0) atomicAdd(&mask_power[b], (double)smask[b]);
+        }
     }
 }
 
-__global__ void k_pk_finalize(const double* __restrict__ acc, const unsigned long long* __restrict__ nmodes,
-                              long long nfields, int nbins, double volfac, double* __restrict__ pk,
-                              int64_t* __restrict__ nmodes_out) {
+// pk = cell^d/(prod n) * S/N_b; for count maps S = acc/Nhat^2 - 2 cross/Nhat + mask_power
+// with Nhat = N_tot/sum f (0 when there are no counts).
+__global__ void k_pk_finalize(const double* __restrict__ acc, const double* __restrict__ acc_cross,
+                              const double* __restrict__ mask_power, const unsigned long long* __restrict__ ntot,
+                              const double* __restrict__ fsum_dev, double fsum_host,
+                              const unsigned long long* __restrict__ nmodes, long long nfields, int nbins,
+                              double volfac, double* __restrict__ pk, int64_t* __restrict__ nmodes_out) {
     const long long total = nfields * nbins;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(idx % nbins);
+        const long long fld = idx / nbins;
         const unsigned long long nm = nmodes[b];
-        pk[idx] = nm ? volfac * acc[idx] / (double)nm : 0.0;
+        double S = acc[idx];
+        if (ntot) {
+            const double fsum = fsum_dev ? fsum_dev[0] : fsum_host;
+            const double nhat = fsum > 0.0 ? (double)ntot[fld] / fsum : 0.0;
+            if (nhat > 0.0) {
+                S = S / (nhat * nhat);
+                if (acc_cross) S += -2.0 * acc_cross[idx] / nhat + mask_power[b];
+            } else {
+                S = 0.0;
+            }
+        }
+        pk[idx] = nm ? volfac * S / (double)nm : 0.0;
         if (idx < nbins && nmodes_out) nmodes_out[idx] = (int64_t)nmodes[idx];
     }
 }
 
+// mean over fields: one block per bin, threads over fields
 __global__ void k_pk_mean(const double* __restrict__ pk, long long nfields, int nbins, double* __restrict__ mean) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbins) return;
+    __shared__ double sh[256];
+    const int b = blockIdx.x;
     double s = 0.0;
-    for (long long f = 0; f < nfields; ++f) s += pk[f * nbins + b];
-    mean[b] = nfields > 0 ? s / (double)nfields : 0.0;
+    for (long long f = threadIdx.x; f < nfields; f += blockDim.x) s += pk[f * nbins + b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[b] = nfields > 0 ? sh[0] / (double)nfields : 0.0;
 }
 
+// unbiased covariance: one block per (a, b) with a <= b, threads over fields
 __global__ void k_pk_cov(const double* __restrict__ pk, const double* __restrict__ mean, long long nfields, int nbins,
                          double* __restrict__ cov) {
-    const int a = blockIdx.x;
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-        double s = 0.0;
-        for (long long f = 0; f < nfields; ++f) s += (pk[f * nbins + a] - mean[a]) * (pk[f * nbins + b] - mean[b]);
-        cov[(size_t)a * nbins + b] = nfields > 1 ? s / (double)(nfields - 1) : 0.0;
+    __shared__ double sh[256];
+    const int a = blockIdx.y, b = blockIdx.x;
+    if (b < a) return;
+    const double ma = mean[a], mb = mean[b];
+    double s = 0.0;
+    for (long long f = threadIdx.x; f < nfields; f += blockDim.x)
+        s += (pk[f * nbins + a] - ma) * (pk[f * nbins + b] - mb);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double c = nfields > 1 ? sh[0] / (double)(nfields - 1) : 0.0;
+        cov[(size_t)a * nbins + b] = c;
+        cov[(size_t)b * nbins + a] = c;
     }
 }
 
@@ -229,7 +278,7 @@ struct PkPlan {
     long long rows;     // prod of leading axes
     size_t elem;
     long long chunk;    // fields per chunk (even)
-    size_t off_bin, off_nmodes, off_acc, off_nhat, off_fsum, off_ntot, off_half, off_half2, total;
+    size_t off_bin, off_nmodes, off_acc, off_cross, off_mpow, off_ntot, off_fsum, off_mask, off_half, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -291,34 +340,34 @@ static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins
     if (chunk > nf_even) chunk = nf_even < 2 ? 2 : nf_even;
     P->chunk = chunk;
     size_t o = 0;
-    P->off_bin = o;
-    o = align256(o + sizeof(int) * (size_t)(P->k2max + 1));
-    P->off_nmodes = o;
-    o = align256(o + sizeof(unsigned long long) * P->nbins);
-    P->off_acc = o;
-    o = align256(o + sizeof(double) * (size_t)nfields * P->nbins);
-    P->off_nhat = o;
-    o = align256(o + sizeof(double) * (size_t)nfields);
-    P->off_fsum = o;
-    o = align256(o + sizeof(double));
-    P->off_ntot = o;
-    o = align256(o + sizeof(unsigned long long) * (size_t)nfields);
-    P->off_half = o;
-    o = align256(o + per_field * (size_t)chunk);
-    P->off_half2 = o;  // unused (3D passes run in place)
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    P->off_bin = take(sizeof(int) * (size_t)(P->k2max + 1));
+    P->off_nmodes = take(sizeof(unsigned long long) * P->nbins);
+    P->off_acc = take(sizeof(double) * (size_t)nfields * P->nbins);
+    P->off_cross = take(sizeof(double) * (size_t)nfields * P->nbins);
+    P->off_mpow = take(sizeof(double) * P->nbins);
+    P->off_ntot = take(sizeof(unsigned long long) * (size_t)nfields);
+    P->off_fsum = take(sizeof(double));
+    P->off_mask = take(per_field);
+    P->off_half = take(per_field * (size_t)chunk);
     P->total = o;
     return CF_OK;
 }
 
 template <typename T, int L>
-static cf_status launch_pk_rows(const void* fields, int kind, const float* f, const double* nhat, const PkPlan& P,
-                                long long nfields, long long f0, long long nchunk, C2<T>* out, cudaStream_t s) {
+static cf_status launch_pk_rows(const void* fields, int kind, const float* f, unsigned long long* ntot,
+                                double* fsum, const PkPlan& P, long long nfields, long long f0, long long nchunk,
+                                C2<T>* out, cudaStream_t s) {
     using Cfg = PkRowsCfg<T, L>;
     auto kern = k_pk_rows<T, L>;
     CF_TRY(prepare_smem(kern, Cfg::SMEM));
     dim3 grid((unsigned)((P.rows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)((nchunk + 1) / 2));
     ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_rows_f32" : "pk_rows_f64", L);
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(fields, kind, f, nhat, P.rows, P.g.ncell, nfields, f0, out,
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(fields, kind, f, ntot, fsum, P.rows, P.g.ncell, nfields, f0, out,
                                                twiddles<T>());
     CF_CHECK_LAUNCH();
     return CF_OK;
@@ -326,17 +375,27 @@ static cf_status launch_pk_rows(const void* fields, int kind, const float* f, co
 
 template <typename T, int L>
 static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mid, const PkPlan& P, const int* bin_of,
-                                double* acc, long long f0, long long nchunk, cudaStream_t s) {
+                                double* acc, double* cross, const C2<T>* mask_spec, unsigned long long* nmodes,
+                                double* mpow, long long f0, long long nchunk, cudaStream_t s) {
     using Cfg = ColsCfg<T, L>;
     auto kern = k_pk_cols<T, L>;
-    const size_t smem = Cfg::SMEM + sizeof(T) * (size_t)P.nbins;
+    const size_t smem = Cfg::SMEM + (3 * sizeof(T) + sizeof(unsigned int)) * (size_t)P.nbins;
     CF_TRY(prepare_smem(kern, smem));
     dim3 grid((unsigned)((inner + Cfg::C - 1) / Cfg::C), (unsigned)nchunk);
     ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_cols_f32" : "pk_cols_f64", L);
     kern<<<grid, Cfg::THREADS, smem, s>>>(in, inner, P.H, n_mid, P.g.n[P.g.ndim - 1], bin_of, P.k2max, P.nbins, acc,
-                                          f0, twiddles<T>());
+                                          cross, mask_spec, nmodes, mpow, f0, twiddles<T>());
     CF_CHECK_LAUNCH();
     return CF_OK;
+}
+
+// Transform along the remaining axes of half spectra [nc][rows][H] in place
+// except the first axis (3D: axis 1).
+template <typename T>
+static cf_status pk_middle_axis(const PkPlan& P, C2<T>* half, long long nc, cudaStream_t s) {
+    if (P.g.ndim != 3) return CF_OK;
+    FieldEpi<T> none{};
+    return launch_cols<T, -1, 0>(P.g.n[1], half, nc * P.g.n[0], P.H, half, 0, none, s);
 }
 
 template <typename T>
@@ -346,53 +405,56 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
     int* bin_of = (int*)(ws + P.off_bin);
     unsigned long long* nmodes = (unsigned long long*)(ws + P.off_nmodes);
     double* acc = (double*)(ws + P.off_acc);
-    double* nhat = (double*)(ws + P.off_nhat);
-    double* fsum = (double*)(ws + P.off_fsum);
+    double* cross = (double*)(ws + P.off_cross);
+    double* mpow = (double*)(ws + P.off_mpow);
     unsigned long long* ntot = (unsigned long long*)(ws + P.off_ntot);
+    double* fsum = (double*)(ws + P.off_fsum);
+    C2<T>* mask_spec = (C2<T>*)(ws + P.off_mask);
     C2<T>* half = (C2<T>*)(ws + P.off_half);
-    {
-    ScopedKernelTimer kt(s, "pk_setup");
-    k_pk_bintable<<<grid_blocks(P.k2max + 1, 256, 1024), 256, 0, s>>>(P.edges, P.nbins, P.k2max, bin_of);
-    CF_CUDA(cudaMemsetAsync(nmodes, 0, sizeof(unsigned long long) * P.nbins, s));
-    CF_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nfields * P.nbins, s));
-    k_pk_nmodes<<<grid_blocks(g.ncell, 256, 1024), 256, 0, s>>>(g, bin_of, P.k2max, nmodes);
-    }
-    CF_CHECK_LAUNCH();
-    if (kind == PK_COUNTS) {
-        CF_CUDA(cudaMemsetAsync(ntot, 0, sizeof(unsigned long long) * (size_t)nfields, s));
-        CF_CUDA(cudaMemsetAsync(fsum, 0, sizeof(double), s));
-        dim3 grid((unsigned)grid_blocks(g.ncell, 256, 64), (unsigned)nfields);
-        ScopedKernelTimer kt(s, "pk_count_totals");
-        k_count_totals<<<grid, 256, 0, s>>>((const int32_t*)fields, g.ncell, f, ntot, fsum);
-        k_nhat<<<(unsigned)((nfields + 255) / 256), 256, 0, s>>>(ntot, fsum, (int)nfields, nhat);
-        CF_CHECK_LAUNCH();
-    }
+    const bool counts = kind == PK_COUNTS;
+    const bool masked = counts && f != nullptr;
     const int d = g.ndim;
     const long long nl = g.n[d - 1];
+    const long long inner = (d == 3 ? g.n[1] : 1) * P.H;
+    const long long n_mid = d == 3 ? g.n[1] : 1;
+    {
+        ScopedKernelTimer kt(s, "pk_setup");
+        k_pk_bintable<<<grid_blocks(P.k2max + 1, 256, 1024), 256, 0, s>>>(P.edges, P.nbins, P.k2max, bin_of);
+        CF_CUDA(cudaMemsetAsync(ws + P.off_nmodes, 0, P.off_half - P.off_nmodes, s));
+    }
+    CF_CHECK_LAUNCH();
+    if (masked) {
+        // spectrum of the unmasked-cell indicator (and sum f) through the same passes
+        CF_TRY(dispatch_line(nl, [&](auto Lc) -> cf_status {
+            return launch_pk_rows<T, decltype(Lc)::value>(nullptr, PK_MASK, f, ntot, fsum, P, 1, 0, 1, mask_spec, s);
+        }));
+        CF_TRY(pk_middle_axis<T>(P, mask_spec, 1, s));
+        FieldEpi<T> none{};
+        CF_TRY((launch_cols<T, -1, 0>(g.n[0], mask_spec, 1, inner, mask_spec, 0, none, s)));
+    }
     for (long long f0 = 0; f0 < nfields; f0 += P.chunk) {
         const long long nc = (nfields - f0) < P.chunk ? (nfields - f0) : P.chunk;
         CF_TRY(dispatch_line(nl, [&](auto Lc) -> cf_status {
-            return launch_pk_rows<T, decltype(Lc)::value>(fields, kind, f, nhat, P, nfields, f0, nc, half, s);
+            return launch_pk_rows<T, decltype(Lc)::value>(fields, kind, f, ntot, fsum, P, nfields, f0, nc, half, s);
         }));
-        if (d == 3) {
-            FieldEpi<T> none{};
-            CF_TRY((launch_cols<T, -1, 0>(g.n[1], half, nc * g.n[0], P.H, half, 0, none, s)));
-        }
-        const long long inner = (d == 3 ? g.n[1] : 1) * P.H;
-        const long long n_mid = d == 3 ? g.n[1] : 1;
+        CF_TRY(pk_middle_axis<T>(P, half, nc, s));
         CF_TRY(dispatch_line(g.n[0], [&](auto Lc) -> cf_status {
-            return launch_pk_cols<T, decltype(Lc)::value>(half, inner, n_mid, P, bin_of, acc, f0, nc, s);
+            return launch_pk_cols<T, decltype(Lc)::value>(half, inner, n_mid, P, bin_of, acc, masked ? cross : nullptr,
+                                                          masked ? mask_spec : nullptr, nmodes, mpow, f0, nc, s);
         }));
     }
     double volfac = 1.0;
     for (int a = 0; a < d; ++a) volfac *= g.cell[a] / (double)g.n[a];
-    ScopedKernelTimer kt(s, "pk_finalize");
-    k_pk_finalize<<<grid_blocks(nfields * P.nbins, 256, 1024), 256, 0, s>>>(acc, nmodes, nfields, P.nbins, volfac,
-                                                                            pk_out, nmodes_out);
-    if (mean || cov) {
-        double* mu = mean ? mean : acc;  // acc is free after finalize when mean is not wanted
-        k_pk_mean<<<(P.nbins + 127) / 128, 128, 0, s>>>(pk_out, nfields, P.nbins, mu);
-        if (cov) k_pk_cov<<<P.nbins, 128, 0, s>>>(pk_out, mu, nfields, P.nbins, cov);
+    {
+        ScopedKernelTimer kt(s, "pk_finalize");
+        k_pk_finalize<<<grid_blocks(nfields * P.nbins, 256, 1024), 256, 0, s>>>(
+            acc, masked ? cross : nullptr, mpow, counts ? ntot : nullptr, masked ? fsum : nullptr, (double)g.ncell,
+            nmodes, nfields, P.nbins, volfac, pk_out, nmodes_out);
+        if (mean || cov) {
+            double* mu = mean ? mean : cross;  // scratch when only the covariance is wanted
+            k_pk_mean<<<P.nbins, 256, 0, s>>>(pk_out, nfields, P.nbins, mu);
+            if (cov) k_pk_cov<<<dim3(P.nbins, P.nbins), 256, 0, s>>>(pk_out, mu, nfields, P.nbins, cov);
+        }
     }
     CF_CHECK_LAUNCH();
     return CF_OK;

@@ -131,16 +131,75 @@ extern "C" const char* cf_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* cf_version(void) { return "cf 0.1 (sm_103a)"; }
 
+namespace cf {
+
+// One non-blocking stream per device on which embeddings are released.
+static cudaStream_t g_free_stream[kMaxDevices];
+static std::mutex g_free_mu;
+
+void record_use(cf_embedding* e, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    for (auto& u : e->uses) {
+        if (u.first == s) {
+            cudaEventRecord(u.second, s);
+            return;
+        }
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return;
+    cudaEventRecord(ev, s);
+    e->uses.emplace_back(s, ev);
+}
+
+__global__ void k_s64(const double* __restrict__ lam, double tau, double inv_total, double* __restrict__ s64,
+                      long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        s64[i] = l > tau ? sqrt(l * inv_total) : 0.0;
+    }
+}
+
+cf_status ensure_s64(cf_embedding* e, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    if (e->s64) return CF_OK;
+    const long long total = e->grid.mtotal;
+    double* p = nullptr;
+    if (cudaMallocAsync((void**)&p, sizeof(double) * total, s) != cudaSuccess)
+        return fail(CF_ERR_NOMEM, "device allocation of the binary64 amplitudes failed");
+    const int blocks = (int)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256);
+    k_s64<<<blocks, 256, 0, s>>>(e->lambda, e->tau, 1.0 / (double)total, p, total);
+    CF_CHECK_LAUNCH();
+    e->s64 = p;
+    return CF_OK;
+}
+
+}  // namespace cf
+
+// Stream-ordered release: a library-owned stream waits for the last recorded
+// use on every stream, then frees; no host-side wait.
 extern "C" cf_status cf_embedding_free(cf_embedding* e) {
     if (!e) return CF_OK;
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(e->device);
-    // enqueued work on any stream may still read the embedding
-    cudaDeviceSynchronize();
-    cudaFree(e->lambda);
-    cudaFree(e->s64);
-    cudaFree(e->s32);
+    cudaStream_t fs = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_free_mu);
+        if (!g_free_stream[e->device]) cudaStreamCreateWithFlags(&g_free_stream[e->device], cudaStreamNonBlocking);
+        fs = g_free_stream[e->device];
+    }
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        for (auto& u : e->uses) {
+            cudaStreamWaitEvent(fs, u.second, 0);
+            cudaEventDestroy(u.second);
+        }
+        e->uses.clear();
+    }
+    if (e->lambda) cudaFreeAsync(e->lambda, fs);
+    if (e->s64) cudaFreeAsync(e->s64, fs);
+    if (e->s32) cudaFreeAsync(e->s32, fs);
     cudaSetDevice(prev);
     delete e;
     return CF_OK;
@@ -150,6 +209,7 @@ extern "C" cf_status cf_embedding_lambda(const cf_embedding* e, double* dst, cf_
     if (!e || !dst) return fail(CF_ERR_ARG, "NULL argument");
     CF_CUDA(cudaMemcpyAsync(dst, e->lambda, sizeof(double) * (size_t)e->grid.mtotal,
                             cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+    record_use(const_cast<cf_embedding*>(e), (cudaStream_t)s);
     return CF_OK;
 }
 
@@ -168,6 +228,7 @@ extern "C" cf_status cf_embedding_sqrt_lambda(const cf_embedding* e, double* dst
     const int blocks = (int)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256);
     k_sqrt_lambda_plus<<<blocks, 256, 0, (cudaStream_t)s>>>(e->lambda, e->tau, dst, total);
     CF_CHECK_LAUNCH();
+    record_use(const_cast<cf_embedding*>(e), (cudaStream_t)s);
     return CF_OK;
 }
 

@@ -16,7 +16,7 @@ namespace cf {
 // one-dimensional grid the fields (and counts) directly.
 // --------------------------------------------------------------------------
 template <typename T, int L>
-__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS)
+__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS, RowsCfg<T, L>::MINB)
     k_sample_rows(const T* __restrict__ s, T amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
                   long long nrows, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
                   const C2<T>* __restrict__ tw) {
@@ -122,6 +122,7 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
     const int chunk = pick_chunk(g, elem, R, ws_bytes);
     if (chunk < 1) return fail(CF_ERR_NOMEM, "workspace of %zu bytes holds no realization (%zu needed)", ws_bytes,
                                per_realization_bytes(g, elem));
+    if (sizeof(T) == 8) CF_TRY(ensure_s64(const_cast<cf_embedding*>(e), st));
     const T* s = sizeof(T) == 4 ? (const T*)(const void*)e->s32 : (const T*)(const void*)e->s64;
     const long long cells = g.ncell;
     const int d = g.ndim;
@@ -161,6 +162,7 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
             CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st)));
         }
     }
+    record_use(const_cast<cf_embedding*>(e), st);
     return CF_OK;
 }
 

@@ -273,22 +273,25 @@ def test_power_spectrum_parity(orc, n, nbins, kind, dt):
     assert np.allclose(cov.cpu().numpy(), oc, rtol=10 * tol, atol=10 * tol * np.abs(oc).max())
 
 
-def test_power_spectrum_counts_parity(orc):
-    n = (64, 64)
-    F = 6
-    f = W.survey_mask(n, seed=51)
+@pytest.mark.parametrize("n,F,masked", [((64, 64), 6, True), ((64, 64), 6, False), ((16, 16, 16), 5, True),
+                                         ((32, 32), 5, False)])
+def test_power_spectrum_counts_parity(orc, n, F, masked):
+    f = W.survey_mask(n, seed=51) if masked else np.ones(n, dtype=np.float32)
     counts = np.random.default_rng(52).poisson(3.0 * f, size=(F,) + n).astype(np.int32)
     g = cf.make_grid(n)
-    bins = cf.make_bins(16)
+    nb = 16 if len(n) == 2 else 8
+    bins = cf.make_bins(nb)
     wsb = cf.cf_power_spectrum_workspace_size(g, F, bins, cf.CF_F32)
     ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
-    pk = torch.empty((F, 16), dtype=torch.float64, device=DEV)
-    nm = torch.empty(16, dtype=torch.int64, device=DEV)
+    pk = torch.empty((F, nb), dtype=torch.float64, device=DEV)
+    nm = torch.empty(nb, dtype=torch.int64, device=DEV)
+    mean = torch.empty(nb, dtype=torch.float64, device=DEV)
     ct = torch.from_numpy(counts).to(DEV)
-    ft = torch.from_numpy(f).to(DEV)
-    cf.cf_power_spectrum_counts(ct, ft, g, F, bins, pk, nm, None, None, ws, wsb)
+    ft = torch.from_numpy(f).to(DEV) if masked else None
+    cf.cf_power_spectrum_counts(ct, ft, g, F, bins, pk, nm, mean, None, ws, wsb)
     torch.cuda.synchronize()
-    dg = orc.counts_to_delta(counts.reshape(F, -1), f.ravel().astype(np.float64)).reshape((F,) + n)
-    opk, onm = orc.power_spectrum(dg, n, orc.bin_edges(0, 16, 0.0, 32.0))
+    dg = orc.counts_to_delta(counts.reshape(F, -1), f.ravel().astype(np.float64) if masked else None)
+    opk, onm = orc.power_spectrum(dg.reshape((F,) + n), n, orc.bin_edges(0, nb, 0.0, n[0] / 2))
     assert np.array_equal(nm.cpu().numpy(), onm)
-    assert np.allclose(pk.cpu().numpy(), opk, rtol=2e-5)
+    assert np.allclose(pk.cpu().numpy(), opk, rtol=2e-5, atol=1e-7 * opk.max())
+    assert np.allclose(mean.cpu().numpy(), opk.mean(0), rtol=2e-5)
