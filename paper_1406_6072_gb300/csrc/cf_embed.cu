@@ -171,9 +171,14 @@ __global__ void __launch_bounds__(kRedThreads)
         s32[i] = sqrtf((float)(lp * inv_total));
     }
     neg = block_sum(neg, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = neg;
-    if (nneg) atomicAdd(&counts[0], nneg);
-    if (nzero) atomicAdd(&counts[1], nzero);
+    // counts are exact in binary64 (< 2^53): reduce per block, one atomic each
+    const double bneg = block_sum((double)nneg, sh);
+    const double bzero = block_sum((double)nzero, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = neg;
+        if (bneg > 0.0) atomicAdd(&counts[0], (unsigned long long)bneg);
+        if (bzero > 0.0) atomicAdd(&counts[1], (unsigned long long)bzero);
+    }
 }
 
 __global__ void __launch_bounds__(kRedThreads)

@@ -28,7 +28,7 @@ struct Edges {
 
 enum { PK_FLOAT = 0, PK_DOUBLE = 1, PK_COUNTS = 2, PK_MASK = 3 };
 
-__global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int* __restrict__ bin_of) {
+__global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int16_t* __restrict__ bin_of) {
     for (long long k2 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k2 <= k2max;
          k2 += (long long)gridDim.x * blockDim.x) {
         int b = -1;
@@ -39,7 +39,7 @@ __global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int* __restr
                 while (!(kn < ed.e[b + 1])) ++b;
             }
         }
-        bin_of[k2] = b;
+        bin_of[k2] = (int16_t)b;
     }
 }
 
@@ -134,70 +134,121 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
     }
 }
 
-// Last pass: FFT along axis 0, |X|^2 with mirror weights, binned.  With a
-// mask spectrum (count maps on a masked survey) the cross term
-// Re(X conj I) is binned as well.  The first field of a call also counts the
-// modes per bin and, with a mask, bins |I|^2.
+// Modes per bin over the full grid, counted on the half spectrum with the
+// mirror weights; with a mask spectrum also sum w |DFT I|^2 per bin.
+template <typename T>
+__global__ void k_pk_nmodes(long long n0, long long n_mid, long long H, long long n_last,
+                            const int16_t* __restrict__ bin_of, long long k2max, int nbins,
+                            const C2<T>* __restrict__ mask_spec, unsigned long long* __restrict__ nmodes,
+                            double* __restrict__ mask_power) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned int* scount = reinterpret_cast<unsigned int*>(smraw);
+    double* smask = reinterpret_cast<double*>(scount + ((nbins + 1) & ~1));
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        scount[b] = 0u;
+        smask[b] = 0.0;
+    }
+    __syncthreads();
+    const long long inner = n_mid * H;
+    const long long total = n0 * inner;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long p = t / inner, i = t - p * inner;
+        const long long il = i % H, imid = i / H;
+        const long long s0 = signed_mode(p, n0), sm = signed_mode(imid, n_mid);
+        const long long k2 = s0 * s0 + sm * sm + il * il;
+        const int b = k2 <= k2max ? bin_of[k2] : -1;
+        if (b < 0) continue;
+        const unsigned int w = (il == 0 || 2 * il == n_last) ? 1u : 2u;
+        atomicAdd(&scount[b], w);
+        if (mask_spec) {
+            const C2<T> m = mask_spec[t];
+            atomicAdd(&smask[b], (double)w * ((double)m.x * m.x + (double)m.y * m.y));
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        if (scount[b]) atomicAdd(&nmodes[b], (unsigned long long)scount[b]);
+        if (mask_spec && smask[b] != 0.0) atomicAdd(&mask_power[b], smask[b]);
+    }
+}
+
+// Last pass: FFT along axis 0, then binning from shared memory.  Thread
+// (column ln, j) walks the E consecutive k0 of its column; neighbouring k0
+// mostly share a bin, so the weighted powers are summed in registers and
+// added to the shared bins once per run of equal bins.  With a mask
+// spectrum the cross term Re(X conj I) is binned the same way.
 template <typename T, int L>
 __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
     k_pk_cols(const C2<T>* __restrict__ in, long long inner, long long H, long long n_mid, long long n_last,
-              const int* __restrict__ bin_of, long long k2max, int nbins, double* __restrict__ acc,
-              double* __restrict__ acc_cross, const C2<T>* __restrict__ mask_spec, unsigned long long* __restrict__ nmodes,
-              double* __restrict__ mask_power, long long f0, const C2<T>* __restrict__ tw) {
+              const int16_t* __restrict__ bin_of, long long k2max, int nbins, double* __restrict__ acc,
+              double* __restrict__ acc_cross, const C2<T>* __restrict__ mask_spec, long long f0,
+              const C2<T>* __restrict__ tw) {
     using Cfg = ColsCfg<T, L>;
     using G = typename Cfg::G;
+    constexpr int E = G::E;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
     T* sbin = reinterpret_cast<T*>(sm + (size_t)Cfg::C * G::PADDED);
     T* scross = sbin + nbins;
-    T* smask = scross + nbins;
-    unsigned int* scount = reinterpret_cast<unsigned int*>(smask + nbins);
-    const bool first = (f0 == 0 && blockIdx.y == 0);
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
         sbin[b] = (T)0;
         scross[b] = (T)0;
-        smask[b] = (T)0;
-        scount[b] = 0u;
     }
-    __syncthreads();
     const int ln = threadIdx.x % Cfg::C;
     const int j = threadIdx.x / Cfg::C;
     const long long i = (long long)blockIdx.x * Cfg::C + ln;
     const long long o = blockIdx.y;
     const bool valid = i < inner;
     const C2<T>* src = in + (size_t)o * L * (size_t)inner + (size_t)(valid ? i : 0);
-    C2<T> v[G::E];
+    C2<T> v[E];
 #pragma unroll
-    for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)inner];
-    const long long il = i % H;          // k_last index in [0, n_last/2]
-    const long long imid = i / H;        // middle-axis index (3D) or 0
-    const long long smid = signed_mode(imid, n_mid);
-    const int wi = (il == 0 || 2 * il == n_last) ? 1 : 2;
-    const T w = (T)wi;
-    auto sink = [&](int, int p, C2<T> val) {
-        if (!valid) return;
-        const long long s0 = signed_mode(p, L);
-        const long long k2 = s0 * s0 + smid * smid + il * il;
-        const int b = k2 <= k2max ? bin_of[k2] : -1;
-        if (b < 0) return;
-        atomicAdd(&sbin[b], w * (val.x * val.x + val.y * val.y));
-        if (mask_spec) {
-            const C2<T> mb = mask_spec[(size_t)p * inner + i];
-            atomicAdd(&scross[b], w * (val.x * mb.x + val.y * mb.y));
-            if (first) atomicAdd(&smask[b], w * (mb.x * mb.x + mb.y * mb.y));
+    for (int q = 0; q < E; ++q) v[q] = src[(size_t)(j + q * (L / E)) * (size_t)inner];
+    ColLayout<E, Cfg::C> lay;
+    auto sink = [&](int lnn, int p, C2<T> val) { sm[lay(lnn, p)] = val; };
+    line_fft<T, L, -1, L, ColLayout<E, Cfg::C>, decltype(sink), true>(sm, lay, ln, j, v, tw, sink);
+    __syncthreads();
+    if (valid) {
+        const long long il = i % H;
+        const long long smid = signed_mode(i / H, n_mid);
+        const long long c2 = smid * smid + il * il;
+        const T w = (il == 0 || 2 * il == n_last) ? (T)1 : (T)2;
+        int cur = -1;
+        T run = (T)0, runx = (T)0;
+#pragma unroll 4
+        for (int t = 0; t < E; ++t) {
+            const int p = j * E + t;
+            const C2<T> x = sm[lay(ln, p)];
+            const long long s0 = signed_mode(p, L);
+            const long long k2 = s0 * s0 + c2;
+            const int b = k2 <= k2max ? (int)bin_of[k2] : -1;
+            if (b != cur) {
+                if (cur >= 0) {
+                    atomicAdd(&sbin[cur], run);
+                    if (mask_spec) atomicAdd(&scross[cur], runx);
+                }
+                cur = b;
+                run = (T)0;
+                runx = (T)0;
+            }
+            if (b >= 0) {
+                run += w * (x.x * x.x + x.y * x.y);
+                if (mask_spec) {
+                    const C2<T> m = mask_spec[(size_t)p * inner + i];
+                    runx += w * (x.x * m.x + x.y * m.y);
+                }
+            }
         }
-        if (first) atomicAdd(&scount[b], (unsigned int)wi);
-    };
-    line_fft<T, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+        if (cur >= 0) {
+            atomicAdd(&sbin[cur], run);
+            if (mask_spec) atomicAdd(&scross[cur], runx);
+        }
+    }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
         const size_t at = (size_t)(f0 + o) * nbins + b;
         if (sbin[b] != (T)0) atomicAdd(&acc[at], (double)sbin[b]);
         if (mask_spec && scross[b] != (T)0) atomicAdd(&acc_cross[at], (double)scross[b]);
-        if (first) {
-            if (scount[b]) atomicAdd(&nmodes[b], (unsigned long long)scount[b]);
-            if (mask_spec && smask[b] != (T)0) atomicAdd(&mask_power[b], (double)smask[b]);
-        }
     }
 }
 
@@ -345,7 +396,7 @@ static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins
         o = align256(o + bytes);
         return at;
     };
-    P->off_bin = take(sizeof(int) * (size_t)(P->k2max + 1));
+    P->off_bin = take(sizeof(int16_t) * (size_t)(P->k2max + 1));
     P->off_nmodes = take(sizeof(unsigned long long) * P->nbins);
     P->off_acc = take(sizeof(double) * (size_t)nfields * P->nbins);
     P->off_cross = take(sizeof(double) * (size_t)nfields * P->nbins);
@@ -374,17 +425,17 @@ static cf_status launch_pk_rows(const void* fields, int kind, const float* f, un
 }
 
 template <typename T, int L>
-static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mid, const PkPlan& P, const int* bin_of,
-                                double* acc, double* cross, const C2<T>* mask_spec, unsigned long long* nmodes,
-                                double* mpow, long long f0, long long nchunk, cudaStream_t s) {
+static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mid, const PkPlan& P,
+                                const int16_t* bin_of, double* acc, double* cross, const C2<T>* mask_spec, long long f0,
+                                long long nchunk, cudaStream_t s) {
     using Cfg = ColsCfg<T, L>;
     auto kern = k_pk_cols<T, L>;
-    const size_t smem = Cfg::SMEM + (3 * sizeof(T) + sizeof(unsigned int)) * (size_t)P.nbins;
+    const size_t smem = Cfg::SMEM + 2 * sizeof(T) * (size_t)P.nbins;
     CF_TRY(prepare_smem(kern, smem));
     dim3 grid((unsigned)((inner + Cfg::C - 1) / Cfg::C), (unsigned)nchunk);
     ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_cols_f32" : "pk_cols_f64", L);
     kern<<<grid, Cfg::THREADS, smem, s>>>(in, inner, P.H, n_mid, P.g.n[P.g.ndim - 1], bin_of, P.k2max, P.nbins, acc,
-                                          cross, mask_spec, nmodes, mpow, f0, twiddles<T>());
+                                          cross, mask_spec, f0, twiddles<T>());
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
@@ -402,7 +453,7 @@ template <typename T>
 static cf_status pk_impl(const void* fields, int kind, const float* f, const PkPlan& P, long long nfields,
                          double* pk_out, int64_t* nmodes_out, double* mean, double* cov, char* ws, cudaStream_t s) {
     const GridInfo& g = P.g;
-    int* bin_of = (int*)(ws + P.off_bin);
+    int16_t* bin_of = (int16_t*)(ws + P.off_bin);
     unsigned long long* nmodes = (unsigned long long*)(ws + P.off_nmodes);
     double* acc = (double*)(ws + P.off_acc);
     double* cross = (double*)(ws + P.off_cross);
@@ -432,6 +483,13 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
         FieldEpi<T> none{};
         CF_TRY((launch_cols<T, -1, 0>(g.n[0], mask_spec, 1, inner, mask_spec, 0, none, s)));
     }
+    {
+        ScopedKernelTimer kt(s, "pk_setup");
+        const size_t smem = (size_t)((P.nbins + 1) & ~1) * sizeof(unsigned int) + (size_t)P.nbins * sizeof(double);
+        k_pk_nmodes<T><<<grid_blocks(g.n[0] * inner, 256, 256), 256, smem, s>>>(
+            g.n[0], n_mid, P.H, nl, bin_of, P.k2max, P.nbins, masked ? mask_spec : nullptr, nmodes, mpow);
+    }
+    CF_CHECK_LAUNCH();
     for (long long f0 = 0; f0 < nfields; f0 += P.chunk) {
         const long long nc = (nfields - f0) < P.chunk ? (nfields - f0) : P.chunk;
         CF_TRY(dispatch_line(nl, [&](auto Lc) -> cf_status {
@@ -440,7 +498,7 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
         CF_TRY(pk_middle_axis<T>(P, half, nc, s));
         CF_TRY(dispatch_line(g.n[0], [&](auto Lc) -> cf_status {
             return launch_pk_cols<T, decltype(Lc)::value>(half, inner, n_mid, P, bin_of, acc, masked ? cross : nullptr,
-                                                          masked ? mask_spec : nullptr, nmodes, mpow, f0, nc, s);
+                                                          masked ? mask_spec : nullptr, f0, nc, s);
         }));
     }
     double volfac = 1.0;
