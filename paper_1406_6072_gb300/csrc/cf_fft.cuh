@@ -38,11 +38,11 @@ struct FftE<double> {
     static constexpr int value = CF_E64;
 };
 
-template <typename T, int L>
+template <typename T, int L, int EMAX = FftE<T>::value>
 struct LineGeom {
-    static constexpr int E = L < FftE<T>::value ? L : FftE<T>::value;  // points per thread
-    static constexpr int TL = L / E;                                   // threads per line
-    static constexpr int PADDED = L + L / E;                           // padded line length
+    static constexpr int E = L < EMAX ? L : EMAX;  // points per thread
+    static constexpr int TL = L / E;               // threads per line
+    static constexpr int PADDED = L + L / E;       // padded line length
 };
 
 // padded shared-memory slot of point p
@@ -208,11 +208,10 @@ __device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, i
 // Full transform of a line whose first-stage inputs v[q] = x[j + q*L/E] are
 // already in registers.  Every thread of the CTA must call this (it contains
 // __syncthreads); threads without a valid line pass dummy data.
-template <typename T, int L, int SIGN, int KEEP, class Lay, class Out, bool SYNC_OUT = false>
-__device__ __forceinline__ void line_fft(C2<T>* sm, const Lay& lay, int line, int j,
-                                         C2<T> (&v)[LineGeom<T, L>::E], const C2<T>* __restrict__ tw,
-                                         Out& out) {
-    fft_stage<T, L, LineGeom<T, L>::E, SIGN, KEEP, 1, SYNC_OUT>(sm, lay, line, j, v, tw, out);
+template <typename T, int L, int SIGN, int KEEP, bool SYNC_OUT = false, int E, class Lay, class Out>
+__device__ __forceinline__ void line_fft(C2<T>* sm, const Lay& lay, int line, int j, C2<T> (&v)[E],
+                                         const C2<T>* __restrict__ tw, Out& out) {
+    fft_stage<T, L, E, SIGN, KEEP, 1, SYNC_OUT>(sm, lay, line, j, v, tw, out);
 }
 
 }  // namespace cf

@@ -57,29 +57,50 @@ struct FieldEpi {
 // out[outer][KEEP][inner] (in place allowed when KEEP == L); mode 1: field
 // epilogue with realization = outer index and cell = point*inner + i.
 // --------------------------------------------------------------------------
-// Build-time tunables of the CTA shapes: threads per CTA and the minimum
-// number of resident CTAs per SM given to the register allocator.
+// Build-time tunables of the CTA shapes, per kernel family: binary32 points
+// per thread (E), threads per CTA, and the minimum number of resident CTAs per
+// SM given to the register allocator.  Families: COLS (column passes:
+// sampler, embedding, power spectrum 3D middle axis), ROWS (in-place row
+// transforms), SROWS (noise-fused sampler rows), PKR / PKC (power spectrum
+// row and binning passes).
+#ifndef CF_COLS_E
+#define CF_COLS_E 8
+#endif
 #ifndef CF_COLS_THREADS
 #define CF_COLS_THREADS 256
 #endif
 #ifndef CF_COLS_MINB
-#define CF_COLS_MINB 1
+#define CF_COLS_MINB 4
+#endif
+#ifndef CF_ROWS_E
+#define CF_ROWS_E 8
 #endif
 #ifndef CF_ROWS_THREADS
 #define CF_ROWS_THREADS 256
 #endif
 #ifndef CF_ROWS_MINB
-#define CF_ROWS_MINB 1
+#define CF_ROWS_MINB 4
 #endif
 
+// binary32 uses the family's E, binary64 the global CF_E64
+template <typename T, int E32>
+struct FamilyE {
+    static constexpr int value = sizeof(T) == 4 ? E32 : CF_E64;
+};
+
+template <typename T, int L, int E32, int THREADS_, int MINB_>
+struct TileCfg {
+    using G = LineGeom<T, L, FamilyE<T, E32>::value>;
+    // lines per CTA
+    static constexpr int LINES = G::TL >= THREADS_ ? 1 : ((THREADS_ / G::TL) > 32 ? 32 : (THREADS_ / G::TL));
+    static constexpr int THREADS = LINES * G::TL;
+    static constexpr int MINB = THREADS * MINB_ <= 2048 ? MINB_ : (2048 / THREADS > 0 ? 2048 / THREADS : 1);
+    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)LINES * (size_t)G::PADDED;
+};
+
 template <typename T, int L>
-struct ColsCfg {
-    using G = LineGeom<T, L>;
-    static constexpr int C =
-        G::TL >= CF_COLS_THREADS ? 1 : ((CF_COLS_THREADS / G::TL) > 32 ? 32 : (CF_COLS_THREADS / G::TL));
-    static constexpr int THREADS = C * G::TL;
-    static constexpr int MINB = THREADS * CF_COLS_MINB <= 2048 ? CF_COLS_MINB : 1;
-    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)C * (size_t)G::PADDED;
+struct ColsCfg : TileCfg<T, L, CF_COLS_E, CF_COLS_THREADS, CF_COLS_MINB> {
+    static constexpr int C = TileCfg<T, L, CF_COLS_E, CF_COLS_THREADS, CF_COLS_MINB>::LINES;
 };
 
 template <typename T, int L, int SIGN, int KEEP_HALF>
@@ -114,12 +135,8 @@ __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
 // Row pass on contiguous lines: in-place complex FFT of rows of length L.
 // --------------------------------------------------------------------------
 template <typename T, int L>
-struct RowsCfg {
-    using G = LineGeom<T, L>;
-    static constexpr int ROWS = G::TL >= CF_ROWS_THREADS ? 1 : CF_ROWS_THREADS / G::TL;
-    static constexpr int THREADS = ROWS * G::TL;
-    static constexpr int MINB = THREADS * CF_ROWS_MINB <= 2048 ? CF_ROWS_MINB : 1;
-    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
+struct RowsCfg : TileCfg<T, L, CF_ROWS_E, CF_ROWS_THREADS, CF_ROWS_MINB> {
+    static constexpr int ROWS = TileCfg<T, L, CF_ROWS_E, CF_ROWS_THREADS, CF_ROWS_MINB>::LINES;
 };
 
 template <typename T, int L, int SIGN>

@@ -45,14 +45,33 @@ __global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int16_t* __r
 
 __device__ __forceinline__ long long signed_mode(long long i, long long n) { return i <= n / 2 ? i : i - n; }
 
+#ifndef CF_PKR_E
+#define CF_PKR_E 8
+#endif
+#ifndef CF_PKR_THREADS
+#define CF_PKR_THREADS 256
+#endif
+#ifndef CF_PKR_MINB
+#define CF_PKR_MINB 4
+#endif
+#ifndef CF_PKC_E
+#define CF_PKC_E 8
+#endif
+#ifndef CF_PKC_THREADS
+#define CF_PKC_THREADS 256
+#endif
+#ifndef CF_PKC_MINB
+#define CF_PKC_MINB 4
+#endif
+
 // Pass 1: pairs of real fields along the last axis -> two half spectra.
 template <typename T, int L>
-struct PkRowsCfg {
-    using G = LineGeom<T, L>;
-    static constexpr int ROWS = G::TL >= CF_ROWS_THREADS ? 1 : CF_ROWS_THREADS / G::TL;
-    static constexpr int THREADS = ROWS * G::TL;
-    static constexpr int MINB = THREADS * CF_ROWS_MINB <= 2048 ? CF_ROWS_MINB : 1;
-    static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)ROWS * (size_t)G::PADDED;
+struct PkRowsCfg : TileCfg<T, L, CF_PKR_E, CF_PKR_THREADS, CF_PKR_MINB> {
+    static constexpr int ROWS = TileCfg<T, L, CF_PKR_E, CF_PKR_THREADS, CF_PKR_MINB>::LINES;
+};
+template <typename T, int L>
+struct PkColsCfg : TileCfg<T, L, CF_PKC_E, CF_PKC_THREADS, CF_PKC_MINB> {
+    static constexpr int C = TileCfg<T, L, CF_PKC_E, CF_PKC_THREADS, CF_PKC_MINB>::LINES;
 };
 
 template <typename T, int L>
@@ -119,7 +138,7 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
     RowLayout<E, G::PADDED> lay;
     // the spectrum of the line goes back into the exchange buffer
     auto sink = [&](int ln, int p, C2<T> val) { sm[lay(ln, p)] = val; };
-    line_fft<T, L, -1, L, RowLayout<E, G::PADDED>, decltype(sink), true>(sm, lay, line, j, v, tw, sink);
+    line_fft<T, L, -1, L, true>(sm, lay, line, j, v, tw, sink);
     __syncthreads();
     if (!valid) return;
     const long long la = fa - f0, lb = fb - f0;
@@ -179,12 +198,12 @@ __global__ void k_pk_nmodes(long long n0, long long n_mid, long long H, long lon
 // added to the shared bins once per run of equal bins.  With a mask
 // spectrum the cross term Re(X conj I) is binned the same way.
 template <typename T, int L>
-__global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
+__global__ void __launch_bounds__(PkColsCfg<T, L>::THREADS, PkColsCfg<T, L>::MINB)
     k_pk_cols(const C2<T>* __restrict__ in, long long inner, long long H, long long n_mid, long long n_last,
               const int16_t* __restrict__ bin_of, long long k2max, int nbins, double* __restrict__ acc,
               double* __restrict__ acc_cross, const C2<T>* __restrict__ mask_spec, long long f0,
               const C2<T>* __restrict__ tw) {
-    using Cfg = ColsCfg<T, L>;
+    using Cfg = PkColsCfg<T, L>;
     using G = typename Cfg::G;
     constexpr int E = G::E;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -206,7 +225,7 @@ __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
     for (int q = 0; q < E; ++q) v[q] = src[(size_t)(j + q * (L / E)) * (size_t)inner];
     ColLayout<E, Cfg::C> lay;
     auto sink = [&](int lnn, int p, C2<T> val) { sm[lay(lnn, p)] = val; };
-    line_fft<T, L, -1, L, ColLayout<E, Cfg::C>, decltype(sink), true>(sm, lay, ln, j, v, tw, sink);
+    line_fft<T, L, -1, L, true>(sm, lay, ln, j, v, tw, sink);
     __syncthreads();
     if (valid) {
         const long long il = i % H;
@@ -428,7 +447,7 @@ template <typename T, int L>
 static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mid, const PkPlan& P,
                                 const int16_t* bin_of, double* acc, double* cross, const C2<T>* mask_spec, long long f0,
                                 long long nchunk, cudaStream_t s) {
-    using Cfg = ColsCfg<T, L>;
+    using Cfg = PkColsCfg<T, L>;
     auto kern = k_pk_cols<T, L>;
     const size_t smem = Cfg::SMEM + 2 * sizeof(T) * (size_t)P.nbins;
     CF_TRY(prepare_smem(kern, smem));

@@ -8,6 +8,21 @@
 
 namespace cf {
 
+#ifndef CF_SROWS_E
+#define CF_SROWS_E 8
+#endif
+#ifndef CF_SROWS_THREADS
+#define CF_SROWS_THREADS 128
+#endif
+#ifndef CF_SROWS_MINB
+#define CF_SROWS_MINB 8
+#endif
+
+template <typename T, int L>
+struct SRowsCfg : TileCfg<T, L, CF_SROWS_E, CF_SROWS_THREADS, CF_SROWS_MINB> {
+    static constexpr int ROWS = TileCfg<T, L, CF_SROWS_E, CF_SROWS_THREADS, CF_SROWS_MINB>::LINES;
+};
+
 // --------------------------------------------------------------------------
 // Pass 1: rows along the last axis.  Each thread draws the noise of its E
 // first-stage points (Philox stream 0), scales it by sqrt(lambda+)/sqrt(M^d),
@@ -16,11 +31,11 @@ namespace cf {
 // one-dimensional grid the fields (and counts) directly.
 // --------------------------------------------------------------------------
 template <typename T, int L>
-__global__ void __launch_bounds__(RowsCfg<T, L>::THREADS, RowsCfg<T, L>::MINB)
+__global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     k_sample_rows(const T* __restrict__ s, T amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
                   long long nrows, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
                   const C2<T>* __restrict__ tw) {
-    using Cfg = RowsCfg<T, L>;
+    using Cfg = SRowsCfg<T, L>;
     using G = typename Cfg::G;
     constexpr int E = G::E;
     constexpr int STEP = L / E;
@@ -71,7 +86,7 @@ static cf_status launch_sample_rows(long long L, const T* s, T amp_scale, uint64
                                     cudaStream_t st) {
     return dispatch_line(L, [&](auto Lc) -> cf_status {
         constexpr int LL = decltype(Lc)::value;
-        using Cfg = RowsCfg<T, LL>;
+        using Cfg = SRowsCfg<T, LL>;
         auto kern = k_sample_rows<T, LL>;
         CF_TRY(prepare_smem(kern, Cfg::SMEM));
         dim3 grid((unsigned)((nrows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)chunk);
