@@ -26,6 +26,7 @@ struct FieldEpi {
     double half_sigma2;
     float half_sigma2_f;
     double nbar;
+    float nbar_f;
     uint32_t pkey0, pkey1;
     uint32_t r0;        // global index of the chunk's first realization
     long long cells;
@@ -40,9 +41,9 @@ struct FieldEpi {
             const float g0 = (float)w.x, g1 = (float)w.y;
             const uint4 x = poisson_words((unsigned long long)cell, r0 + (uint32_t)rl, pkey0, pkey1);
             const float fi = f ? f[cell] : 1.0f;
-            counts[base] = poisson_count_fast(g0, half_sigma2, half_sigma2_f, nbar, fi, bits53(x.x, x.y));
+            counts[base] = poisson_count_fast(g0, half_sigma2, half_sigma2_f, nbar, nbar_f, fi, bits53(x.x, x.y));
             counts[base + cells] =
-                poisson_count_fast(g1, half_sigma2, half_sigma2_f, nbar, fi, bits53(x.z, x.w));
+                poisson_count_fast(g1, half_sigma2, half_sigma2_f, nbar, nbar_f, fi, bits53(x.z, x.w));
             if (delta) {
                 delta[base] = expf(g0 - half_sigma2_f) - 1.0f;
                 delta[base + cells] = expf(g1 - half_sigma2_f) - 1.0f;

@@ -21,7 +21,7 @@ __global__ void k_lognormal_poisson(const T* __restrict__ G, long long cells, lo
         const T g = G[idx];
         int n;
         if constexpr (sizeof(T) == 4) {
-            n = poisson_count_fast(g, half_sigma2, half_sigma2_f, nbar, fi, ub);
+            n = poisson_count_fast(g, half_sigma2, half_sigma2_f, nbar, (float)nbar, fi, ub);
             if (delta) delta[idx] = expf(g - half_sigma2_f) - 1.0f;
         } else {
             const double rho = exp(g - half_sigma2);

@@ -16,6 +16,9 @@
 // against the mask spectrum DFT I, and the final pass combines them.
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "cf_kernels.cuh"
 
 namespace cf {
@@ -49,13 +52,13 @@ __device__ __forceinline__ long long signed_mode(long long i, long long n) { ret
 #define CF_PKR_E 8
 #endif
 #ifndef CF_PKR_THREADS
-#define CF_PKR_THREADS 256
+#define CF_PKR_THREADS 128
 #endif
 #ifndef CF_PKR_MINB
-#define CF_PKR_MINB 4
+#define CF_PKR_MINB 8
 #endif
 #ifndef CF_PKC_E
-#define CF_PKC_E 8
+#define CF_PKC_E 16
 #endif
 #ifndef CF_PKC_THREADS
 #define CF_PKC_THREADS 256
@@ -179,7 +182,7 @@ __global__ void k_pk_nmodes(long long n0, long long n_mid, long long H, long lon
         const int b = k2 <= k2max ? bin_of[k2] : -1;
         if (b < 0) continue;
         const unsigned int w = (il == 0 || 2 * il == n_last) ? 1u : 2u;
-        atomicAdd(&scount[b], w);
+        if (nmodes) atomicAdd(&scount[b], w);
         if (mask_spec) {
             const C2<T> m = mask_spec[t];
             atomicAdd(&smask[b], (double)w * ((double)m.x * m.x + (double)m.y * m.y));
@@ -187,7 +190,7 @@ __global__ void k_pk_nmodes(long long n0, long long n_mid, long long H, long lon
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-        if (scount[b]) atomicAdd(&nmodes[b], (unsigned long long)scount[b]);
+        if (nmodes && scount[b]) atomicAdd(&nmodes[b], (unsigned long long)scount[b]);
         if (mask_spec && smask[b] != 0.0) atomicAdd(&mask_power[b], smask[b]);
     }
 }
@@ -428,6 +431,74 @@ static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins
     return CF_OK;
 }
 
+// Bin tables and mode counts depend only on (device, grid, edges): they are
+// built once per key on the first call's stream and kept for the life of the
+// process (at most kBinCacheMax keys; beyond that they are rebuilt per call
+// in the workspace).  Later calls on other streams wait on the build event.
+struct BinCacheEntry {
+    int device;
+    int ndim;
+    long long n0;
+    int nbins;
+    std::vector<double> edges;
+    int16_t* bin_of;
+    unsigned long long* nmodes;
+    cudaEvent_t ready;
+};
+constexpr size_t kBinCacheMax = 32;
+static std::mutex g_bin_mu;
+static std::vector<BinCacheEntry> g_bin_cache;
+
+static cf_status build_bins(const PkPlan& P, int16_t* bin_of, unsigned long long* nmodes, cudaStream_t s) {
+    const GridInfo& g = P.g;
+    const int d = g.ndim;
+    const long long n_mid = d == 3 ? g.n[1] : 1;
+    const long long inner = n_mid * P.H;
+    k_pk_bintable<<<grid_blocks(P.k2max + 1, 256, 1024), 256, 0, s>>>(P.edges, P.nbins, P.k2max, bin_of);
+    CF_CUDA(cudaMemsetAsync(nmodes, 0, sizeof(unsigned long long) * P.nbins, s));
+    const size_t smem = (size_t)((P.nbins + 1) & ~1) * sizeof(unsigned int) + (size_t)P.nbins * sizeof(double);
+    k_pk_nmodes<float><<<grid_blocks(g.n[0] * inner, 256, 256), 256, smem, s>>>(
+        g.n[0], n_mid, P.H, g.n[d - 1], bin_of, P.k2max, P.nbins, nullptr, nmodes, nullptr);
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+// Returns the cached tables for P (building them on stream s if needed), or
+// the workspace copies when the cache is full.
+static cf_status get_bins(const PkPlan& P, char* ws, cudaStream_t s, const int16_t** bin_of,
+                          const unsigned long long** nmodes) {
+    int dev = 0;
+    CF_CUDA(cudaGetDevice(&dev));
+    std::vector<double> edges(P.edges.e, P.edges.e + P.nbins + 1);
+    std::lock_guard<std::mutex> lk(g_bin_mu);
+    for (auto& c : g_bin_cache) {
+        if (c.device == dev && c.ndim == P.g.ndim && c.n0 == P.g.n[0] && c.nbins == P.nbins && c.edges == edges) {
+            CF_CUDA(cudaStreamWaitEvent(s, c.ready, 0));
+            *bin_of = c.bin_of;
+            *nmodes = c.nmodes;
+            return CF_OK;
+        }
+    }
+    if (g_bin_cache.size() >= kBinCacheMax) {
+        int16_t* b = (int16_t*)(ws + P.off_bin);
+        unsigned long long* nm = (unsigned long long*)(ws + P.off_nmodes);
+        CF_TRY(build_bins(P, b, nm, s));
+        *bin_of = b;
+        *nmodes = nm;
+        return CF_OK;
+    }
+    BinCacheEntry c{dev, P.g.ndim, P.g.n[0], P.nbins, edges, nullptr, nullptr, nullptr};
+    CF_CUDA(cudaMalloc((void**)&c.bin_of, sizeof(int16_t) * (size_t)(P.k2max + 1)));
+    CF_CUDA(cudaMalloc((void**)&c.nmodes, sizeof(unsigned long long) * P.nbins));
+    CF_CUDA(cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming));
+    CF_TRY(build_bins(P, c.bin_of, c.nmodes, s));
+    CF_CUDA(cudaEventRecord(c.ready, s));
+    g_bin_cache.push_back(c);
+    *bin_of = c.bin_of;
+    *nmodes = c.nmodes;
+    return CF_OK;
+}
+
 template <typename T, int L>
 static cf_status launch_pk_rows(const void* fields, int kind, const float* f, unsigned long long* ntot,
                                 double* fsum, const PkPlan& P, long long nfields, long long f0, long long nchunk,
@@ -472,8 +543,8 @@ template <typename T>
 static cf_status pk_impl(const void* fields, int kind, const float* f, const PkPlan& P, long long nfields,
                          double* pk_out, int64_t* nmodes_out, double* mean, double* cov, char* ws, cudaStream_t s) {
     const GridInfo& g = P.g;
-    int16_t* bin_of = (int16_t*)(ws + P.off_bin);
-    unsigned long long* nmodes = (unsigned long long*)(ws + P.off_nmodes);
+    const int16_t* bin_of = nullptr;
+    const unsigned long long* nmodes = nullptr;
     double* acc = (double*)(ws + P.off_acc);
     double* cross = (double*)(ws + P.off_cross);
     double* mpow = (double*)(ws + P.off_mpow);
@@ -489,8 +560,9 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
     const long long n_mid = d == 3 ? g.n[1] : 1;
     {
         ScopedKernelTimer kt(s, "pk_setup");
-        k_pk_bintable<<<grid_blocks(P.k2max + 1, 256, 1024), 256, 0, s>>>(P.edges, P.nbins, P.k2max, bin_of);
-        CF_CUDA(cudaMemsetAsync(ws + P.off_nmodes, 0, P.off_half - P.off_nmodes, s));
+        CF_TRY(get_bins(P, ws, s, &bin_of, &nmodes));
+        // zero the accumulators (acc .. mask spectrum)
+        CF_CUDA(cudaMemsetAsync(ws + P.off_acc, 0, P.off_half - P.off_acc, s));
     }
     CF_CHECK_LAUNCH();
     if (masked) {
@@ -502,11 +574,11 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
         FieldEpi<T> none{};
         CF_TRY((launch_cols<T, -1, 0>(g.n[0], mask_spec, 1, inner, mask_spec, 0, none, s)));
     }
-    {
+    if (masked) {
         ScopedKernelTimer kt(s, "pk_setup");
         const size_t smem = (size_t)((P.nbins + 1) & ~1) * sizeof(unsigned int) + (size_t)P.nbins * sizeof(double);
         k_pk_nmodes<T><<<grid_blocks(g.n[0] * inner, 256, 256), 256, smem, s>>>(
-            g.n[0], n_mid, P.H, nl, bin_of, P.k2max, P.nbins, masked ? mask_spec : nullptr, nmodes, mpow);
+            g.n[0], n_mid, P.H, nl, bin_of, P.k2max, P.nbins, mask_spec, nullptr, mpow);
     }
     CF_CHECK_LAUNCH();
     for (long long f0 = 0; f0 < nfields; f0 += P.chunk) {

@@ -9,7 +9,7 @@
 namespace cf {
 
 #ifndef CF_SROWS_E
-#define CF_SROWS_E 8
+#define CF_SROWS_E 16
 #endif
 #ifndef CF_SROWS_THREADS
 #define CF_SROWS_THREADS 128
@@ -157,6 +157,7 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
             epi.half_sigma2 = 0.5 * lp->sigma2;
             epi.half_sigma2_f = (float)(0.5 * lp->sigma2);
             epi.nbar = lp->nbar;
+            epi.nbar_f = (float)lp->nbar;
             epi.pkey0 = (uint32_t)lp->seed;
             epi.pkey1 = (uint32_t)(lp->seed >> 32);
         }
