@@ -38,7 +38,7 @@ UNIT = "cells/s"
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
@@ -65,7 +65,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -112,28 +112,51 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------------- roofline
-def kernel_costs(wl, R, chunks):
-    """Algorithmic bytes per step of each kernel of the binary32 2D path.
+SMS, LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 
-    sample_rows: writes the pruned intermediate R*M0*N1 complex64 and reads
-    sqrt(lambda) (M0*M1 float32) once per launch; icols_fields_lp: reads the
-    intermediate, writes 2 fields (float32) + 2 count maps (int32) per
-    realization; pk_rows: reads F fields (4 B/cell), writes F half spectra
-    n*(n/2+1) complex64; pk_cols: reads the half spectra."""
+
+def kernel_costs(wl, R, chunks):
+    """Algorithmic bytes and operations per step of each kernel of the binary32
+    2D path (definitions in the design doc section 7; FMA = 1 op).
+
+    sample_rows: writes the pruned intermediate R*M0*N1 complex64, reads
+    sqrt(lambda) once per launch; 76 ops of noise per embedded cell plus the
+    row transforms.  icols_fields_lp: reads the intermediate, writes 2 fields
+    + 2 count maps per realization; column transforms plus the Poisson step.
+    pk_rows / pk_cols: fields in, half spectra out / in, for the Gaussian
+    fields and the count maps."""
     n0, n1 = wl.n
     m0, m1 = wl.m
     F = 2 * R
+    lg = lambda v: v.bit_length() - 1
     inter = R * m0 * n1 * 8
     half = F * n0 * (n1 // 2 + 1) * 8
+    nbar = wl.nbar or 0.0
     return {
-        "sample_rows_f32": inter + chunks * m0 * m1 * 4,
-        "icols_fields_lp_f32": inter + F * n0 * n1 * 8,
-        "pk_rows_f32": 2 * (F * n0 * n1 * 4 + half),   # Gaussian fields and count maps
-        "pk_cols_f32": 2 * half,
+        "sample_rows_f32": {"bytes": inter + chunks * m0 * m1 * 4,
+                            "ops": R * m0 * m1 * 76 + R * m0 * 4 * m1 * lg(m1)},
+        "icols_fields_lp_f32": {"bytes": inter + F * n0 * n1 * 8,
+                                "ops": R * n1 * 4 * m0 * lg(m0) + F * n0 * n1 * (30 + 10 + 4 * (nbar + 1))},
+        "pk_rows_f32": {"bytes": 2 * (F * n0 * n1 * 4 + half),
+                        "ops": 2 * (F // 2) * n0 * 4 * n1 * lg(n1)},
+        "pk_cols_f32": {"bytes": 2 * half, "ops": 2 * F * (n1 // 2 + 1) * (4 * n0 * lg(n0) + 8 * n0)},
     }
 
 
-def roofline(wl, R, timing, steps, hbm_peak, peak_kind):
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current version of that kernel."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dominant_kernel_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel") == kernel and d.get("current", False):
+            return d["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def roofline(wl, R, timing, steps, hbm_peak, peak_kind, sm_mhz):
     per_kernel = {}
     for name, (launches, ms) in timing.items():
         base = name.split("<")[0]
@@ -147,13 +170,21 @@ def roofline(wl, R, timing, steps, hbm_peak, peak_kind):
     if dom not in costs:
         dom = max(costs, key=lambda k: per_kernel.get(k, [0, 0.0])[1])
     launches, ms = per_kernel[dom]
-    bytes_per_launch = costs[dom] * steps / launches
-    avg_ms = ms / launches
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_source": peak_kind,
-            "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_ms, 5),
-            "launches": launches}, per_kernel
+    avg_s = ms / launches * 1e-3
+    ops = costs[dom]["ops"] * steps / launches
+    byts = costs[dom]["bytes"] * steps / launches
+    clock = sm_mhz or 2070.0
+    alu_peak = SMS * LANES * clock * 1e6 / 1e12
+    achieved = ops / avg_s / 1e12
+    hbm = byts / avg_s / 1e9
+    return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
+            "unit": "TOP/s", "frac": round(achieved / alu_peak, 4), "traffic": recorded_traffic(dom),
+            "peak_source": "152 SMs x 128 FP32 lanes x %s SM clock %.0f MHz (one op per lane per cycle)"
+                           % ("sampled" if sm_mhz else "maximum", clock),
+            "ops_per_launch": int(ops), "bytes_per_launch": int(byts), "avg_launch_ms": round(avg_s * 1e3, 5),
+            "launches": launches,
+            "hbm": {"achieved": round(hbm, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(hbm / hbm_peak, 4),
+                    "peak_source": peak_kind}}, per_kernel
 
 
 # --------------------------------------------------------------------- CPU oracle
@@ -206,13 +237,16 @@ def run_reference(args):
     if args.warmup > 0:
         oracle_sample_run(wl, R, 0)  # loads the library and touches the code paths once
     total_cells, total_t = 0, 0.0
-    for k in range(args.steps):
+    # each step is a bounded sample (one realization with its embedding); at
+    # most 60 are timed so that the run ends within a few minutes
+    steps = min(args.steps, 60)
+    for k in range(steps):
         cells, dt, _ = oracle_sample_run(wl, R, (k + 1) * R)
         total_cells += cells
         total_t += dt
     value = total_cells / total_t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "text": wl.text,
                                             "sample_realizations_per_step": R},
@@ -331,7 +365,7 @@ def main():
     cells_all = pipe.cells_per_step * world
     value = cells_all / (ms_max * 1e-3)
     hbm_peak, peak_kind = measured_peaks()
-    roof, per_kernel = roofline(wl, R, timing, args.steps, hbm_peak, peak_kind)
+    roof, per_kernel = roofline(wl, R, timing, args.steps, hbm_peak, peak_kind, clk.get("sm_mhz"))
     launches = sum(v[0] for v in per_kernel.values())
 
     e2e = None
