@@ -178,6 +178,31 @@ CF_API cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, cf_d
 CF_API cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, cf_dtype dt,
                     void* fields_out, void* ws, size_t ws_bytes, cf_stream_t s);
 
+/* cf_sample (binary32) without a caller workspace.  The paper has no
+ * counterpart: this entry exists for callers that cannot allocate device
+ * memory where they sample -- code running while another thread captures a
+ * CUDA graph in global capture mode, where cudaMalloc is an error, and
+ * programs whose device memory is fixed up front by a budget or another
+ * allocator.  They pass the embedding and fields_out ([R][2][n...] float) as
+ * for cf_sample; the intermediate lives in a 16 MiB array inside the library
+ * that every device loading the library holds until the process exits.
+ *  - Sizes whose single realization needs more than 16 MiB of intermediate
+ *    (e.g. 2D surveys above 1024x1024, 3D above 64^3) are rejected with
+ *    CF_ERR_UNSUPPORTED and a message giving the bytes needed.
+ *  - Nothing is allocated on the device: no cudaMalloc, cudaFree or allocator
+ *    call.  The first call on a device does a one-time set-up (the array's
+ *    device address, an ordering event, the twiddle tables): make it before
+ *    any stream capture.  The first use of an embedding on a stream other
+ *    than the one it was built on creates one CUDA event (host-side object)
+ *    so that cf_embedding_free can wait for the work.
+ *  - All calls share the array, which keeps the last call's contents; every
+ *    element a call reads it has written first, so nothing needs clearing.
+ *    The library orders successive calls on the GPU (host lock + device
+ *    event); calls whose work nevertheless overlapped on the GPU would race
+ *    on the array. */
+CF_API cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R,
+                                   void* fields_out, cf_stream_t s);
+
 /* Lognormal + Poisson parameters (section 3.1, eqs. (Lncov), (sampling)). */
 typedef struct {
     double sigma2;          /* variance of G: rho = exp(G - sigma2/2), delta = rho - 1 */

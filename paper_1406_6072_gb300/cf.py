@@ -84,6 +84,7 @@ _sigs = {
     "cf_sample": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, _P, C.c_size_t, _S],
     "cf_sample_lp": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, C.POINTER(cf_lp_params), _P,
                      C.c_size_t, _S],
+    "cf_sample_noalloc": [_P, C.c_uint64, C.c_uint64, C.c_int32, _P, _S],
     "cf_lognormal_poisson": [_P, C.c_int32, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, C.c_uint64,
                              C.c_uint64, _P, _P, _S],
     "cf_power_spectrum_workspace_size": [C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), C.c_int32,
@@ -242,6 +243,12 @@ def cf_sample_workspace_size(emb, R, dtype):
 def cf_sample(emb, seed, r0, R, dtype, fields_out, ws, ws_bytes, stream=None):
     _check(_lib.cf_sample(emb.handle, seed, r0, R, dtype, _ptr(fields_out), _ptr(ws), ws_bytes, _stream(stream)),
            "cf_sample")
+
+
+def cf_sample_noalloc(emb, seed, r0, R, fields_out, stream=None):
+    """Binary32 sampler with its intermediate in the library's static array
+    (no device allocation); see include/cf.h."""
+    _check(_lib.cf_sample_noalloc(emb.handle, seed, r0, R, _ptr(fields_out), _stream(stream)), "cf_sample_noalloc")
 
 
 def make_lp(sigma2, nbar, counts_out, seed, f=None, delta_out=None):

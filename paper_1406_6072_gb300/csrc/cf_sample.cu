@@ -215,6 +215,17 @@ __global__ void k_noise_f64(uint32_t key0, uint32_t key1, uint32_t r0, long long
         o[k] = noise_f64((unsigned long long)k, r, key0, key1);
 }
 
+// Entry for cf_sample_noalloc (cf_noalloc.cu): the binary32 sampler into a
+// given workspace, and the intermediate bytes one realization needs.
+cf_status sample_f32_into(const cf_embedding* e, uint64_t seed, uint64_t r0, int R, void* fields, void* ws,
+                          size_t ws_bytes, cudaStream_t st) {
+    return sample_impl<float>(e, seed, r0, R, fields, nullptr, ws, ws_bytes, 1.0, st);
+}
+
+size_t sample_bytes_per_realization(const cf_embedding* e, cf_dtype dt) {
+    return per_realization_bytes(e->grid, dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>));
+}
+
 }  // namespace cf
 
 using namespace cf;
