@@ -217,6 +217,26 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 __global__ void __launch_bounds__(kRedThreads)
+    k_cov_error_partial_real(const double* __restrict__ z, const double* __restrict__ c, GridInfo g,
+                             double* __restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    double mx = 0.0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.mtotal;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx;
+        bool survey = true;
+        for (int a = g.ndim - 1; a >= 0; --a) {
+            const long long m = rem % g.m[a];
+            rem /= g.m[a];
+            if (m == g.n[a]) survey = false;
+        }
+        if (survey) mx = fmax(mx, fabs(z[idx] - c[idx]));
+    }
+    mx = block_max(mx, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = mx;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
     k_cov_error_final(const double* __restrict__ part, int nparts, EmbedStats* st) {
     __shared__ double sh[kRedThreads];
     double mx = 0.0;
@@ -233,6 +253,148 @@ __global__ void k_lambda_plus_complex(const double* __restrict__ lam, double tau
         const double l = lam[i];
         z[i] = mk(l > tau ? l : 0.0, 0.0);
     }
+}
+
+// ---------------------------------------------------------------------------
+// DFT of a real array that is even along every axis (x(M - m) = x(m) per
+// axis), as the embedded row of an isotropic xi is.  Its DFT is real and even,
+// so two real lines are transformed as the real and imaginary parts of one
+// complex line and read back as Re and Im, and along the last axis only the
+// non-redundant half k <= M/2 is kept; the full result is mirrored at the end.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(RowsCfg<double, L>::THREADS, RowsCfg<double, L>::MINB)
+    k_even_rows(const double* __restrict__ in, long long nrows, double* __restrict__ out,
+                const C2<double>* __restrict__ tw) {
+    using Cfg = RowsCfg<double, L>;
+    using G = typename Cfg::G;
+    constexpr int H = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<double>* sm = reinterpret_cast<C2<double>*>(smraw);
+    const int line = threadIdx.x / G::TL;
+    const int j = threadIdx.x % G::TL;
+    const long long pair = (long long)blockIdx.x * Cfg::ROWS + line;
+    const long long ra = 2 * pair, rb = ra + 1;
+    const bool valid = ra < nrows;
+    const bool hasb = rb < nrows;
+    const double* a = in + (size_t)(valid ? ra : 0) * L;
+    const double* b = in + (size_t)(hasb ? rb : 0) * L;
+    C2<double> v[G::E];
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) {
+        const int x = j + q * (L / G::E);
+        v[q] = mk(a[x], hasb ? b[x] : 0.0);
+    }
+    auto sink = [&](int, int k, C2<double> val) {
+        if (!valid || k >= H) return;
+        out[(size_t)ra * H + k] = val.x;
+        if (hasb) out[(size_t)rb * H + k] = val.y;
+    };
+    line_fft<double, L, -1, L>(sm, RowLayout<G::E, G::PADDED>(), line, j, v, tw, sink);
+}
+
+// Columns of in[outer][L][inner] in pairs (i, i+1): out has the same layout
+// (in place allowed).
+template <int L>
+__global__ void __launch_bounds__(ColsCfg<double, L>::THREADS, ColsCfg<double, L>::MINB)
+    k_even_cols(const double* in, long long inner, double* out, const C2<double>* __restrict__ tw) {
+    using Cfg = ColsCfg<double, L>;
+    using G = typename Cfg::G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<double>* sm = reinterpret_cast<C2<double>*>(smraw);
+    const int ln = threadIdx.x % Cfg::C;
+    const int j = threadIdx.x / Cfg::C;
+    const long long ia = 2 * ((long long)blockIdx.x * Cfg::C + ln), ib = ia + 1;
+    const long long o = blockIdx.y;
+    const bool valid = ia < inner;
+    const bool hasb = ib < inner;
+    const size_t base = (size_t)o * L * (size_t)inner;
+    C2<double> v[G::E];
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) {
+        const size_t row = base + (size_t)(j + q * (L / G::E)) * (size_t)inner;
+        v[q] = mk(valid ? in[row + ia] : 0.0, hasb ? in[row + ib] : 0.0);
+    }
+    auto sink = [&](int, int p, C2<double> val) {
+        if (!valid) return;
+        const size_t row = base + (size_t)p * (size_t)inner;
+        out[row + ia] = val.x;
+        if (hasb) out[row + ib] = val.y;
+    };
+    line_fft<double, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+}
+
+// full[rows][M] from half[rows][M/2+1] of an even last axis, times scale
+__global__ void k_even_mirror(const double* __restrict__ half, long long rows, long long M, double scale,
+                              double* __restrict__ full) {
+    const long long H = M / 2 + 1;
+    const long long total = rows * M;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / M, k = t - r * M;
+        const long long kk = k < H ? k : M - k;
+        full[t] = half[r * H + kk] * scale;
+    }
+}
+
+// lambda+ (threshold tau read on the device) as a real array
+__global__ void k_lambda_plus_real(const double* __restrict__ lam, const struct EmbedStats* __restrict__ st,
+                                   double* __restrict__ out, long long total) {
+    const double tau = st->tau;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        out[i] = l > tau ? l : 0.0;
+    }
+}
+
+template <int L>
+static cf_status launch_even_rows(const double* in, long long nrows, double* out, cudaStream_t s) {
+    using Cfg = RowsCfg<double, L>;
+    auto kern = k_even_rows<L>;
+    CF_TRY(prepare_smem(kern, Cfg::SMEM));
+    const long long pairs = (nrows + 1) / 2;
+    ScopedKernelTimer kt(s, "even_rows_f64", L);
+    kern<<<(unsigned)((pairs + Cfg::ROWS - 1) / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, s>>>(in, nrows, out,
+                                                                                     twiddles<double>());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+template <int L>
+static cf_status launch_even_cols(double* data, long long outer, long long inner, cudaStream_t s) {
+    using Cfg = ColsCfg<double, L>;
+    auto kern = k_even_cols<L>;
+    CF_TRY(prepare_smem(kern, Cfg::SMEM));
+    if (outer > 65535) return fail(CF_ERR_UNSUPPORTED, "even transform with %lld outer slices", outer);
+    const long long pairs = (inner + 1) / 2;
+    dim3 grid((unsigned)((pairs + Cfg::C - 1) / Cfg::C), (unsigned)outer);
+    ScopedKernelTimer kt(s, "even_cols_f64", L);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(data, inner, data, twiddles<double>());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+// full = scale * DFT(x) for x real and even along every axis; half is scratch
+// of (mtotal / M_last) * (M_last/2 + 1) doubles.
+static cf_status even_dft(const double* x, const GridInfo& g, double scale, double* half, double* full,
+                          cudaStream_t s) {
+    const int d = g.ndim;
+    const long long Ml = g.m[d - 1];
+    const long long H = Ml / 2 + 1;
+    const long long rows = g.mtotal / Ml;
+    CF_TRY(dispatch_line(Ml, [&](auto Lc) -> cf_status { return launch_even_rows<decltype(Lc)::value>(x, rows, half, s); }));
+    for (int a = d - 2; a >= 0; --a) {
+        long long inner = H, outer = 1;
+        for (int b2 = a + 1; b2 < d - 1; ++b2) inner *= g.m[b2];
+        for (int b2 = 0; b2 < a; ++b2) outer *= g.m[b2];
+        CF_TRY(dispatch_line(g.m[a], [&](auto Lc) -> cf_status {
+            return launch_even_cols<decltype(Lc)::value>(half, outer, inner, s);
+        }));
+    }
+    k_even_mirror<<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
+    CF_CHECK_LAUNCH();
+    return CF_OK;
 }
 
 // Device buffers of one embedding computation.
@@ -252,10 +414,14 @@ struct EmbedScratch {
     }
 };
 
-// Common tail: z holds lambda (complex, Re used), c the embedded row (target
-// covariance).  Runs a3 and builds the embedding.
-static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t flags,
-                                  cf_embedding** out, cf_embed_report* rep) {
+// Common tail: lambda is either in `lam_real` (real, from the even transform)
+// or in Re of sc.z (general complex transform); sc.c holds the embedded row
+// (target covariance).  Runs a3 and builds the embedding with one host
+// synchronisation: the realised-covariance error of the clamped spectrum is
+// computed before it (from the device-side threshold) whenever clamping is
+// allowed, and reported only if clamping happened.
+static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t flags, const double* lam_real,
+                                  bool even, cf_embedding** out, cf_embed_report* rep) {
     cudaStream_t s = sc.s;
     const long long total = gi.mtotal;
     const int blocks = grid_blocks(total, kRedThreads, kRedBlocks);
@@ -272,16 +438,45 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
     }
     const bool want_error = (flags & CF_EMBED_CLAMP) && !(flags & CF_EMBED_SKIP_ERROR);
     {
-    ScopedKernelTimer kt(s, "embed_psd");
-    k_take_real<<<blocks, kRedThreads, 0, s>>>(sc.z, 1.0, e->lambda, total);
-    k_minmax_partial<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.part);
-    k_minmax_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
-    CF_CUDA(cudaMemsetAsync(sc.counts, 0, 2 * sizeof(unsigned long long), s));
-    k_threshold<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.st, 1.0 / (double)total, e->s32, sc.part,
-                                               sc.counts);
-    k_threshold_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.counts, sc.st);
+        ScopedKernelTimer kt(s, "embed_psd");
+        if (lam_real)
+            CF_CUDA(cudaMemcpyAsync(e->lambda, lam_real, sizeof(double) * total, cudaMemcpyDeviceToDevice, s));
+        else
+            k_take_real<<<blocks, kRedThreads, 0, s>>>(sc.z, 1.0, e->lambda, total);
+        k_minmax_partial<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.part);
+        k_minmax_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
+        CF_CUDA(cudaMemsetAsync(sc.counts, 0, 2 * sizeof(unsigned long long), s));
+        k_threshold<<<blocks, kRedThreads, 0, s>>>(e->lambda, total, sc.st, 1.0 / (double)total, e->s32, sc.part,
+                                                   sc.counts);
+        k_threshold_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.counts, sc.st);
     }
     CF_CHECK_LAUNCH();
+    if (want_error) {
+        // realised covariance = IDFT(lambda+)/M^d, compared with c on survey lags
+        double* buf = (double*)sc.z;  // M^d doubles, then scratch for the half spectra
+        {
+            ScopedKernelTimer kt(s, "embed_cov_error");
+            k_lambda_plus_real<<<blocks, kRedThreads, 0, s>>>(e->lambda, sc.st, buf, total);
+        }
+        CF_CHECK_LAUNCH();
+        if (even) {
+            // lambda+ is real and even: its inverse transform equals its forward one
+            CF_TRY(even_dft(buf, gi, 1.0 / (double)total, buf + total, buf, s));
+            ScopedKernelTimer kt(s, "embed_cov_error");
+            k_cov_error_partial_real<<<blocks, kRedThreads, 0, s>>>(buf, sc.c, gi, sc.part);
+        } else {
+            {
+                ScopedKernelTimer kt(s, "embed_cov_error");
+                k_real_to_complex<<<blocks, kRedThreads, 0, s>>>(buf, nullptr, sc.z, total);
+            }
+            CF_CHECK_LAUNCH();
+            CF_TRY((fft_nd_inplace<double, +1>(sc.z, gi, s)));
+            ScopedKernelTimer kt(s, "embed_cov_error");
+            k_cov_error_partial<<<blocks, kRedThreads, 0, s>>>(sc.z, sc.c, gi, 1.0 / (double)total, sc.part);
+        }
+        k_cov_error_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
+        CF_CHECK_LAUNCH();
+    }
     EmbedStats st{};
     CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
     CF_CUDA(cudaStreamSynchronize(s));
@@ -312,24 +507,7 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
         }
         r.clamped = 1;
         r.exact = 0;
-        if (want_error) {
-            // realised covariance = IDFT(lambda+)/M^d
-            {
-                ScopedKernelTimer kt(s, "embed_cov_error");
-                k_lambda_plus_complex<<<blocks, kRedThreads, 0, s>>>(e->lambda, st.tau, sc.z, total);
-            }
-            CF_CHECK_LAUNCH();
-            CF_TRY((fft_nd_inplace<double, +1>(sc.z, gi, s)));
-            {
-                ScopedKernelTimer kt(s, "embed_cov_error");
-                k_cov_error_partial<<<blocks, kRedThreads, 0, s>>>(sc.z, sc.c, gi, 1.0 / (double)total, sc.part);
-                k_cov_error_final<<<1, kRedThreads, 0, s>>>(sc.part, blocks, sc.st);
-            }
-            CF_CHECK_LAUNCH();
-            CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
-            CF_CUDA(cudaStreamSynchronize(s));
-            r.cov_error = st.cov_error;
-        }
+        if (want_error) r.cov_error = st.cov_error;
     }
     e->report = r;
     if (rep) *rep = r;
@@ -382,8 +560,14 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
         k_fill_row<<<blocks, kRedThreads, 0, sc.s>>>(gi, xi->kind, xi->amp, xi->scale, xi->beta, sc.c, sc.z);
     }
     CF_CHECK_LAUNCH();
+    if (xi->kind != CF_XI_TABLE) {
+        // the row depends on |lag| only: even along every axis
+        double* full = (double*)sc.z;
+        CF_TRY(even_dft(sc.c, gi, 1.0, full + gi.mtotal, full, sc.s));
+        return finish_embedding(gi, sc, flags, full, true, out, rep);
+    }
     CF_TRY((fft_nd_inplace<double, -1>(sc.z, gi, sc.s)));
-    return finish_embedding(gi, sc, flags, out, rep);
+    return finish_embedding(gi, sc, flags, nullptr, false, out, rep);
 }
 
 extern "C" cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
@@ -406,5 +590,5 @@ extern "C" cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda
     k_take_real<<<blocks, kRedThreads, 0, sc.s>>>(sc.z, 1.0 / (double)gi.mtotal, sc.c, gi.mtotal);
     k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(lambda, nullptr, sc.z, gi.mtotal);
     CF_CHECK_LAUNCH();
-    return finish_embedding(gi, sc, flags, out, rep);
+    return finish_embedding(gi, sc, flags, nullptr, false, out, rep);
 }

@@ -94,6 +94,29 @@ def test_embedding_parity(orc, n, kind, amp, scale, beta, clamp):
     emb.close()
 
 
+@pytest.mark.parametrize("on_device", [False, True])
+def test_embedding_from_table(orc, on_device):
+    """A tabulated first row (the general, not necessarily even, path): here the
+    row of the generalised-Cauchy family plus an odd perturbation."""
+    n = (16, 32)
+    c = orc.embed_row(list(n), 1, 0.8, 3.0, 0.4)
+    c = c + 1e-3 * np.sin(2 * np.pi * np.arange(c.shape[1]) / c.shape[1])[None, :]
+    tab = torch.from_numpy(np.ascontiguousarray(c))
+    if on_device:
+        tab = tab.to(DEV)
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_TABLE, table=tab), cf.CF_EMBED_CLAMP)
+    lam = torch.empty(c.shape, dtype=torch.float64, device=DEV)
+    cf.cf_embedding_lambda(emb, lam)
+    torch.cuda.synchronize()
+    ref = np.real(orc.fft_nd(c.astype(np.complex128), -1))
+    assert np.max(np.abs(lam.cpu().numpy() - ref)) <= 1e-12 * np.abs(ref).max()
+    _, _, orep = orc.psd(list(n), c, ref, clamp=True)
+    assert emb.report["n_negative"] == orep["n_negative"]
+    if orep["clamped"]:
+        assert emb.report["cov_error"] == pytest.approx(orep["cov_error"], rel=1e-6, abs=1e-13)
+    emb.close()
+
+
 def test_not_psd_is_reported(orc):
     g = cf.make_grid((64, 64))
     with pytest.raises(cf.CfError) as ei:
