@@ -274,6 +274,87 @@ CF_API cf_status cf_power_spectrum_counts(const int32_t* counts, const float* f_
                                    int64_t* nmodes_out, double* mean_or_null, double* cov_or_null,
                                    void* ws, size_t ws_bytes, cf_stream_t s);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching (not in the paper; it
+ * serves the paper's sampler, sections 2 and 3.1, to many clients).
+ *
+ * A server owns one device.  Requests (grid, xi, realization range, optional
+ * lognormal + Poisson step) are queued by cf_serve_submit and run by a worker
+ * thread: requests are admitted while a slot (stream) is free and their
+ * device memory fits the HBM budget; queued requests of the same grid shape
+ * are batched into one launch (even with different xi or seeds); the
+ * eigenvalues of each spectrum are kept on the device (LRU cache keyed by
+ * grid, family, scale, beta and flags -- the amplitude is applied as
+ * sqrt(amp) at sampling, since lambda is linear in amp).  Results stay in
+ * server-owned device memory until cf_serve_release; optionally they are also
+ * copied to host memory (pinned memory keeps the worker from blocking).
+ * Binary32 fields only; the Poisson step uses f = 1 (no survey mask).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t device;                  /* CUDA device index                                  */
+    int32_t max_inflight;            /* concurrent batches (streams), >= 1                 */
+    int32_t queue_capacity;          /* queued requests before submit returns CF_ERR_BUSY  */
+    int32_t cache_entries;           /* embeddings kept on the device                      */
+    int32_t max_batch_realizations;  /* realizations per batched launch                    */
+    int32_t pad_;
+    size_t hbm_budget;               /* bytes: cached embeddings + in-flight + unreleased results */
+} cf_serve_cfg;
+
+typedef struct {
+    cf_grid grid;
+    cf_xi xi;                        /* CF_XI_GAUSSIAN / GEN_CAUCHY / EXPONENTIAL          */
+    uint32_t embed_flags;            /* CF_EMBED_CLAMP etc.                                */
+    int32_t want_counts;             /* 1: also lognormal + Poisson counts                 */
+    uint64_t seed;                   /* noise seed                                         */
+    uint64_t r0;                     /* first realization                                  */
+    int32_t R;                       /* realizations (two fields each)                     */
+    int32_t pad_;
+    double sigma2, nbar;             /* lognormal / Poisson parameters (want_counts)       */
+    uint64_t lp_seed;                /* Poisson seed                                       */
+    float* host_fields;              /* optional host copy [R][2][n...] float              */
+    int32_t* host_counts;            /* optional host copy [R][2][n...] int32              */
+} cf_request;
+
+typedef struct {
+    cf_status status;                /* CF_OK, CF_ERR_NOT_PSD, CF_ERR_NOMEM, ...           */
+    int32_t cache_hit;               /* embedding served from the cache                    */
+    double queue_ms, run_ms, latency_ms;  /* submit->start, start->done, submit->done    */
+    const float* dev_fields;         /* server-owned device results, valid until release   */
+    const int32_t* dev_counts;
+    cf_embed_report embed;           /* report of the request's spectrum (at its amp)      */
+} cf_result;
+
+typedef struct {
+    uint64_t submitted, completed, failed, rejected;
+    int64_t queued, inflight;
+    uint64_t cache_hits, cache_misses, cache_evictions;
+    uint64_t batches, batched_requests, realizations;
+    size_t bytes_in_use, bytes_peak, budget;
+    double p50_ms, p99_ms, mean_ms;  /* submit->done latency over completed requests       */
+    double realizations_per_s;       /* completed realizations / (last done - first submit) */
+} cf_serve_statistics;
+
+typedef struct cf_server cf_server;
+
+/* Starts a server (worker thread, streams) on cfg->device. */
+CF_API cf_status cf_serve_create(const cf_serve_cfg* cfg, cf_server** out);
+/* Queues a request; *ticket identifies it.  CF_ERR_ARG for an invalid
+ * request, CF_ERR_BUSY when the queue is full. */
+CF_API cf_status cf_serve_submit(cf_server* sv, const cf_request* req, uint64_t* ticket);
+/* CF_OK and *res when the request has finished (res->status is its
+ * outcome); CF_ERR_BUSY while it is queued or running; CF_ERR_NOT_FOUND for
+ * an unknown or released ticket. */
+CF_API cf_status cf_serve_poll(cf_server* sv, uint64_t ticket, cf_result* res);
+/* As cf_serve_poll, waiting up to timeout_us microseconds (< 0: no limit);
+ * CF_ERR_TIMEOUT if it has not finished by then. */
+CF_API cf_status cf_serve_wait(cf_server* sv, uint64_t ticket, int64_t timeout_us, cf_result* res);
+/* Frees a finished request's device results (and forgets the ticket). */
+CF_API cf_status cf_serve_release(cf_server* sv, uint64_t ticket);
+CF_API cf_status cf_serve_stats(cf_server* sv, cf_serve_statistics* st);
+/* Stops the worker after the running batches finish; queued requests end
+ * with CF_ERR_BUSY; frees everything. */
+CF_API cf_status cf_serve_destroy(cf_server* sv);
+
 /* Kernel timing (tracing).  cf_kernel_timing(1) clears the accumulators and
  * makes every subsequent library launch record a CUDA event pair on its own
  * stream; cf_kernel_timing(0) stops recording.  cf_kernel_timing_read waits

@@ -70,6 +70,43 @@ class cf_bins(C.Structure):
                 ("edges", C.c_void_p)]
 
 
+class cf_serve_cfg(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_inflight", C.c_int32), ("queue_capacity", C.c_int32),
+                ("cache_entries", C.c_int32), ("max_batch_realizations", C.c_int32), ("pad_", C.c_int32),
+                ("hbm_budget", C.c_size_t)]
+
+
+class cf_request(C.Structure):
+    _fields_ = [("grid", cf_grid), ("xi", cf_xi), ("embed_flags", C.c_uint32), ("want_counts", C.c_int32),
+                ("seed", C.c_uint64), ("r0", C.c_uint64), ("R", C.c_int32), ("pad_", C.c_int32),
+                ("sigma2", C.c_double), ("nbar", C.c_double), ("lp_seed", C.c_uint64),
+                ("host_fields", C.c_void_p), ("host_counts", C.c_void_p)]
+
+
+class cf_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("cache_hit", C.c_int32), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double), ("dev_fields", C.c_void_p), ("dev_counts", C.c_void_p),
+                ("embed", cf_embed_report)]
+
+    def asdict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "embed"}
+        d["embed"] = self.embed.asdict()
+        return d
+
+
+class cf_serve_statistics(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("rejected", C.c_uint64), ("queued", C.c_int64), ("inflight", C.c_int64),
+                ("cache_hits", C.c_uint64), ("cache_misses", C.c_uint64), ("cache_evictions", C.c_uint64),
+                ("batches", C.c_uint64), ("batched_requests", C.c_uint64), ("realizations", C.c_uint64),
+                ("bytes_in_use", C.c_size_t), ("bytes_peak", C.c_size_t), ("budget", C.c_size_t),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("realizations_per_s", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P = C.c_void_p
 _S = C.c_void_p  # cudaStream_t
 _sigs = {
@@ -93,6 +130,13 @@ _sigs = {
                           C.c_size_t, _S],
     "cf_power_spectrum_counts": [_P, _P, C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), _P, _P, _P, _P, _P,
                                  C.c_size_t, _S],
+    "cf_serve_create": [C.POINTER(cf_serve_cfg), C.POINTER(_P)],
+    "cf_serve_submit": [_P, C.POINTER(cf_request), C.POINTER(C.c_uint64)],
+    "cf_serve_poll": [_P, C.c_uint64, C.POINTER(cf_result)],
+    "cf_serve_wait": [_P, C.c_uint64, C.c_int64, C.POINTER(cf_result)],
+    "cf_serve_release": [_P, C.c_uint64],
+    "cf_serve_stats": [_P, C.POINTER(cf_serve_statistics)],
+    "cf_serve_destroy": [_P],
 }
 for _name, _args in _sigs.items():
     _fn = getattr(_lib, _name)
@@ -288,6 +332,87 @@ def cf_power_spectrum_counts(counts, f, grid, nfields, bins, pk_out, nmodes_out,
     _check(_lib.cf_power_spectrum_counts(_ptr(counts), _ptr(f), C.byref(grid), nfields, C.byref(bins),
                                          _ptr(pk_out), _ptr(nmodes_out), _ptr(mean), _ptr(cov), _ptr(ws), ws_bytes,
                                          _stream(stream)), "cf_power_spectrum_counts")
+
+
+# ----------------------------------------------------------------- serving
+def make_serve_cfg(device=0, max_inflight=4, queue_capacity=100000, cache_entries=64, max_batch_realizations=256,
+                   hbm_budget=32 << 30):
+    c = cf_serve_cfg()
+    c.device, c.max_inflight, c.queue_capacity = device, max_inflight, queue_capacity
+    c.cache_entries, c.max_batch_realizations, c.hbm_budget = cache_entries, max_batch_realizations, hbm_budget
+    return c
+
+
+def make_request(n, kind, amp, scale, beta=0.0, seed=0, r0=0, R=1, embed_flags=CF_EMBED_CLAMP, want_counts=False,
+                 sigma2=0.0, nbar=0.0, lp_seed=0, host_fields=None, host_counts=None, cell=None):
+    r = cf_request()
+    r.grid = make_grid(n, cell)
+    r.xi = make_xi(kind, amp, scale, beta)
+    r.embed_flags, r.want_counts = embed_flags, int(bool(want_counts))
+    r.seed, r.r0, r.R = seed, r0, R
+    r.sigma2, r.nbar, r.lp_seed = sigma2, nbar, lp_seed
+    r.host_fields, r.host_counts = _ptr(host_fields), _ptr(host_counts)
+    return r
+
+
+class Server:
+    """Owns a cf_server handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            _lib.cf_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cf_serve_create(cfg):
+    h = _P()
+    _check(_lib.cf_serve_create(C.byref(cfg), C.byref(h)), "cf_serve_create")
+    return Server(h.value)
+
+
+def cf_serve_submit(sv, req):
+    t = C.c_uint64()
+    _check(_lib.cf_serve_submit(sv.handle, C.byref(req), C.byref(t)), "cf_serve_submit")
+    return t.value
+
+
+def cf_serve_poll(sv, ticket):
+    """Result dict when finished, None while queued or running."""
+    r = cf_result()
+    st = _lib.cf_serve_poll(sv.handle, ticket, C.byref(r))
+    if st == CF_ERR_BUSY:
+        return None
+    _check(st, "cf_serve_poll")
+    return r.asdict()
+
+
+def cf_serve_wait(sv, ticket, timeout_us=-1):
+    r = cf_result()
+    _check(_lib.cf_serve_wait(sv.handle, ticket, timeout_us, C.byref(r)), "cf_serve_wait")
+    return r.asdict()
+
+
+def cf_serve_release(sv, ticket):
+    _check(_lib.cf_serve_release(sv.handle, ticket), "cf_serve_release")
+
+
+def cf_serve_stats(sv):
+    s = cf_serve_statistics()
+    _check(_lib.cf_serve_stats(sv.handle, C.byref(s)), "cf_serve_stats")
+    return s.asdict()
+
+
+def cf_serve_destroy(sv):
+    sv.close()
 
 
 def cf_kernel_timing(enable):

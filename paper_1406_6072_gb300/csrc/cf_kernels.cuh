@@ -17,6 +17,21 @@ namespace cf {
 // Re/Im fields and (binary32) apply the lognormal transform and the Poisson
 // draw of section 3.1 to both fields of the survey cell.
 // --------------------------------------------------------------------------
+// Per-realization parameters of a batched launch (realizations of several
+// requests of one grid shape in one launch): the request's amplitudes, noise
+// key and realization index, its output arrays and lognormal/Poisson step.
+struct RealDesc {
+    const float* s;         // sqrt(lambda+/M^d) of the request's embedding (amplitude 1)
+    float* fields;          // [2][cells] of this realization
+    int32_t* counts;        // [2][cells] or null
+    double half_sigma2, nbar;
+    float amp_scale;        // sqrt(amp)
+    float half_sigma2_f, nbar_f;
+    uint32_t r;             // realization index (noise counter and Poisson field pair)
+    uint32_t key0, key1;    // noise key
+    uint32_t pkey0, pkey1;  // Poisson key
+};
+
 template <typename T>
 struct FieldEpi {
     T* fields;          // [chunk][2][cells] or null
@@ -30,8 +45,13 @@ struct FieldEpi {
     uint32_t pkey0, pkey1;
     uint32_t r0;        // global index of the chunk's first realization
     long long cells;
+    const RealDesc* desc;  // batched launch: per-realization parameters (else null)
 
     __device__ __forceinline__ void operator()(int rl, long long cell, C2<T> w) const {
+        if (desc) {
+            batched(desc[rl], cell, w);
+            return;
+        }
         const size_t base = (size_t)rl * 2 * (size_t)cells + (size_t)cell;
         if (fields) {
             fields[base] = w.x;
@@ -48,6 +68,19 @@ struct FieldEpi {
                 delta[base] = expf(g0 - half_sigma2_f) - 1.0f;
                 delta[base + cells] = expf(g1 - half_sigma2_f) - 1.0f;
             }
+        }
+    }
+
+    __device__ __forceinline__ void batched(const RealDesc& d, long long cell, C2<T> w) const {
+        const float g0 = (float)w.x, g1 = (float)w.y;
+        d.fields[cell] = g0;
+        d.fields[cell + cells] = g1;
+        if (d.counts) {
+            const uint4 x = poisson_words((unsigned long long)cell, d.r, d.pkey0, d.pkey1);
+            d.counts[cell] = poisson_count_fast(g0, d.half_sigma2, d.half_sigma2_f, d.nbar, d.nbar_f, 1.0f,
+                                                bits53(x.x, x.y));
+            d.counts[cell + cells] = poisson_count_fast(g1, d.half_sigma2, d.half_sigma2_f, d.nbar, d.nbar_f, 1.0f,
+                                                        bits53(x.z, x.w));
         }
     }
 };

@@ -34,7 +34,7 @@ template <typename T, int L>
 __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     k_sample_rows(const T* __restrict__ s, T amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
                   long long nrows, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
-                  const C2<T>* __restrict__ tw) {
+                  const C2<T>* __restrict__ tw, const RealDesc* __restrict__ desc) {
     using Cfg = SRowsCfg<T, L>;
     using G = typename Cfg::G;
     constexpr int E = G::E;
@@ -45,7 +45,17 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     const int j = threadIdx.x % G::TL;
     const long long row = (long long)blockIdx.x * Cfg::ROWS + line;
     const int rl = blockIdx.y;
-    const uint32_t r = r0 + (uint32_t)rl;
+    uint32_t r = r0 + (uint32_t)rl;
+    if constexpr (sizeof(T) == 4) {
+        if (desc) {  // batched launch: this realization's request
+            const RealDesc& d = desc[rl];
+            s = (const T*)d.s;
+            amp_scale = (T)d.amp_scale;
+            key0 = d.key0;
+            key1 = d.key1;
+            r = d.r;
+        }
+    }
     const bool valid = row < nrows;
     const long long rw = valid ? row : 0;
     const T* srow = s + (size_t)rw * L;
@@ -83,7 +93,7 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
 template <typename T>
 static cf_status launch_sample_rows(long long L, const T* s, T amp_scale, uint64_t seed, uint32_t r0,
                                     int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, const RealDesc* desc = nullptr) {
     return dispatch_line(L, [&](auto Lc) -> cf_status {
         constexpr int LL = decltype(Lc)::value;
         using Cfg = SRowsCfg<T, LL>;
@@ -92,7 +102,7 @@ static cf_status launch_sample_rows(long long L, const T* s, T amp_scale, uint64
         dim3 grid((unsigned)((nrows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)chunk);
         ScopedKernelTimer kt(st, sizeof(T) == 4 ? "sample_rows_f32" : "sample_rows_f64", LL);
         kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
-                                                     nrows, out, mode, epi, twiddles<T>());
+                                                     nrows, out, mode, epi, twiddles<T>(), desc);
         CF_CHECK_LAUNCH();
         return CF_OK;
     });
@@ -213,6 +223,44 @@ __global__ void k_noise_f64(uint32_t key0, uint32_t key1, uint32_t r0, long long
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells;
          k += (long long)gridDim.x * blockDim.x)
         o[k] = noise_f64((unsigned long long)k, r, key0, key1);
+}
+
+// Batched binary32 sampler (serving): nreal realizations described by
+// desc (device array) on grid g, all writing fields (and counts) through their
+// descriptors; ws holds the chunk intermediates.
+cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    const size_t elem = sizeof(C2<float>);
+    const int chunk = pick_chunk(g, elem, nreal, ws_bytes);
+    if (chunk < 1) return fail(CF_ERR_NOMEM, "batch workspace too small");
+    const long long cells = g.ncell;
+    const int d = g.ndim;
+    C2<float>* buf1 = (C2<float>*)ws;
+    C2<float>* buf2 = d == 3 ? buf1 + (size_t)chunk * g.m[0] * g.m[1] * g.n[2] : nullptr;
+    const long long Ml = g.m[d - 1];
+    const long long nrows = g.mtotal / Ml;
+    for (int c0 = 0; c0 < nreal; c0 += chunk) {
+        const int nr = (nreal - c0) < chunk ? (nreal - c0) : chunk;
+        FieldEpi<float> epi{};
+        epi.cells = cells;
+        epi.desc = desc + c0;
+        if (d == 1) {
+            CF_TRY(launch_sample_rows<float>(Ml, nullptr, 1.0f, 0, 0, nr, nrows, nullptr, 1, epi, st, desc + c0));
+        } else if (d == 2) {
+            CF_TRY(launch_sample_rows<float>(Ml, nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
+            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st)));
+        } else {
+            CF_TRY(launch_sample_rows<float>(Ml, nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
+            CF_TRY((launch_cols<float, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st)));
+            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st)));
+        }
+    }
+    return CF_OK;
+}
+
+size_t sample_chunk_bytes(const GridInfo& g, int nreal) {
+    const size_t per = per_realization_bytes(g, sizeof(C2<float>));
+    return per * (size_t)pick_chunk(g, sizeof(C2<float>), nreal < 1 ? 1 : nreal, (size_t)-1);
 }
 
 // Entry for cf_sample_noalloc (cf_noalloc.cu): the binary32 sampler into a

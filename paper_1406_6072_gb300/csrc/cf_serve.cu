@@ -1,0 +1,260 @@
+// cf_serve.cu -- CUDA backend of the serving loop and its C ABI.
+//
+// Each slot is one stream with its own descriptor staging buffers and
+// completion event.  A batch is one chunked, descriptor-driven sampler launch
+// (cf_sample.cu: sample_batch_f32) covering the realizations of all its
+// requests, followed by the optional host copies; results stay in
+// stream-ordered device allocations until the client releases them.
+#include <math.h>
+
+#include <memory>
+
+#include "cf_kernels.cuh"
+#include "cf_serve_core.h"
+
+namespace cf {
+cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, void* ws, size_t ws_bytes,
+                           cudaStream_t st);
+size_t sample_chunk_bytes(const GridInfo& g, int nreal);
+}  // namespace cf
+
+using namespace cf;
+
+namespace {
+
+struct CudaSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    RealDesc* host_desc = nullptr;   // pinned staging
+    RealDesc* dev_desc = nullptr;
+    void* ws = nullptr;
+    int capacity = 0;
+};
+
+class CudaBackend : public cfserve::Backend {
+  public:
+    CudaBackend(int device, int nslots, int max_real) : device_(device), max_real_(max_real) {
+        cudaSetDevice(device_);
+        cudaStreamCreateWithFlags(&embed_stream_, cudaStreamNonBlocking);
+        slots_.resize(nslots);
+        for (auto& s : slots_) {
+            cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+            cudaMallocHost((void**)&s.host_desc, sizeof(RealDesc) * (size_t)max_real);
+            cudaMalloc((void**)&s.dev_desc, sizeof(RealDesc) * (size_t)max_real);
+            s.capacity = max_real;
+        }
+    }
+
+    ~CudaBackend() override {
+        cudaSetDevice(device_);
+        cudaDeviceSynchronize();
+        for (auto& s : slots_) {
+            if (s.ws) cudaFree(s.ws);
+            cudaFree(s.dev_desc);
+            cudaFreeHost(s.host_desc);
+            cudaEventDestroy(s.done);
+            cudaStreamDestroy(s.stream);
+        }
+        cudaStreamDestroy(embed_stream_);
+    }
+
+    static GridInfo grid_of(const cf_request& r) {
+        GridInfo g{};
+        check_grid(&r.grid, &g);
+        return g;
+    }
+
+    size_t embed_bytes(const cf_request& r) override {
+        const GridInfo g = grid_of(r);
+        // kept: lambda (8 B) + binary32 amplitudes (4 B); transient scratch while built: 24 B
+        return (size_t)g.mtotal * (8 + 4 + 24);
+    }
+
+    cf_status embed(const cf_request& r, void** handle, cf_embed_report* rep) override {
+        cudaSetDevice(device_);
+        cf_embedding* e = nullptr;
+        const cf_status st = cf_embed(&r.grid, &r.xi, r.embed_flags, (cf_stream_t)embed_stream_, &e, rep);
+        *handle = e;
+        return st;
+    }
+
+    void free_embedding(void* h) override { cf_embedding_free((cf_embedding*)h); }
+
+    size_t result_bytes(const cf_request& r) override {
+        const GridInfo g = grid_of(r);
+        const size_t cells = (size_t)g.ncell * 2 * (size_t)r.R;
+        return cells * sizeof(float) + (r.want_counts ? cells * sizeof(int32_t) : 0);
+    }
+
+    size_t batch_bytes(const std::vector<cfserve::Job*>& jobs) override {
+        int n = 0;
+        for (auto* j : jobs) n += j->req.R;
+        return sample_chunk_bytes(grid_of(jobs[0]->req), n);
+    }
+
+    cf_status alloc_result(int slot, cfserve::Job* j) override {
+        cudaSetDevice(device_);
+        const GridInfo g = grid_of(j->req);
+        const size_t cells = (size_t)g.ncell * 2 * (size_t)j->req.R;
+        cudaStream_t s = slots_[slot].stream;
+        if (cudaMallocAsync(&j->dev_fields, cells * sizeof(float), s) != cudaSuccess)
+            return fail(CF_ERR_NOMEM, "result allocation failed");
+        if (j->req.want_counts && cudaMallocAsync(&j->dev_counts, cells * sizeof(int32_t), s) != cudaSuccess)
+            return fail(CF_ERR_NOMEM, "result allocation failed");
+        result_stream_[j] = s;
+        return CF_OK;
+    }
+
+    void free_result(cfserve::Job* j) override {
+        cudaSetDevice(device_);
+        cudaStream_t s = slots_[0].stream;
+        auto it = result_stream_.find(j);
+        if (it != result_stream_.end()) {
+            s = it->second;
+            result_stream_.erase(it);
+        }
+        if (j->dev_fields) cudaFreeAsync(j->dev_fields, s);
+        if (j->dev_counts) cudaFreeAsync(j->dev_counts, s);
+        j->dev_fields = nullptr;
+        j->dev_counts = nullptr;
+    }
+
+    cf_status launch(int slot, const std::vector<cfserve::Job*>& jobs) override {
+        cudaSetDevice(device_);
+        CudaSlot& sl = slots_[slot];
+        const GridInfo g = grid_of(jobs[0]->req);
+        int n = 0;
+        for (auto* j : jobs) n += j->req.R;
+        if (n > sl.capacity) return fail(CF_ERR_ARG, "batch larger than the descriptor capacity");
+        // the previous batch of this slot has finished (retired), so the
+        // staging buffer is free
+        int k = 0;
+        for (auto* j : jobs) {
+            const cf_embedding* e = (const cf_embedding*)j->emb->handle;
+            const cf_request& r = j->req;
+            for (int i = 0; i < r.R; ++i, ++k) {
+                RealDesc& d = sl.host_desc[k];
+                d.s = e->s32;
+                d.fields = (float*)j->dev_fields + (size_t)i * 2 * (size_t)g.ncell;
+                d.counts = r.want_counts ? (int32_t*)j->dev_counts + (size_t)i * 2 * (size_t)g.ncell : nullptr;
+                d.half_sigma2 = 0.5 * r.sigma2;
+                d.nbar = r.nbar;
+                d.amp_scale = (float)sqrt(r.xi.amp);
+                d.half_sigma2_f = (float)(0.5 * r.sigma2);
+                d.nbar_f = (float)r.nbar;
+                d.r = (uint32_t)(r.r0 + (uint64_t)i);
+                d.key0 = (uint32_t)r.seed;
+                d.key1 = (uint32_t)(r.seed >> 32);
+                d.pkey0 = (uint32_t)r.lp_seed;
+                d.pkey1 = (uint32_t)(r.lp_seed >> 32);
+            }
+        }
+        CF_CUDA(cudaMemcpyAsync(sl.dev_desc, sl.host_desc, sizeof(RealDesc) * (size_t)n, cudaMemcpyHostToDevice,
+                                sl.stream));
+        const size_t wsb = sample_chunk_bytes(g, n);
+        if (wsb && cudaMallocAsync(&sl.ws, wsb, sl.stream) != cudaSuccess)
+            return fail(CF_ERR_NOMEM, "batch workspace allocation failed");
+        CF_TRY(sample_batch_f32(g, sl.dev_desc, n, sl.ws, wsb, sl.stream));
+        for (auto* j : jobs) {
+            const size_t cells = (size_t)g.ncell * 2 * (size_t)j->req.R;
+            if (j->req.host_fields)
+                CF_CUDA(cudaMemcpyAsync(j->req.host_fields, j->dev_fields, cells * sizeof(float),
+                                        cudaMemcpyDeviceToHost, sl.stream));
+            if (j->req.want_counts && j->req.host_counts)
+                CF_CUDA(cudaMemcpyAsync(j->req.host_counts, j->dev_counts, cells * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, sl.stream));
+            // the embedding is read by this stream's work
+            record_use((cf_embedding*)j->emb->handle, sl.stream);
+        }
+        CF_CUDA(cudaEventRecord(sl.done, sl.stream));
+        return CF_OK;
+    }
+
+    bool done(int slot) override {
+        cudaSetDevice(device_);
+        return cudaEventQuery(slots_[slot].done) == cudaSuccess;
+    }
+
+    void finish(int slot) override {
+        CudaSlot& sl = slots_[slot];
+        if (sl.ws) {
+            cudaFreeAsync(sl.ws, sl.stream);
+            sl.ws = nullptr;
+        }
+    }
+
+  private:
+    int device_;
+    int max_real_;
+    cudaStream_t embed_stream_ = nullptr;
+    std::vector<CudaSlot> slots_;
+    std::map<cfserve::Job*, cudaStream_t> result_stream_;
+};
+
+}  // namespace
+
+struct cf_server {
+    std::unique_ptr<CudaBackend> backend;
+    std::unique_ptr<cfserve::Scheduler> sched;
+};
+
+extern "C" cf_status cf_serve_create(const cf_serve_cfg* cfg, cf_server** out) {
+    clear_error();
+    if (!cfg || !out) return fail(CF_ERR_ARG, "cfg and out are required");
+    *out = nullptr;
+    if (cfg->max_inflight < 1 || cfg->queue_capacity < 1 || cfg->cache_entries < 1 ||
+        cfg->max_batch_realizations < 1 || cfg->hbm_budget == 0)
+        return fail(CF_ERR_ARG, "cfg fields must be positive");
+    int ndev = 0;
+    CF_CUDA(cudaGetDeviceCount(&ndev));
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(CF_ERR_ARG, "device %d does not exist", cfg->device);
+    CF_CUDA(cudaSetDevice(cfg->device));
+    CF_TRY(ensure_device_init());
+    cf_server* sv = new cf_server();
+    sv->backend.reset(new CudaBackend(cfg->device, cfg->max_inflight, cfg->max_batch_realizations));
+    CF_CUDA(cudaGetLastError());
+    sv->sched.reset(new cfserve::Scheduler(*cfg, sv->backend.get()));
+    *out = sv;
+    return CF_OK;
+}
+
+extern "C" cf_status cf_serve_submit(cf_server* sv, const cf_request* req, uint64_t* ticket) {
+    if (!sv || !req || !ticket) return fail(CF_ERR_ARG, "NULL argument");
+    GridInfo g;
+    CF_TRY(check_grid(&req->grid, &g));
+    const cf_status st = sv->sched->submit(*req, ticket);
+    if (st == CF_ERR_ARG) return fail(st, "invalid request (R >= 1, amp > 0, scale > 0, parametric xi required)");
+    if (st == CF_ERR_BUSY) return fail(st, "queue full or server stopping");
+    return st;
+}
+
+extern "C" cf_status cf_serve_poll(cf_server* sv, uint64_t ticket, cf_result* res) {
+    if (!sv) return fail(CF_ERR_ARG, "NULL server");
+    return sv->sched->poll(ticket, res);
+}
+
+extern "C" cf_status cf_serve_wait(cf_server* sv, uint64_t ticket, int64_t timeout_us, cf_result* res) {
+    if (!sv) return fail(CF_ERR_ARG, "NULL server");
+    return sv->sched->wait(ticket, timeout_us, res);
+}
+
+extern "C" cf_status cf_serve_release(cf_server* sv, uint64_t ticket) {
+    if (!sv) return fail(CF_ERR_ARG, "NULL server");
+    return sv->sched->release(ticket);
+}
+
+extern "C" cf_status cf_serve_stats(cf_server* sv, cf_serve_statistics* st) {
+    if (!sv || !st) return fail(CF_ERR_ARG, "NULL argument");
+    sv->sched->stats(st);
+    return CF_OK;
+}
+
+extern "C" cf_status cf_serve_destroy(cf_server* sv) {
+    if (!sv) return CF_OK;
+    sv->sched->stop();
+    sv->sched.reset();
+    sv->backend.reset();
+    delete sv;
+    return CF_OK;
+}
