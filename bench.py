@@ -45,6 +45,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-realizations", type=int, default=8)
+    p.add_argument("--serve-requests", type=int, default=10000)
     return p.parse_args()
 
 
@@ -257,6 +258,125 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------- serving
+def run_serving(args):
+    """Mixed request stream through cf_serve_* (continuous batching), against
+    the sequential one-request-at-a-time binary64 path (cf_embed + cf_sample
+    in binary64, synchronised per request) on a 200-request subsample."""
+    import threading as th
+
+    import numpy as np
+    import torch
+
+    from paper_1406_6072_gb300 import cf
+    from paper_1406_6072_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    base = W.serving_requests(args.serve_requests, seed=5, rate_hz=1.0)
+
+    def req_of(q):
+        return cf.make_request(q["n"], q["xi_kind"], q["amp"], q["scale"], q["beta"], seed=q["seed"], r0=0, R=q["R"],
+                               embed_flags=cf.CF_EMBED_CLAMP)
+
+    def serve(reqs, rate):
+        sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=4, cache_entries=96, max_batch_realizations=256,
+                                                  hbm_budget=96 << 30))
+        tickets = []
+        lock = th.Lock()
+        done_flag = [False]
+
+        def waiter():
+            k = 0
+            clamped = 0
+            while True:
+                with lock:
+                    if k >= len(tickets):
+                        if done_flag[0]:
+                            break
+                        t = None
+                    else:
+                        t = tickets[k]
+                if t is None:
+                    time.sleep(1e-4)
+                    continue
+                r = cf.cf_serve_wait(sv, t, -1)
+                clamped += r["embed"]["clamped"]
+                cf.cf_serve_release(sv, t)
+                k += 1
+            waiter.clamped = clamped
+
+        w = th.Thread(target=waiter)
+        w.start()
+        t0 = time.perf_counter()
+        for q in reqs:
+            if rate:
+                delay = t0 + q["t_arrival"] / rate - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            tk = cf.cf_serve_submit(sv, req_of(q))
+            with lock:
+                tickets.append(tk)
+        with lock:
+            done_flag[0] = True
+        w.join()
+        wall = time.perf_counter() - t0
+        st = cf.cf_serve_stats(sv)
+        cf.cf_serve_destroy(sv)
+        st["wall_s"] = wall
+        st["clamped_requests"] = waiter.clamped
+        return st
+
+    n_cap = min(1000, len(base))
+    cap = serve(base[:n_cap], None)   # closed loop: everything at once
+    cap_rps = cap["completed"] / cap["wall_s"]
+    rates = {}
+    per = max(1, (len(base) - n_cap) // 4)
+    for i, f in enumerate((0.5, 0.8, 1.0, 1.2)):
+        chunk = base[n_cap + i * per: n_cap + (i + 1) * per]
+        t_first = chunk[0]["t_arrival"]
+        chunk = [dict(q, t_arrival=q["t_arrival"] - t_first) for q in chunk]
+        st = serve(chunk, f * cap_rps)
+        rates["%.1fx" % f] = {"offered_req_per_s": f * cap_rps, "completed": st["completed"],
+                              "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                              "realizations_per_s": st["realizations_per_s"], "batches": st["batches"],
+                              "batched_requests": st["batched_requests"], "cache_hits": st["cache_hits"],
+                              "cache_misses": st["cache_misses"], "peak_gb": st["bytes_peak"] / 1e9,
+                              "clamped_requests": st["clamped_requests"]}
+    # sequential binary64 path on a subsample
+    rng = np.random.default_rng(7)
+    sub = [base[i] for i in rng.choice(len(base), size=min(200, len(base)), replace=False)]
+    lat, reals = [], 0
+    t_all = time.perf_counter()
+    for q in sub:
+        t1 = time.perf_counter()
+        emb = cf.cf_embed(cf.make_grid(q["n"]), cf.make_xi(q["xi_kind"], q["amp"], q["scale"], q["beta"]),
+                          cf.CF_EMBED_CLAMP)
+        wsb = cf.cf_sample_workspace_size(emb, q["R"], cf.CF_F64)
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device="cuda:0")
+        out = torch.empty((q["R"], 2) + tuple(q["n"]), dtype=torch.float64, device="cuda:0")
+        cf.cf_sample(emb, q["seed"], 0, q["R"], cf.CF_F64, out, ws, wsb)
+        torch.cuda.synchronize()
+        emb.close()
+        lat.append(1e3 * (time.perf_counter() - t1))
+        reals += q["R"]
+        del out, ws
+    seq_wall = time.perf_counter() - t_all
+    lat = np.sort(np.asarray(lat))
+    served = rates["1.0x"]
+    line = {"metric": "served realizations/s, mixed 2D/3D request stream (Poisson arrivals at capacity)",
+            "value": served["realizations_per_s"], "unit": "realizations/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving", "requests": len(base), "capacity_req_per_s": cap_rps,
+                       "capacity_realizations_per_s": cap["realizations_per_s"],
+                       "text": "2D sides 64..1024 and 3D sides 32..128, gaussian / generalised-Cauchy xi, amp "
+                               "U(0.2,1.5), scale in {2,..,16}, 1-32 realizations, clamping allowed, seed 5"},
+            "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"], "rates": rates,
+            "sequential_f64": {"requests": len(sub), "realizations_per_s": reals / seq_wall,
+                               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                               "note": "one request at a time: cf_embed + binary64 cf_sample, synchronised"}}
+    print(json.dumps(line))
+    return 0
+
+
 # --------------------------------------------------------------------- our arm
 def e2e_run(pipe, wl, steps, warmup, rank):
     """Same metric through the public API with host buffers: the xi table is
@@ -313,6 +433,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import torch
 
     from paper_1406_6072_gb300 import cf
