@@ -46,6 +46,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-realizations", type=int, default=8)
     p.add_argument("--serve-requests", type=int, default=10000)
+    p.add_argument("--tune", action="store_true", help="autotune the sampler's chunk schedule before warm-up")
     return p.parse_args()
 
 
@@ -118,30 +119,38 @@ SMS, LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 
 def kernel_costs(wl, R, chunks):
     """Algorithmic bytes and operations per step of each kernel of the binary32
-    2D path (definitions in the design doc section 7; FMA = 1 op).
+    path, 2D or 3D (definitions in the design doc section 7; FMA = 1 op).
 
-    sample_rows: writes the pruned intermediate R*M0*N1 complex64, reads
+    sample_rows: noise + last-axis transform of every embedded row; writes the
+    pruned intermediate (R * prod(M[:-1]) * n[-1] complex64) and reads
     sqrt(lambda) once per launch; 76 ops of noise per embedded cell plus the
-    row transforms.  icols_fields_lp: reads the intermediate, writes 2 fields
+    row transforms.  icols (3D only): axis-1 pass between the intermediates.
+    icols_fields_lp: last pass (axis 0), reads its intermediate, writes 2 fields
     + 2 count maps per realization; column transforms plus the Poisson step.
     pk_rows / pk_cols: fields in, half spectra out / in, for the Gaussian
     fields and the count maps."""
-    n0, n1 = wl.n
-    m0, m1 = wl.m
+    import math
+    n, m = list(wl.n), list(wl.m)
+    d = len(n)
     F = 2 * R
     lg = lambda v: v.bit_length() - 1
-    inter = R * m0 * n1 * 8
-    half = F * n0 * (n1 // 2 + 1) * 8
+    cells = math.prod(n)
     nbar = wl.nbar or 0.0
-    return {
-        "sample_rows_f32": {"bytes": inter + chunks * m0 * m1 * 4,
-                            "ops": R * m0 * m1 * 76 + R * m0 * 4 * m1 * lg(m1)},
-        "icols_fields_lp_f32": {"bytes": inter + F * n0 * n1 * 8,
-                                "ops": R * n1 * 4 * m0 * lg(m0) + F * n0 * n1 * (30 + 10 + 4 * (nbar + 1))},
-        "pk_rows_f32": {"bytes": 2 * (F * n0 * n1 * 4 + half),
-                        "ops": 2 * (F // 2) * n0 * 4 * n1 * lg(n1)},
-        "pk_cols_f32": {"bytes": 2 * half, "ops": 2 * F * (n1 // 2 + 1) * (4 * n0 * lg(n0) + 8 * n0)},
-    }
+    inter1 = R * math.prod(m[:-1]) * n[-1] * 8
+    costs = {"sample_rows_f32": {"bytes": inter1 + chunks * math.prod(m) * 4,
+                                 "ops": R * math.prod(m) * 76 + R * math.prod(m[:-1]) * 4 * m[-1] * lg(m[-1])}}
+    inter_last = R * m[0] * (cells // n[0]) * 8
+    if d == 3:
+        costs["icols_f32"] = {"bytes": inter1 + inter_last, "ops": R * m[0] * n[2] * 4 * m[1] * lg(m[1])}
+    costs["icols_fields_lp_f32"] = {"bytes": inter_last + F * cells * 8,
+                                    "ops": R * (cells // n[0]) * 4 * m[0] * lg(m[0])
+                                    + F * cells * (30 + 10 + 4 * (nbar + 1))}
+    half = F * (cells // n[-1]) * (n[-1] // 2 + 1) * 8
+    costs["pk_rows_f32"] = {"bytes": 2 * (F * cells * 4 + half),
+                            "ops": 2 * F * (cells // n[-1]) * 2 * n[-1] * lg(n[-1])}
+    lines0 = F * (cells // (n[0] * n[-1])) * (n[-1] // 2 + 1)  # axis-0 lines of the half spectra
+    costs["pk_cols_f32"] = {"bytes": 2 * half, "ops": 2 * lines0 * (4 * n[0] * lg(n[0]) + 8 * n[0])}
+    return costs
 
 
 def recorded_traffic(kernel):
@@ -256,6 +265,78 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# --------------------------------------------------------------- precision sweep
+def run_sweep(args):
+    """2D 2048^2 survey in 4096^2, 32 realizations per step: sampler + power
+    spectrum in binary64, binary32 and the bf16 / fp16 tensor-core modes, the
+    same seeds for all.  Reports cells/s per precision (embedding cached, as
+    in a sweep over precisions of one spectrum); the error of each precision
+    against the binary64 oracle is measured by tests/test_gpu_tc.py."""
+    import torch
+
+    from paper_1406_6072_gb300 import cf
+    from paper_1406_6072_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.CONFIGS["cauchy2d_n2048_sweep"]
+    stream = torch.cuda.Stream(dev)
+    grid = cf.make_grid(wl.n)
+    R, F = wl.R, 2 * wl.R
+    bins = cf.make_bins(wl.nbins)
+    out = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        emb = cf.cf_embed(grid, cf.make_xi(wl.xi_kind, wl.amp, wl.scale, wl.beta), cf.CF_EMBED_CLAMP, stream)
+        for name, dt in (("f64", cf.CF_F64), ("f32", cf.CF_F32), ("bf16_tc", cf.CF_BF16_TC),
+                         ("f16_tc", cf.CF_F16_TC)):
+            fdt = cf.CF_F64 if dt == cf.CF_F64 else cf.CF_F32
+            tdt = torch.float64 if fdt == cf.CF_F64 else torch.float32
+            wsb = cf.cf_sample_workspace_size(emb, R, dt)
+            ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+            fields = torch.empty((R, 2) + tuple(wl.n), dtype=tdt, device=dev)
+            pkb = cf.cf_power_spectrum_workspace_size(grid, F, bins, fdt)
+            pkws = torch.empty(pkb, dtype=torch.uint8, device=dev)
+            pk = torch.empty((F, wl.nbins), dtype=torch.float64, device=dev)
+            nm = torch.empty(wl.nbins, dtype=torch.int64, device=dev)
+            mean = torch.empty(wl.nbins, dtype=torch.float64, device=dev)
+            cov = torch.empty((wl.nbins, wl.nbins), dtype=torch.float64, device=dev)
+
+            def step(k):
+                cf.cf_sample(emb, wl.seed, k * R, R, dt, fields, ws, wsb, stream)
+                cf.cf_power_spectrum(fields, fdt, grid, F, bins, pk, nm, mean, cov, pkws, pkb, stream)
+
+            steps = max(3, min(args.steps, 20))
+            for k in range(max(3, args.warmup)):
+                step(k)
+            torch.cuda.synchronize()
+            cf.cf_kernel_timing(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(steps):
+                step(100 + k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            timing = cf.cf_kernel_timing_read()
+            cf.cf_kernel_timing(0)
+            ms = e0.elapsed_time(e1) / steps
+            if dt in (cf.CF_BF16_TC, cf.CF_F16_TC):
+                assert cf.cf_tc_faults(stream) == 0
+            kern = {k: list(v) for k, v in timing.items()}
+            out[name] = {"ms_per_step": ms, "cells_per_s": 2 * R * wl.cells_per_field / (ms * 1e-3),
+                         "realizations_per_s": R / (ms * 1e-3),
+                         "kernels_ms_per_step": {k: v[1] / steps for k, v in sorted(kern.items())}}
+            del ws, fields, pkws
+        emb.close()
+    clk = clocks.stop()
+    line = {"metric": "cells/s per precision, 2D 2048^2 sampler + power spectrum", "value": out["f32"]["cells_per_s"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "sweep", "data": "synthetic",
+            "config": {"workload": wl.name, "text": wl.text, "realizations_per_step": R,
+                       "note": "embedding cached across steps; errors vs the binary64 oracle: tests/test_gpu_tc.py"},
+            "precisions": out, "clocks": clk}
+    print(json.dumps(line))
 
 
 # --------------------------------------------------------------------- serving
@@ -435,6 +516,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "cauchy2d_n2048_sweep":
+        return run_sweep(args)
     import torch
 
     from paper_1406_6072_gb300 import cf
@@ -459,6 +542,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    tuned = None
+    if args.tune:
+        with torch.cuda.stream(stream):
+            pipe.embed()
+            chunk, tms = pipe.tune()
+            tuned = {"chunk": chunk, "ms_per_realization": tms}
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
             pipe.step(r0=(rank * 100000 + k) * R)
@@ -512,7 +601,7 @@ def main():
                        "cells_per_step": cells_all, "realizations_per_s": R * world / (ms_max * 1e-3),
                        "l2": "each step writes %d MiB of fields and counts (> 129 MB L2)"
                              % (2 * pipe.cells_per_step * 4 >> 20),
-                       "parallelism": "replicas x%d" % world},
+                       "parallelism": "replicas x%d" % world, "tuned_chunk": tuned},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report,
             "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(per_kernel.items())},

@@ -69,8 +69,9 @@ typedef enum {
 typedef enum {
     CF_F64 = 0,      /* binary64 noise, transforms and fields                         */
     CF_F32 = 1,      /* binary32 noise, transforms and fields (eigenvalues stay FP64) */
-    CF_BF16_TC = 2,  /* reserved: tensor-core DFT stages, not in this build           */
-    CF_F16_TC = 3    /* reserved: tensor-core DFT stages, not in this build           */
+    CF_BF16_TC = 2,  /* binary32 noise; bf16 DFT-matrix tensor-core stages with binary32
+                        accumulation; binary32 fields (cf_sample only, 2D, sides 256/4096) */
+    CF_F16_TC = 3    /* as CF_BF16_TC with fp16 stage inputs                               */
 } cf_dtype;
 
 /* Survey grid (section 2, eq. (grid)): ndim in {1,2,3}; n[i] survey cells on
@@ -203,6 +204,22 @@ CF_API cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, in
 CF_API cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R,
                                    void* fields_out, cf_stream_t s);
 
+/* Autotuner of the sampler's chunk schedule (realizations per launch of the
+ * transform passes).  Times cf_sample on R realizations of e for each
+ * candidate chunk that fits ws_bytes (1, 2, 4, ... up to R), writing into
+ * fields_scratch ([R][2][n...] of dt), and records the fastest for this
+ * device, grid shape and dtype; later cf_sample / cf_sample_lp /
+ * cf_sample_workspace_size calls with that shape use it.  Synchronises s.
+ * *chunk_out (may be NULL) receives the chosen chunk, *ms_out (may be NULL)
+ * its time per realization. */
+CF_API cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, void* ws, size_t ws_bytes,
+                                void* fields_scratch, cf_stream_t s, int32_t* chunk_out, double* ms_out);
+
+/* Tensor-core modes: number of tensor-core waits that ran out of time (1 s
+ * each) on the current device since the last call; synchronises s and
+ * resets the count.  A non-zero count means the affected fields are invalid. */
+CF_API cf_status cf_tc_faults(cf_stream_t s, uint32_t* count);
+
 /* Lognormal + Poisson parameters (section 3.1, eqs. (Lncov), (sampling)). */
 typedef struct {
     double sigma2;          /* variance of G: rho = exp(G - sigma2/2), delta = rho - 1 */
@@ -295,7 +312,7 @@ typedef struct {
     int32_t max_inflight;            /* concurrent batches (streams), >= 1                 */
     int32_t queue_capacity;          /* queued requests before submit returns CF_ERR_BUSY  */
     int32_t cache_entries;           /* embeddings kept on the device                      */
-    int32_t max_batch_realizations;  /* realizations per batched launch                    */
+    int32_t max_batch_realizations;  /* realizations per batched launch (and per request)  */
     int32_t pad_;
     size_t hbm_budget;               /* bytes: cached embeddings + in-flight + unreleased results */
 } cf_serve_cfg;

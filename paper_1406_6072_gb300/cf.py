@@ -122,6 +122,9 @@ _sigs = {
     "cf_sample_lp": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, C.POINTER(cf_lp_params), _P,
                      C.c_size_t, _S],
     "cf_sample_noalloc": [_P, C.c_uint64, C.c_uint64, C.c_int32, _P, _S],
+    "cf_tc_faults": [_S, C.POINTER(C.c_uint32)],
+    "cf_tune_sample": [_P, C.c_int32, C.c_int32, _P, C.c_size_t, _P, _S, C.POINTER(C.c_int32),
+                       C.POINTER(C.c_double)],
     "cf_lognormal_poisson": [_P, C.c_int32, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, C.c_uint64,
                              C.c_uint64, _P, _P, _S],
     "cf_power_spectrum_workspace_size": [C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), C.c_int32,
@@ -293,6 +296,22 @@ def cf_sample_noalloc(emb, seed, r0, R, fields_out, stream=None):
     """Binary32 sampler with its intermediate in the library's static array
     (no device allocation); see include/cf.h."""
     _check(_lib.cf_sample_noalloc(emb.handle, seed, r0, R, _ptr(fields_out), _stream(stream)), "cf_sample_noalloc")
+
+
+def cf_tune_sample(emb, dtype, R, ws, ws_bytes, fields_scratch, stream=None):
+    """Times the candidate chunk schedules; returns (chunk, ms per realization)."""
+    c = C.c_int32()
+    ms = C.c_double()
+    _check(_lib.cf_tune_sample(emb.handle, dtype, R, _ptr(ws), ws_bytes, _ptr(fields_scratch), _stream(stream),
+                               C.byref(c), C.byref(ms)), "cf_tune_sample")
+    return c.value, ms.value
+
+
+def cf_tc_faults(stream=None):
+    """Tensor-core waits that ran out of time since the last call (0 = all good)."""
+    c = C.c_uint32()
+    _check(_lib.cf_tc_faults(_stream(stream), C.byref(c)), "cf_tc_faults")
+    return c.value
 
 
 def make_lp(sigma2, nbar, counts_out, seed, f=None, delta_out=None):

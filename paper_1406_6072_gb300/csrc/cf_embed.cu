@@ -431,8 +431,8 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
     e->alloc_stream = s;
     auto cleanup = [&]() { cf_embedding_free(e); };
     // persistent arrays: stream-ordered allocations, released after their last use
-    if (cudaMallocAsync((void**)&e->lambda, sizeof(double) * total, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&e->s32, sizeof(float) * total, s) != cudaSuccess) {
+    if (pool_malloc((void**)&e->lambda, sizeof(double) * total, s) != cudaSuccess ||
+        pool_malloc((void**)&e->s32, sizeof(float) * total, s) != cudaSuccess) {
         cleanup();
         return fail(CF_ERR_NOMEM, "device allocation of the embedding (%lld cells) failed", total);
     }
@@ -523,11 +523,11 @@ using namespace cf;
 
 static cf_status alloc_scratch(EmbedScratch& sc, long long total) {
     cudaStream_t s = sc.s;
-    if (cudaMallocAsync((void**)&sc.z, sizeof(C2<double>) * total, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&sc.c, sizeof(double) * total, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&sc.part, sizeof(double) * kRedBlocks * 2, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&sc.st, sizeof(EmbedStats), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&sc.counts, sizeof(unsigned long long) * 2, s) != cudaSuccess)
+    if (pool_malloc((void**)&sc.z, sizeof(C2<double>) * total, s) != cudaSuccess ||
+        pool_malloc((void**)&sc.c, sizeof(double) * total, s) != cudaSuccess ||
+        pool_malloc((void**)&sc.part, sizeof(double) * kRedBlocks * 2, s) != cudaSuccess ||
+        pool_malloc((void**)&sc.st, sizeof(EmbedStats), s) != cudaSuccess ||
+        pool_malloc((void**)&sc.counts, sizeof(unsigned long long) * 2, s) != cudaSuccess)
         return fail(CF_ERR_NOMEM, "device allocation for the embedding of %lld cells failed", total);
     return CF_OK;
 }

@@ -49,6 +49,9 @@ bool sync_check_enabled();
 // One-time per-device set-up (twiddle tables).  Synchronises the device the
 // first time it runs on a device.
 cf_status ensure_device_init();
+// Stream-ordered allocation from the library's pool on the current device
+// (release with cudaFreeAsync).
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
 // Entry-point prologue: makes the device of stream s current (the legacy
 // default stream keeps the current device) and runs the one-time set-up.
 cf_status enter(cudaStream_t s);
@@ -97,6 +100,8 @@ struct cf_embedding {
     double* lambda = nullptr;    // raw eigenvalues [mtotal]
     double* s64 = nullptr;       // sqrt(lambda+ / mtotal) [mtotal], built on first binary64 use
     float* s32 = nullptr;        // sqrt(lambda+ / mtotal) in binary32 [mtotal]
+    double* sumsq = nullptr;     // sum of s32^2 (tensor-core input scaling), built on first use
+    cudaEvent_t s64_ready = nullptr, sumsq_ready = nullptr;  // completion of the lazy builds
     double tau = 0.0;
     cf_embed_report report{};
     int device = 0;
@@ -108,6 +113,8 @@ struct cf_embedding {
 namespace cf {
 // Records that work enqueued on stream s reads embedding e (the free waits for it).
 void record_use(cf_embedding* e, cudaStream_t s);
-// Builds e->s64 (on stream s) if it does not exist yet.
+// Builds e->s64 (on stream s) if it does not exist yet; s waits for the build.
 cf_status ensure_s64(cf_embedding* e, cudaStream_t s);
+// Builds e->sumsq (on stream s) if it does not exist yet; s waits for the build.
+cf_status ensure_sumsq(cf_embedding* e, cudaStream_t s);
 }  // namespace cf

@@ -15,6 +15,7 @@
 // N_tot per field, the binning pass accumulates |DFT X|^2 and the cross term
 // against the mask spectrum DFT I, and the final pass combines them.
 #include <math.h>
+#include <stdlib.h>
 
 #include <mutex>
 #include <vector>
@@ -405,7 +406,12 @@ static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins
     P->rows = g.ncell / nl;
     P->elem = elem;
     const size_t per_field = elem * (size_t)P->rows * (size_t)P->H;
-    long long chunk = (long long)((48ull << 20) / (per_field ? per_field : 1));
+    static const size_t target = [] {
+        const char* e = getenv("CF_PK_CHUNK_MB");  // half spectra per chunk (measured: large is faster)
+        long mb = e ? atol(e) : 1024;
+        return (size_t)(mb < 1 ? 1 : mb) << 20;
+    }();
+    long long chunk = (long long)(target / (per_field ? per_field : 1));
     if (chunk < 2) chunk = 2;
     chunk &= ~1ll;
     if (chunk > 65534) chunk = 65534;

@@ -44,6 +44,11 @@ static std::mutex g_init_mu;
 static bool g_inited[kMaxDevices];
 static C2<float>* g_tw32_ptr[kMaxDevices];
 static C2<double>* g_tw64_ptr[kMaxDevices];
+// Library memory pool per device: stream-ordered allocations of embeddings,
+// scratch and served results.  Freed blocks stay in the pool (release
+// threshold: unlimited), so that repeated embeddings do not map and unmap
+// device memory at every synchronisation.
+static cudaMemPool_t g_pool[kMaxDevices];
 
 static int current_device() {
     int d = 0;
@@ -66,8 +71,19 @@ cf_status ensure_device_init() {
     CF_CUDA(cudaDeviceSynchronize());
     g_tw32_ptr[dev] = (C2<float>*)p32;
     g_tw64_ptr[dev] = (C2<double>*)p64;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    CF_CUDA(cudaMemPoolCreate(&g_pool[dev], &props));
+    uint64_t keep = ~0ull;
+    CF_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
     g_inited[dev] = true;
     return CF_OK;
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+    return cudaMallocFromPoolAsync(p, bytes, g_pool[current_device()], s);
 }
 
 bool sync_check_enabled() {
@@ -162,15 +178,68 @@ __global__ void k_s64(const double* __restrict__ lam, double tau, double inv_tot
 
 cf_status ensure_s64(cf_embedding* e, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(e->mu);
-    if (e->s64) return CF_OK;
+    if (e->s64) {
+        CF_CUDA(cudaStreamWaitEvent(s, e->s64_ready, 0));
+        return CF_OK;
+    }
     const long long total = e->grid.mtotal;
     double* p = nullptr;
-    if (cudaMallocAsync((void**)&p, sizeof(double) * total, s) != cudaSuccess)
+    if (pool_malloc((void**)&p, sizeof(double) * total, s) != cudaSuccess)
         return fail(CF_ERR_NOMEM, "device allocation of the binary64 amplitudes failed");
     const int blocks = (int)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256);
     k_s64<<<blocks, 256, 0, s>>>(e->lambda, e->tau, 1.0 / (double)total, p, total);
     CF_CHECK_LAUNCH();
+    CF_CUDA(cudaEventCreateWithFlags(&e->s64_ready, cudaEventDisableTiming));
+    CF_CUDA(cudaEventRecord(e->s64_ready, s));
     e->s64 = p;
+    return CF_OK;
+}
+
+// sum of s^2 over the embedding: per-block partial sums, then one block
+__global__ void __launch_bounds__(256) k_sumsq_partial(const float* __restrict__ s, long long total,
+                                                       double* __restrict__ part) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < total; i += (long long)gridDim.x * 256)
+        acc += (double)s[i] * (double)s[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(256) k_sumsq_final(const double* __restrict__ part, int n, double* out) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+cf_status ensure_sumsq(cf_embedding* e, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    if (e->sumsq) {
+        CF_CUDA(cudaStreamWaitEvent(s, e->sumsq_ready, 0));
+        return CF_OK;
+    }
+    constexpr int kParts = 1024;
+    double* p = nullptr;
+    if (pool_malloc((void**)&p, sizeof(double) * (kParts + 1), s) != cudaSuccess)
+        return fail(CF_ERR_NOMEM, "device allocation of the amplitude sum failed");
+    k_sumsq_partial<<<kParts, 256, 0, s>>>(e->s32, e->grid.mtotal, p + 1);
+    k_sumsq_final<<<1, 256, 0, s>>>(p + 1, kParts, p);
+    CF_CHECK_LAUNCH();
+    CF_CUDA(cudaEventCreateWithFlags(&e->sumsq_ready, cudaEventDisableTiming));
+    CF_CUDA(cudaEventRecord(e->sumsq_ready, s));
+    e->sumsq = p;
     return CF_OK;
 }
 
@@ -199,6 +268,9 @@ extern "C" cf_status cf_embedding_free(cf_embedding* e) {
     }
     if (e->lambda) cudaFreeAsync(e->lambda, fs);
     if (e->s64) cudaFreeAsync(e->s64, fs);
+    if (e->sumsq) cudaFreeAsync(e->sumsq, fs);
+    if (e->s64_ready) cudaEventDestroy(e->s64_ready);
+    if (e->sumsq_ready) cudaEventDestroy(e->sumsq_ready);
     if (e->s32) cudaFreeAsync(e->s32, fs);
     cudaSetDevice(prev);
     delete e;

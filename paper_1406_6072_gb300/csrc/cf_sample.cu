@@ -6,6 +6,10 @@
 
 #include <stdlib.h>
 
+#include <map>
+#include <mutex>
+#include <string>
+
 namespace cf {
 
 #ifndef CF_SROWS_E
@@ -115,21 +119,48 @@ static size_t per_realization_bytes(const GridInfo& g, size_t elem) {
     return elem * ((size_t)g.m[0] * g.m[1] * g.n[2] + (size_t)g.m[0] * g.n[1] * g.n[2]);
 }
 
-// Target bytes of one chunk's intermediates (kept L2-resident between passes).
+// Target bytes of one chunk's intermediates: large launches (measured faster
+// than L2-sized chunks whose intermediate stays in L2); CF_CHUNK_MB overrides.
 static size_t chunk_target_bytes() {
     static size_t v = [] {
         const char* e = getenv("CF_CHUNK_MB");
-        long mb = e ? atol(e) : 48;
+        long mb = e ? atol(e) : 1024;
         if (mb < 1) mb = 1;
         return (size_t)mb << 20;
     }();
     return v;
 }
 
+// Tensor-core modes (cf_tc.cu).
+cf_status tc_check_grid(const GridInfo& g);
+size_t tc_bytes_per_realization(const GridInfo& g);
+size_t tc_header_bytes();
+cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0, int R, float* fields, void* ws,
+                    size_t ws_bytes, int chunk, double amp_scale, cudaStream_t st);
+
+// Tuned chunk per (device, grid shape, element size), set by cf_tune_sample.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tuned_chunk;
+
+static std::string tune_key(const GridInfo& g, size_t elem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    char b[128];
+    snprintf(b, sizeof b, "%d:%d:%lld:%lld:%lld:%zu", dev, g.ndim, g.m[0], g.m[1], g.m[2], elem);
+    return b;
+}
+
+static int tuned_chunk(const GridInfo& g, size_t elem) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_chunk.find(tune_key(g, elem));
+    return it == g_tuned_chunk.end() ? 0 : it->second;
+}
+
 static int pick_chunk(const GridInfo& g, size_t elem, int R, size_t ws_bytes) {
     const size_t per = per_realization_bytes(g, elem);
     if (per == 0) return R < 65535 ? R : 65535;  // grid.y bound
-    size_t c = chunk_target_bytes() / per;
+    const int tuned = tuned_chunk(g, elem);
+    size_t c = tuned > 0 ? (size_t)tuned : chunk_target_bytes() / per;
     if (c < 1) c = 1;
     if (c > (size_t)R) c = (size_t)R;
     if (c > 65535) c = 65535;
@@ -192,10 +223,17 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
     return CF_OK;
 }
 
-static cf_status check_sample_args(const cf_embedding* e, uint64_t r0, int32_t R, cf_dtype dt) {
+static bool is_tc(cf_dtype dt) { return dt == CF_BF16_TC || dt == CF_F16_TC; }
+
+static cf_status check_sample_args(const cf_embedding* e, uint64_t r0, int32_t R, cf_dtype dt, bool tc_ok = false) {
     if (!e) return fail(CF_ERR_ARG, "embedding is NULL");
     if (R < 0) return fail(CF_ERR_ARG, "R must be >= 0");
-    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    if (is_tc(dt)) {
+        if (!tc_ok) return fail(CF_ERR_UNSUPPORTED, "dtype %d is available in cf_sample only", dt);
+        CF_TRY(tc_check_grid(e->grid));
+    } else if (dt != CF_F32 && dt != CF_F64) {
+        return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    }
     if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
     return CF_OK;
 }
@@ -281,6 +319,12 @@ using namespace cf;
 extern "C" cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, cf_dtype dt, size_t* bytes) {
     clear_error();
     if (!e || !bytes) return fail(CF_ERR_ARG, "NULL argument");
+    if (is_tc(dt)) {
+        CF_TRY(tc_check_grid(e->grid));
+        const int chunk = pick_chunk(e->grid, 4, R < 1 ? 1 : R, (size_t)-1);
+        *bytes = tc_header_bytes() + tc_bytes_per_realization(e->grid) * (size_t)(chunk < 1 ? 1 : chunk);
+        return CF_OK;
+    }
     if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
     const size_t elem = dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>);
     const size_t per = per_realization_bytes(e->grid, elem);
@@ -292,10 +336,21 @@ extern "C" cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, 
 extern "C" cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, cf_dtype dt,
                                void* fields_out, void* ws, size_t ws_bytes, cf_stream_t s) {
     clear_error();
-    CF_TRY(check_sample_args(e, r0, R, dt));
+    CF_TRY(check_sample_args(e, r0, R, dt, true));
     if (!fields_out) return fail(CF_ERR_ARG, "fields_out is NULL");
     if (R == 0) return CF_OK;
     CF_TRY(enter((cudaStream_t)s));
+    if (is_tc(dt)) {
+        const size_t head = tc_header_bytes();
+        const int chunk = ws && ws_bytes > head ? pick_chunk(e->grid, 4, R, ws_bytes - head) : 0;
+        if (chunk < 1)
+            return fail(CF_ERR_NOMEM, "workspace of %zu bytes holds no realization (%zu needed)", ws_bytes,
+                        head + tc_bytes_per_realization(e->grid));
+        CF_TRY(sample_tc(e, dt == CF_BF16_TC, seed, r0, R, (float*)fields_out, ws, ws_bytes, chunk, 1.0,
+                         (cudaStream_t)s));
+        record_use(const_cast<cf_embedding*>(e), (cudaStream_t)s);
+        return CF_OK;
+    }
     if (dt == CF_F32) return sample_impl<float>(e, seed, r0, R, fields_out, nullptr, ws, ws_bytes, 1.0, (cudaStream_t)s);
     return sample_impl<double>(e, seed, r0, R, fields_out, nullptr, ws, ws_bytes, 1.0, (cudaStream_t)s);
 }
@@ -311,6 +366,66 @@ extern "C" cf_status cf_sample_lp(const cf_embedding* e, uint64_t seed, uint64_t
     if (R == 0) return CF_OK;
     CF_TRY(enter((cudaStream_t)s));
     return sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, (cudaStream_t)s);
+}
+
+extern "C" cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, void* ws, size_t ws_bytes,
+                                    void* fields_scratch, cf_stream_t s, int32_t* chunk_out, double* ms_out) {
+    clear_error();
+    CF_TRY(check_sample_args(e, 0, R, dt));
+    if (R < 1 || !fields_scratch) return fail(CF_ERR_ARG, "R >= 1 and fields_scratch are required");
+    CF_TRY(enter((cudaStream_t)s));
+    const cudaStream_t st = (cudaStream_t)s;
+    const size_t elem = dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>);
+    const size_t per = per_realization_bytes(e->grid, elem);
+    const std::string key = tune_key(e->grid, elem);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_chunk.erase(key);
+    }
+    cudaEvent_t a, b;
+    CF_CUDA(cudaEventCreate(&a));
+    CF_CUDA(cudaEventCreate(&b));
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int c = 1; c <= R; c *= 2) {
+        if (per > 0 && per * (size_t)c > ws_bytes) break;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned_chunk[key] = c;
+        }
+        cf_status r = CF_OK;
+        for (int rep = 0; rep < 3 && r == CF_OK; ++rep) {  // warm-up, then two timed runs
+            if (rep == 1) cudaEventRecord(a, st);
+            r = dt == CF_F32 ? sample_impl<float>(e, 1, 0, R, fields_scratch, nullptr, ws, ws_bytes, 1.0, st)
+                             : sample_impl<double>(e, 1, 0, R, fields_scratch, nullptr, ws, ws_bytes, 1.0, st);
+        }
+        cudaEventRecord(b, st);
+        if (r != CF_OK) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned_chunk.erase(key);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return r;
+        }
+        CF_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms *= 0.5f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+        if (per == 0) break;  // one-dimensional grids have no intermediate
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_chunk[key] = best;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (chunk_out) *chunk_out = best;
+    if (ms_out) *ms_out = (double)best_ms / (double)R;
+    return CF_OK;
 }
 
 extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_t ncells, int64_t m_last,

@@ -98,9 +98,9 @@ class CudaBackend : public cfserve::Backend {
         const GridInfo g = grid_of(j->req);
         const size_t cells = (size_t)g.ncell * 2 * (size_t)j->req.R;
         cudaStream_t s = slots_[slot].stream;
-        if (cudaMallocAsync(&j->dev_fields, cells * sizeof(float), s) != cudaSuccess)
+        if (pool_malloc(&j->dev_fields, cells * sizeof(float), s) != cudaSuccess)
             return fail(CF_ERR_NOMEM, "result allocation failed");
-        if (j->req.want_counts && cudaMallocAsync(&j->dev_counts, cells * sizeof(int32_t), s) != cudaSuccess)
+        if (j->req.want_counts && pool_malloc(&j->dev_counts, cells * sizeof(int32_t), s) != cudaSuccess)
             return fail(CF_ERR_NOMEM, "result allocation failed");
         result_stream_[j] = s;
         return CF_OK;
@@ -153,7 +153,7 @@ class CudaBackend : public cfserve::Backend {
         CF_CUDA(cudaMemcpyAsync(sl.dev_desc, sl.host_desc, sizeof(RealDesc) * (size_t)n, cudaMemcpyHostToDevice,
                                 sl.stream));
         const size_t wsb = sample_chunk_bytes(g, n);
-        if (wsb && cudaMallocAsync(&sl.ws, wsb, sl.stream) != cudaSuccess)
+        if (wsb && pool_malloc(&sl.ws, wsb, sl.stream) != cudaSuccess)
             return fail(CF_ERR_NOMEM, "batch workspace allocation failed");
         CF_TRY(sample_batch_f32(g, sl.dev_desc, n, sl.ws, wsb, sl.stream));
         for (auto* j : jobs) {
@@ -224,7 +224,9 @@ extern "C" cf_status cf_serve_submit(cf_server* sv, const cf_request* req, uint6
     GridInfo g;
     CF_TRY(check_grid(&req->grid, &g));
     const cf_status st = sv->sched->submit(*req, ticket);
-    if (st == CF_ERR_ARG) return fail(st, "invalid request (R >= 1, amp > 0, scale > 0, parametric xi required)");
+    if (st == CF_ERR_ARG)
+        return fail(st, "invalid request (1 <= R <= max_batch_realizations, amp > 0, scale > 0, parametric xi "
+                        "required)");
     if (st == CF_ERR_BUSY) return fail(st, "queue full or server stopping");
     return st;
 }

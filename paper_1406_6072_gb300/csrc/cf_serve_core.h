@@ -129,6 +129,7 @@ class Scheduler {
         for (int a = 0; a < r.grid.ndim; ++a)
             if (r.grid.n[a] < 1) return CF_ERR_ARG;
         if (r.r0 + (uint64_t)r.R > (1ull << 32)) return CF_ERR_ARG;
+        if (r.R > cfg_.max_batch_realizations) return CF_ERR_ARG;  // a request runs in one launch
         std::lock_guard<std::mutex> lk(mu_);
         if (stopping_) return CF_ERR_BUSY;
         if ((int)queue_.size() >= cfg_.queue_capacity) {

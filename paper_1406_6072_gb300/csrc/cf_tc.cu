@@ -1,0 +1,467 @@
+// cf_tc.cu -- the per-realization inverse transforms of section 2 (closing
+// paragraph: the field is the inverse DFT of sqrt(lambda) times white noise)
+// run as DFT-matrix GEMMs on the fifth-generation tensor cores:
+// cf_dtype CF_BF16_TC and CF_F16_TC.
+//
+// A line of L = 16^S points is transformed in S radix-16 stages.  With
+// n = n_0 + 16 n_1 (+ 256 n_2) and k = k_0 + 16 k_1 (+ 256 k_2), stage s is the
+// 16-point DFT over the most significant untransformed digit, written as a
+// real GEMM: A rows are the other digits (L/16 rows per line), A columns the
+// 16 complex inputs interleaved as (re, im) (K = 32); B is the real 32 x 32
+// form of the 16-point DFT matrix; D (binary32, in tensor memory) holds the 16
+// complex outputs of each row.  Between stages the epilogue multiplies by the
+// twiddle factors w_L^{u k} in binary32, rounds to the 16-bit input type and
+// scatters into the next stage's A.  The DFT matrix is split into a 16-bit
+// head and a 16-bit remainder (two MMAs accumulate A*B_hi + A*B_lo), so its
+// entries act at nearly binary32 accuracy; the data are rounded to 16 bits
+// at every stage, which sets the error of these modes.
+//
+// 2D only: pass 1 draws the noise of one embedded row per line (the same
+// binary32 noise as CF_F32), scales it and transforms the last axis, keeping
+// n1 outputs (16-bit complex intermediate [M0][n1]); pass 2 transforms the
+// columns, keeping n0 outputs, and writes the Re/Im fields in binary32.
+// The inputs are pre-scaled by a power of two alpha chosen from sum(s^2)
+// (computed once per embedding) so the intermediate has unit mean square
+// (range of fp16); the fields are multiplied by 1/alpha at the end.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "cf_device.cuh"
+#include "cf_kernels.cuh"
+#include "cf_tc.cuh"
+
+namespace cf {
+namespace {
+
+constexpr int kWgRows = 1024;                // A rows per warpgroup and stage
+constexpr int kTiles = kWgRows / 128;        // M = 128 tiles per warpgroup
+// A: the 4 core matrices of a row group (K = 32) are contiguous (LBO = 128),
+// row groups 528 bytes apart (16 bytes of padding shift rows r and r + 8 by
+// four banks).  Every descriptor's reach stays inside the operand whichever
+// of the two strides is taken along K.
+constexpr int kLBO = 128;                    // K-direction core-matrix stride
+constexpr int kSBO = 4 * 128 + 16;           // row-direction core-matrix stride
+constexpr int kABytes = (kWgRows / 8) * kSBO;
+constexpr int kBBytes = 32 * 32 * 2;         // one 32 x 32 16-bit matrix
+constexpr int kThreads = 256;                // two warpgroups, each with its own lines
+constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 64;
+constexpr uint32_t kTmemCols = 512;          // 256 per warpgroup: 8 tiles x 32 columns
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per tensor-core wait
+
+__device__ unsigned int g_tc_faults;         // waits that ran out of time
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase; a wait that runs out is counted.
+__device__ __forceinline__ void wait_phase(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > kWaitNs) {
+            atomicAdd(&g_tc_faults, 1u);
+            return;
+        }
+    }
+}
+
+// Input scale alpha = 2^-round(log2(sqrt(sum(s^2) * factor))), factor =
+// 2 L1 amp^2 / M^d: the mean square of the row-transformed intermediate is
+// 2 L1 amp^2 sum(s^2) / M^d (E|eps|^2 = 2, the row transform multiplies the
+// mean square by L1), so alpha brings it to about 1.  inverse: 1/alpha.
+__device__ __forceinline__ float input_scale(const double* __restrict__ sumsq, double factor, bool inverse) {
+    const double ms = sumsq[0] * factor;
+    int e = ms > 0.0 ? (int)lrint(-0.5 * log2(ms)) : 0;
+    e = e < -60 ? -60 : (e > 60 ? 60 : e);
+    return ldexpf(1.0f, inverse ? -e : e);
+}
+
+__device__ __forceinline__ uint32_t a_off(int r, int kappa) {
+    return (uint32_t)((r >> 3) * kSBO + (kappa >> 3) * kLBO + (r & 7) * 16 + (kappa & 7) * 2);
+}
+
+// B (N = 32 rows n, K = 32): core matrices of a row group contiguous (LBO =
+// 128), row groups 512 bytes apart.
+__device__ __forceinline__ uint32_t b_off(int n, int kappa) {
+    return (uint32_t)((n >> 3) * 512 + (kappa >> 3) * 128 + (n & 7) * 16 + (kappa & 7) * 2);
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float re, float im) {
+    if constexpr (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __half2 h = __floats2half2_rn(re, im);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t round16(float v, float& back) {
+    if constexpr (BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        back = __bfloat162float(h);
+        return *reinterpret_cast<const uint16_t*>(&h);
+    } else {
+        const __half h = __float2half_rn(v);
+        back = __half2float(h);
+        return *reinterpret_cast<const uint16_t*>(&h);
+    }
+}
+
+__device__ __forceinline__ C2<float> cmulf(C2<float> a, C2<float> b) {
+    return mk(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Real 32 x 32 form of the 16-point inverse DFT matrix, head and remainder:
+// B(2j + pj, 2k + pk) from w16^{jk} = c + i s: (c, s; -s, c).
+template <bool BF16>
+__device__ void build_dft16(unsigned char* bhi, unsigned char* blo, const C2<float>* __restrict__ tw) {
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+        const int kappa = e & 31, n = e >> 5;
+        const int j = kappa >> 1, pj = kappa & 1, k = n >> 1, pk = n & 1;
+        const C2<float> w = tw[((j * k) & 15) * (TWN / 16)];
+        const float v = pj == 0 ? (pk == 0 ? w.x : w.y) : (pk == 0 ? -w.y : w.x);
+        float back;
+        const uint16_t h = round16<BF16>(v, back);
+        float unused;
+        const uint16_t l = round16<BF16>(v - back, unused);
+        *reinterpret_cast<uint16_t*>(bhi + b_off(n, kappa)) = h;
+        *reinterpret_cast<uint16_t*>(blo + b_off(n, kappa)) = l;
+    }
+}
+
+// One stage of the warpgroup's 8 tiles: D_t = A_t * (B_hi + B_lo), N outputs.
+template <int N, bool BF16>
+__device__ __forceinline__ void issue_stage(uint32_t a_addr, uint32_t bhi, uint32_t blo, uint32_t tmem,
+                                            uint32_t bar) {
+    constexpr uint32_t idesc = tc::idesc_f16(128, N, BF16);
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int t = 0; t < kTiles; ++t) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint64_t ad = tc::sdesc(a_addr + (uint32_t)(t * 16 * kSBO + c * 2 * kLBO), kLBO, kSBO);
+            tc::mma_f16(tmem + 32 * t, ad, tc::sdesc(bhi + c * 256, 128, 512), idesc, c > 0 ? 1u : 0u);
+            tc::mma_f16(tmem + 32 * t, ad, tc::sdesc(blo + c * 256, 128, 512), idesc, 1u);
+        }
+    }
+    tc::mma_commit(bar);
+}
+
+// Twiddle w_L^{u k}, k = 0..15, applied to the 16 outputs of one row and
+// scattered into the next stage's A (row dst0 + dstride k, column pair kk).
+template <bool BF16>
+__device__ __forceinline__ void twiddle_scatter(const uint32_t (&r)[32], const C2<float>* __restrict__ tw, int step,
+                                                unsigned char* A, int dst0, int dstride, int kk) {
+    const C2<float> w1 = tw[step & (TWN - 1)];
+    const C2<float> w4 = tw[(4 * step) & (TWN - 1)];
+    const C2<float> w2 = cmulf(w1, w1), w3 = cmulf(w2, w1);
+    const C2<float> w8 = cmulf(w4, w4), w12 = cmulf(w8, w4);
+    const C2<float> wb[4] = {mk(1.0f, 0.0f), w1, w2, w3};
+    const C2<float> wa[4] = {mk(1.0f, 0.0f), w4, w8, w12};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int k = 4 * a + b;
+            const C2<float> w = (a == 0) ? wb[b] : (b == 0 ? wa[a] : cmulf(wa[a], wb[b]));
+            const C2<float> y = cmulf(mk(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1])), w);
+            *reinterpret_cast<uint32_t*>(A + a_off(dst0 + dstride * k, kk)) = pack2<BF16>(y.x, y.y);
+        }
+    }
+}
+
+// Epilogue of stage `stage` (< S) for local A row `row` of this warpgroup.
+template <int S, int stage, bool BF16>
+__device__ __forceinline__ void stage_epilogue(const uint32_t (&r)[32], int row, const C2<float>* __restrict__ tw,
+                                               unsigned char* A) {
+    constexpr int L = S == 3 ? 4096 : 256;
+    constexpr int RPL = L / 16;
+    const int line = row / RPL, lrow = row % RPL;
+    const int base = line * RPL;
+    if constexpr (S == 3 && stage == 1) {
+        // rows (n0, n1) -> next rows (n0, k0), column n1; twiddle w^{(n0 + 16 n1) k0}
+        twiddle_scatter<BF16>(r, tw, lrow * (TWN / L), A, base + (lrow & 15), 16, 2 * (lrow >> 4));
+    } else if constexpr (S == 3 && stage == 2) {
+        // rows (n0, k0) -> next rows (k0, k1), column n0; twiddle w^{16 n0 k1}
+        twiddle_scatter<BF16>(r, tw, 16 * (lrow & 15) * (TWN / L), A, base + (lrow >> 4), 16, 2 * (lrow & 15));
+    } else {
+        // S == 2: rows n0 -> next rows k0, column n0; twiddle w^{n0 k0}
+        twiddle_scatter<BF16>(r, tw, lrow * (TWN / L), A, base, 1, 2 * lrow);
+    }
+}
+
+// Kept output points of the last stage: row (k0[, k1]) holds k = row + (L/16) k_last, k_last < 8.
+template <int S>
+__device__ __forceinline__ int out_point(int lrow, int klast) {
+    return lrow + (S == 3 ? 256 : 16) * klast;
+}
+
+// Runs the S stages of one warpgroup on its A (loaded, fenced, synchronised),
+// calling sink(line, point, re, im) for every kept output.
+template <int S, bool BF16, class Sink>
+__device__ __forceinline__ void run_stages(unsigned char* A, uint32_t a_addr, uint32_t bhi, uint32_t blo,
+                                           uint32_t tmem, uint32_t bar, uint32_t& phase,
+                                           const C2<float>* __restrict__ tw, int wg, Sink&& sink) {
+    constexpr int L = S == 3 ? 4096 : 256;
+    constexpr int RPL = L / 16;
+    const int wtid = threadIdx.x & 127;
+    const int warp = wtid >> 5, lane = wtid & 31;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+#pragma unroll 1
+    for (int stage = 1; stage <= S; ++stage) {
+        const bool last = stage == S;
+        if (wtid == 0) {
+            if (last)
+                issue_stage<16, BF16>(a_addr, bhi, blo, tmem, bar);
+            else
+                issue_stage<32, BF16>(a_addr, bhi, blo, tmem, bar);
+        }
+        wait_phase(bar, phase);
+        phase ^= 1u;
+        __syncwarp();  // tcgen05.ld is warp-collective: reconverge after the per-thread wait
+        tc::fence_after_sync();
+#pragma unroll 1
+        for (int t = 0; t < kTiles; ++t) {
+            const int row = 128 * t + 32 * warp + lane;
+            uint32_t r[32];
+            const uint32_t taddr = tmem + lane_base + 32 * t;
+            if (last)
+                tc::tmem_ld16(taddr, r);
+            else
+                tc::tmem_ld32(taddr, r);
+            tc::tmem_ld_wait(r);
+            if (last) {
+                const int line = row / RPL, lrow = row % RPL;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    sink(line, out_point<S>(lrow, k), __uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+            } else if (stage == 1) {
+                stage_epilogue<S, 1, BF16>(r, row, tw, A);
+            } else {
+                stage_epilogue<S, 2, BF16>(r, row, tw, A);
+            }
+        }
+        tc::fence_before_sync();
+        if (!last) tc::fence_proxy_async_smem();
+        tc::bar_sync(1 + wg, 128);
+    }
+}
+
+struct TcShared {
+    unsigned char* A;     // this warpgroup's operand
+    uint32_t a_addr, bhi, blo, tmem, bar;
+};
+
+// Common prologue: barriers, tensor memory, DFT matrices.  Returns this
+// warpgroup's view.
+template <bool BF16>
+__device__ __forceinline__ TcShared tc_prologue(unsigned char* smraw, const C2<float>* __restrict__ tw, int wg) {
+    unsigned char* A0 = smraw;
+    unsigned char* Bh = smraw + 2 * kABytes;
+    unsigned char* Bl = Bh + kBBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bl + kBBytes);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_u32(&bars[0]), 1);
+        tc::mbar_init(tc::smem_u32(&bars[1]), 1);
+        tc::fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(tc::smem_u32(tslot), kTmemCols);
+        tc::tmem_relinquish();
+    }
+    build_dft16<BF16>(Bh, Bl, tw);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    TcShared s;
+    s.A = A0 + wg * kABytes;
+    s.a_addr = tc::smem_u32(s.A);
+    s.bhi = tc::smem_u32(Bh);
+    s.blo = tc::smem_u32(Bl);
+    s.tmem = *tslot + (uint32_t)(256 * wg);
+    s.bar = tc::smem_u32(&bars[wg]);
+    return s;
+}
+
+__device__ __forceinline__ void tc_epilogue(unsigned char* smraw) {
+    const uint32_t* tslot =
+        reinterpret_cast<const uint32_t*>(smraw + 2 * kABytes + 2 * kBBytes + 2 * sizeof(uint64_t));
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(*tslot, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------- pass 1
+// Rows of the embedded grid (L = M1): noise, scale, transform, keep n1 = L/2.
+// Block: 2 * LPW consecutive rows of realization r0 + blockIdx.y.
+template <int S, bool BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_rows(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
+              long long nrows, uint32_t* __restrict__ inter, const double* __restrict__ sumsq, double factor,
+              const C2<float>* __restrict__ tw) {
+    constexpr int L = S == 3 ? 4096 : 256;
+    constexpr int RPL = L / 16;
+    constexpr int LPW = kWgRows / RPL;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const int wg = threadIdx.x >> 7, wtid = threadIdx.x & 127;
+    const TcShared sh = tc_prologue<BF16>(tc_smem, tw, wg);
+    const float alpha = input_scale(sumsq, factor, false);
+    const uint32_t r = r0 + blockIdx.y;
+    const long long row0 = (long long)blockIdx.x * (2 * LPW) + wg * LPW;
+    // loader: pairs (col, col + L/2) of each line share one Philox call
+#pragma unroll 1
+    for (int q = wtid; q < LPW * (L / 2); q += 128) {
+        const int g = q / (L / 2), col = q % (L / 2);
+        const long long row = row0 + g;
+        C2<float> lo, hi;
+        noise_pair_f32((unsigned long long)row * (L / 2) + col, r, key0, key1, lo, hi);
+        const float* srow = s + (size_t)row * L;
+        const C2<float> xl = cscale(cscale(lo, srow[col] * amp_scale), alpha);
+        const C2<float> xh = cscale(cscale(hi, srow[col + L / 2] * amp_scale), alpha);
+        const int ch = col + L / 2;
+        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + col % RPL, 2 * (col / RPL))) = pack2<BF16>(xl.x, xl.y);
+        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + ch % RPL, 2 * (ch / RPL))) = pack2<BF16>(xh.x, xh.y);
+    }
+    tc::fence_proxy_async_smem();
+    tc::bar_sync(1 + wg, 128);
+    uint32_t phase = 0;
+    uint32_t* out = inter + ((size_t)blockIdx.y * nrows + row0) * (L / 2);
+    run_stages<S, BF16>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
+                        [&](int line, int p, float re, float im) {
+                            out[(size_t)line * (L / 2) + p] = pack2<BF16>(re, im);
+                        });
+    tc_epilogue(tc_smem);
+}
+
+// ---------------------------------------------------------------- pass 2
+// Columns of the intermediate [M0][n1] (L = M0): transform, keep n0 = L/2,
+// write field 2r (Re) and 2r + 1 (Im) times 1/alpha.
+template <int S, bool BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_cols(const uint32_t* __restrict__ inter, long long n1, float* __restrict__ fields, long long cells,
+              const double* __restrict__ sumsq, double factor, const C2<float>* __restrict__ tw) {
+    constexpr int L = S == 3 ? 4096 : 256;
+    constexpr int RPL = L / 16;
+    constexpr int LPW = kWgRows / RPL;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const int wg = threadIdx.x >> 7, wtid = threadIdx.x & 127;
+    const TcShared sh = tc_prologue<BF16>(tc_smem, tw, wg);
+    const float inv_alpha = input_scale(sumsq, factor, true);
+    const long long c0 = (long long)blockIdx.x * (2 * LPW) + wg * LPW;
+    const uint32_t* in = inter + (size_t)blockIdx.y * L * n1;
+#pragma unroll 1
+    for (int q = wtid; q < LPW * L; q += 128) {
+        const int g = q % LPW, n = q / LPW;
+        const uint32_t v = in[(size_t)n * n1 + c0 + g];
+        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + n % RPL, 2 * (n / RPL))) = v;
+    }
+    tc::fence_proxy_async_smem();
+    tc::bar_sync(1 + wg, 128);
+    uint32_t phase = 0;
+    float* f0 = fields + (size_t)blockIdx.y * 2 * cells;
+    run_stages<S, BF16>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
+                        [&](int line, int p, float re, float im) {
+                            const size_t o = (size_t)p * n1 + c0 + line;
+                            f0[o] = re * inv_alpha;
+                            f0[o + cells] = im * inv_alpha;
+                        });
+    tc_epilogue(tc_smem);
+}
+
+template <bool BF16>
+cf_status launch_tc(int S, bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
+                    uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
+                    long long cells, const double* sumsq, double factor) {
+    const C2<float>* tw = twiddles_f32();
+    if (rows) {
+        auto kern = S == 3 ? k_tc_rows<3, BF16> : k_tc_rows<2, BF16>;
+        CF_TRY(prepare_smem(kern, kSmem));
+        ScopedKernelTimer kt(st, BF16 ? "tc_rows_bf16" : "tc_rows_f16", S == 3 ? 4096 : 256);
+        kern<<<grid, kThreads, kSmem, st>>>(s, amp, key0, key1, r0, nrows, inter, sumsq, factor, tw);
+    } else {
+        auto kern = S == 3 ? k_tc_cols<3, BF16> : k_tc_cols<2, BF16>;
+        CF_TRY(prepare_smem(kern, kSmem));
+        ScopedKernelTimer kt(st, BF16 ? "tc_cols_bf16" : "tc_cols_f16", S == 3 ? 4096 : 256);
+        kern<<<grid, kThreads, kSmem, st>>>(inter, n1, fields, cells, sumsq, factor, tw);
+    }
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+int stages_of(long long L) { return L == 4096 ? 3 : (L == 256 ? 2 : 0); }
+
+}  // namespace
+
+// Lines per block of a pass with line length L (two warpgroups).
+static long long tc_lines_per_block(long long L) { return 2 * (kWgRows / (L / 16)); }
+
+cf_status tc_check_grid(const GridInfo& g) {
+    if (g.ndim != 2 || !stages_of(g.m[0]) || !stages_of(g.m[1]))
+        return fail(CF_ERR_UNSUPPORTED,
+                    "tensor-core modes need a 2D grid with embedded sides 256 or 4096 (got %dD, %lld x %lld)",
+                    g.ndim, g.m[0], g.ndim > 1 ? g.m[1] : 0);
+    return CF_OK;
+}
+
+size_t tc_bytes_per_realization(const GridInfo& g) { return 4 * (size_t)g.m[0] * (size_t)g.n[1]; }
+size_t tc_header_bytes() { return 0; }
+
+// Fields [R][2][n0][n1] (binary32) of realizations r0.. through the tensor
+// cores; ws: header + chunk intermediates.
+cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0, int R, float* fields, void* ws,
+                    size_t ws_bytes, int chunk, double amp_scale, cudaStream_t st) {
+    const GridInfo& g = e->grid;
+    CF_TRY(tc_check_grid(g));
+    CF_TRY(ensure_sumsq(const_cast<cf_embedding*>(e), st));
+    const double* sumsq = e->sumsq;
+    const double factor = 2.0 * (double)g.m[1] * amp_scale * amp_scale / (double)g.mtotal;
+    uint32_t* inter = (uint32_t*)ws;
+    const int S0 = stages_of(g.m[0]), S1 = stages_of(g.m[1]);
+    const long long cells = g.ncell;
+    for (int c0 = 0; c0 < R; c0 += chunk) {
+        const int nr = (R - c0) < chunk ? (R - c0) : chunk;
+        const dim3 g1((unsigned)(g.m[0] / tc_lines_per_block(g.m[1])), (unsigned)nr);
+        const dim3 g2((unsigned)(g.n[1] / tc_lines_per_block(g.m[0])), (unsigned)nr);
+        const uint32_t rr = (uint32_t)(r0 + (uint64_t)c0);
+        float* f = fields + (size_t)c0 * 2 * (size_t)cells;
+        if (bf16) {
+            CF_TRY(launch_tc<true>(S1, true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                   rr, g.m[0], inter, g.n[1], nullptr, cells, sumsq, factor));
+            CF_TRY(launch_tc<true>(S0, false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
+                                   factor));
+        } else {
+            CF_TRY(launch_tc<false>(S1, true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed,
+                                    (uint32_t)(seed >> 32), rr, g.m[0], inter, g.n[1], nullptr, cells, sumsq, factor));
+            CF_TRY(launch_tc<false>(S0, false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
+                                    factor));
+        }
+    }
+    return CF_OK;
+}
+
+}  // namespace cf
+
+extern "C" cf_status cf_tc_faults(cf_stream_t s, uint32_t* count) {
+    using namespace cf;
+    clear_error();
+    if (!count) return fail(CF_ERR_ARG, "count is NULL");
+    CF_TRY(enter((cudaStream_t)s));
+    CF_CUDA(cudaStreamSynchronize((cudaStream_t)s));
+    unsigned int v = 0, zero = 0;
+    CF_CUDA(cudaMemcpyFromSymbol(&v, g_tc_faults, sizeof v));
+    CF_CUDA(cudaMemcpyToSymbol(g_tc_faults, &zero, sizeof zero));
+    *count = v;
+    return CF_OK;
+}

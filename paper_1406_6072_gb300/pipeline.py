@@ -56,6 +56,19 @@ class FieldPipeline:
             self.ws = torch.empty(max(need, 1), dtype=torch.uint8, device=self.dev)
         return self.emb.report
 
+    def tune(self):
+        """Times the sampler's chunk schedules on this workload's grid (the
+        pipeline's field buffer serves as scratch) and keeps the fastest for
+        later calls; returns (chunk, ms per realization)."""
+        per = cf.cf_sample_workspace_size(self.emb, 1, self.dtype)
+        cap = per * self.R
+        ws = torch.empty(max(cap, 1), dtype=torch.uint8, device=self.dev)
+        chunk, ms = cf.cf_tune_sample(self.emb, self.dtype, self.R, ws, cap, self.fields, self.stream)
+        del ws
+        self.ws_bytes = cf.cf_sample_workspace_size(self.emb, self.R, self.dtype)
+        self.ws = torch.empty(max(self.ws_bytes, 1), dtype=torch.uint8, device=self.dev)
+        return chunk, ms
+
     def sample(self, r0=0):
         wl = self.wl
         if self.with_lp:

@@ -243,5 +243,17 @@ int main() {
         }
         printf("{\"scenario\": \"fifo\", \"started\": %zu, \"max_delay\": %ld}\n", be.start_order.size(), max_delay);
     }
+    {  // a request larger than one batch is refused at submission
+        FakeBackend be(1);
+        Scheduler s(make_cfg(1ull << 30, 1, 10, 2, 8), &be);
+        uint64_t a = 0, b = 0;
+        const cf_status too_big = s.submit(make_req(16, 2, 9, 2.0), &a);
+        const cf_status fits = s.submit(make_req(16, 2, 8, 2.0), &b);
+        cf_result r;
+        s.wait(b, 5000000, &r);
+        printf("{\"scenario\": \"oversize\", \"too_big\": %d, \"fits\": %d, \"status\": %d}\n", (int)too_big,
+               (int)fits, (int)r.status);
+        s.release(b);
+    }
     return 0;
 }

@@ -29,24 +29,28 @@ REQS = [((64, 64), cf.CF_XI_GAUSSIAN, 0.7, 3.0, 0.0, 11, 0, 3),
         ((256,), cf.CF_XI_EXPONENTIAL, 1.5, 6.0, 0.0, 16, 3, 5)]
 
 
-def _serve(sv, specs, want_counts=False):
-    tickets, outs = [], []
+def _serve(sv, specs, want_counts=False, first=None):
+    """Serves specs (host buffers pinned up front); `first` is submitted just
+    before them.  Returns (results, host outputs, ticket of `first`)."""
+    tickets, outs, reqs = [], [], []
     for n, kind, amp, scale, beta, seed, r0, R in specs:
         hf = _host((R, 2) + n)
         hc = _host((R, 2) + n, torch.int32) if want_counts else None
-        req = cf.make_request(n, kind, amp, scale, beta, seed=seed, r0=r0, R=R, want_counts=want_counts,
-                              sigma2=amp, nbar=2.0, lp_seed=seed + 1, host_fields=hf, host_counts=hc)
-        tickets.append(cf.cf_serve_submit(sv, req))
+        reqs.append(cf.make_request(n, kind, amp, scale, beta, seed=seed, r0=r0, R=R, want_counts=want_counts,
+                                    sigma2=amp, nbar=2.0, lp_seed=seed + 1, host_fields=hf, host_counts=hc))
         outs.append((hf, hc))
+    t_first = cf.cf_serve_submit(sv, first) if first is not None else None
+    for req in reqs:
+        tickets.append(cf.cf_serve_submit(sv, req))
     res = [cf.cf_serve_wait(sv, t, 30_000_000) for t in tickets]
     for t in tickets:
         cf.cf_serve_release(sv, t)
-    return res, outs
+    return res, outs, t_first
 
 
 def test_served_fields_match_cf_sample():
     sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=3))
-    res, outs = _serve(sv, REQS)
+    res, outs, _ = _serve(sv, REQS)
     for (n, kind, amp, scale, beta, seed, r0, R), r, (hf, _) in zip(REQS, res, outs):
         assert r["status"] == cf.CF_OK
         emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(kind, amp, scale, beta), cf.CF_EMBED_CLAMP)
@@ -76,11 +80,16 @@ def test_same_result_alone_and_in_a_mixed_batched_stream():
     alone_sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=1, max_batch_realizations=8))
     alone = []
     for s in specs[:12]:
-        _, outs = _serve(alone_sv, [s], want_counts=True)
+        _, outs, _ = _serve(alone_sv, [s], want_counts=True)
         alone.append(outs[0])
     cf.cf_serve_destroy(alone_sv)
-    mix_sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=4, max_batch_realizations=64))
-    res, outs = _serve(mix_sv, specs, want_counts=True)
+    # one slot, held by a large request while the mixed stream queues behind
+    # it, so that the queued requests of each shape are batched
+    mix_sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=1, max_batch_realizations=64))
+    big = cf.make_request((1024, 1024), cf.CF_XI_GAUSSIAN, 1.0, 4.0, R=64)
+    res, outs, blocker = _serve(mix_sv, specs, want_counts=True, first=big)
+    assert cf.cf_serve_wait(mix_sv, blocker, 30_000_000)["status"] == cf.CF_OK
+    cf.cf_serve_release(mix_sv, blocker)
     st = cf.cf_serve_stats(mix_sv)
     assert all(r["status"] == cf.CF_OK for r in res)
     assert st["batches"] < st["batched_requests"]  # requests were batched
@@ -94,7 +103,7 @@ def test_same_result_alone_and_in_a_mixed_batched_stream():
 def test_served_counts_match_standalone_poisson():
     sv = cf.cf_serve_create(cf.make_serve_cfg())
     spec = ((64, 64), cf.CF_XI_GAUSSIAN, 0.8, 3.0, 0.0, 21, 4, 3)
-    res, outs = _serve(sv, [spec], want_counts=True)
+    res, outs, _ = _serve(sv, [spec], want_counts=True)
     hf, hc = outs[0]
     f = hf.to(DEV)
     c = torch.empty(hc.shape, dtype=torch.int32, device=DEV)

@@ -81,3 +81,9 @@ def test_no_request_is_overtaken_by_more_than_a_batch(scenarios):
     s = scenarios["fifo"]
     assert s["started"] == 30
     assert s["max_delay"] <= 3  # max_batch_realizations
+
+
+def test_request_larger_than_a_batch_is_refused(scenarios):
+    s = scenarios["oversize"]
+    assert s["too_big"] == 1  # CF_ERR_ARG
+    assert s["fits"] == 0 and s["status"] == 0
