@@ -107,6 +107,13 @@ typedef struct {
 /* cf_embed flags */
 #define CF_EMBED_CLAMP 1u        /* set eigenvalues < -tau to zero instead of failing */
 #define CF_EMBED_SKIP_ERROR 2u   /* with CF_EMBED_CLAMP: skip the covariance-error pass */
+#define CF_EMBED_LOG1P 4u        /* xi is the correlation function of the lognormal
+                                    density delta; the Gaussian covariance embedded is
+                                    ln(1 + xi) (section 3.1, eq. (Lncov)).  xi must stay
+                                    above -1 (a table entry <= -1 gives CF_ERR_NOT_PSD);
+                                    the lognormal variance is then sigma^2 = ln(1 + xi(0)).
+                                    Not accepted by the serving loop (its cache scales
+                                    amplitudes linearly). */
 
 /* Outcome of the positivity check (section 2, eq. (condition)).
  * tau = 1e-12 lambda_max.  Eigenvalues in [-tau, tau] are set to zero (n_zeroed);
@@ -220,6 +227,42 @@ CF_API cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, v
  * resets the count.  A non-zero count means the affected fields are invalid. */
 CF_API cf_status cf_tc_faults(cf_stream_t s, uint32_t* count);
 
+/* ---------------------------------------------------------------- counts in cells
+ * Section 3.4.  Counts are int32 maps [nfields][cells]; f is the surface
+ * fraction [cells] (NULL: f = 1); cells with f = 0 are ignored.  All device
+ * pointers, asynchronous on s. */
+
+/* Histogram P(N) = #{i : f_i != 0, N_i = N} for N < nbins (larger counts are
+ * not binned) of every map: hist_out [nfields][nbins] (binary64 holding
+ * integers); optionally its mean [nbins] and unbiased covariance
+ * [nbins][nbins] over the maps.  nbins <= 1024, nfields <= 65535. */
+CF_API cf_status cf_cic_histogram(const int32_t* counts, int64_t cells, int64_t nfields, const float* f,
+                                  int32_t nbins, double* hist_out, double* mean_or_null, double* cov_or_null,
+                                  cf_stream_t s);
+
+/* Mean histogram of the Poisson-lognormal model, section 3.4:
+ * <P(N)> = int dA N(A; -sigma2_A/2, sigma2_A) sum_{f_i != 0} Poisson(N; nbar f_i e^A),
+ * N < nbins <= 64, by a 512-node trapezoid rule over +-10 standard deviations
+ * (pred_out [nbins], binary64). */
+CF_API cf_status cf_cic_prediction(double sigma2_A, double nbar, const float* f, int64_t cells, int32_t nbins,
+                                   double* pred_out, cf_stream_t s);
+
+/* The non-linear transform of eq. (As): out = A*, the root of
+ * exp(A) nbar_i sigma2_A + A = sigma2_A (N - 1/2), nbar_i = nbar f_i, per cell
+ * of every map (binary32 out [nfields][cells]; 0 where f = 0). */
+CF_API cf_status cf_astar(const int32_t* counts, const float* f, int64_t cells, int64_t nfields, double nbar,
+                          double sigma2_A, float* out, cf_stream_t s);
+
+/* Cumulative information of section 3.3, eq. (cuminfo), from the mean [nbins]
+ * and covariance [nbins][nbins] of binned power spectra (cf_power_spectrum):
+ * info_out[b] = sum_{b1, b2 <= b} [C^{-1}]_{b1 b2} over the bins up to b, with
+ * C_{12} = cov_{12} / (mean_1 mean_2).  Bins with mean <= 0 are left out (their
+ * entry repeats the previous one); from a bin whose pivot is not positive
+ * (too few fields for the number of bins) on, the entries are NaN.
+ * ws: device scratch of 8 (nbins^2 + nbins) + 4 nbins bytes; nbins <= 4096. */
+CF_API cf_status cf_cumulative_information(const double* mean, const double* cov, int32_t nbins, double* info_out,
+                                           void* ws, size_t ws_bytes, cf_stream_t s);
+
 /* Lognormal + Poisson parameters (section 3.1, eqs. (Lncov), (sampling)). */
 typedef struct {
     double sigma2;          /* variance of G: rho = exp(G - sigma2/2), delta = rho - 1 */
@@ -290,6 +333,32 @@ CF_API cf_status cf_power_spectrum_counts(const int32_t* counts, const float* f_
                                    int64_t nfields, const cf_bins* bins, double* pk_out,
                                    int64_t* nmodes_out, double* mean_or_null, double* cov_or_null,
                                    void* ws, size_t ws_bytes, cf_stream_t s);
+
+/* ---------------------------------------------------------------- plans
+ * The binary32 per-realization path of one embedding recorded once as a CUDA
+ * graph: R realizations drawn with `seed` (cf_sample's noise), the optional
+ * lognormal + Poisson step (lp: sigma2, nbar, seed, counts_out; no mask, no
+ * delta output) and, with bins, the power spectra of the 2R fields
+ * (pk_out [2R][nbins], nmodes_out, optional mean/cov) and of the count maps
+ * (pk_counts_out and its optional mean/cov; needs lp).  Each cf_plan_launch
+ * replays the graph on s and draws the next R realizations: launch k after
+ * creation (or after cf_plan_seek(r0)) covers [r0 + kR, r0 + (k+1)R), with
+ * results identical to cf_sample_lp / cf_power_spectrum on that range.  The
+ * realization counter lives on the device and advances inside the graph.
+ * The plan owns its workspaces; all output arrays are the caller's and must
+ * outlive the plan.  cf_plan_create synchronises s (one eager pass fills the
+ * library's caches before the capture). */
+typedef struct cf_plan cf_plan;
+CF_API cf_status cf_plan_create(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R,
+                                const cf_lp_params* lp_or_null, const cf_bins* bins_or_null, float* fields_out,
+                                double* pk_out, int64_t* nmodes_out, double* mean_or_null, double* cov_or_null,
+                                double* pk_counts_out, double* mean_counts_or_null, double* cov_counts_or_null,
+                                cf_stream_t s, cf_plan** out);
+CF_API cf_status cf_plan_launch(cf_plan* p, cf_stream_t s);
+/* Next launch starts at realization r0; synchronises s. */
+CF_API cf_status cf_plan_seek(cf_plan* p, uint64_t r0, cf_stream_t s);
+CF_API cf_status cf_plan_destroy(cf_plan* p);
+
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching (not in the paper; it

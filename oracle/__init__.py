@@ -5,9 +5,11 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library and its Python
 binding never import it; the two implementations share no code.
 
-The arithmetic lives in ``cf_oracle.c`` (plain C, binary64, compiled with
-``-ffp-contract=off``); this module only builds/loads it and marshals numpy
-arrays.  ``build()`` compiles it with gcc.
+The arithmetic of the sampler lives in ``cf_oracle.c`` (plain C, binary64,
+compiled with ``-ffp-contract=off``); this module builds/loads it and
+marshals numpy arrays.  ``build()`` compiles it with gcc.  The counts-in-cells
+functions of section 3.4 (histogram, mixture prediction, A*) are written here
+in plain numpy.
 """
 from __future__ import annotations
 
@@ -160,7 +162,10 @@ def fft_nd(x, sign):
 
 
 # ---------------------------------------------------------------- embedding
-def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None):
+def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, log1p=False):
+    """First row c of the circulant (step a1, section 2 eq. (grid)).  log1p:
+    xi is the correlation function of the lognormal density and the Gaussian
+    covariance is ln(1 + xi) (section 3.1, eq. (Lncov))."""
     dims, d = _dims(n)
     cellv = np.ones(3) if cell is None else np.asarray(list(cell) + [1.0] * (3 - len(cell)))
     M = [2 * int(v) for v in n]
@@ -168,6 +173,8 @@ def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None):
     tab = None if table is None else np.ascontiguousarray(table, dtype=np.float64).ravel()
     _lib_handle().or_embed_row(d, _ptr(dims), _ptr(cellv), kind, amp, scale, beta, _ptr(tab),
                                _ptr(c))
+    if log1p:
+        c = np.log1p(c)
     return c.reshape(M)
 
 
@@ -191,9 +198,9 @@ def psd(n, c, lam, clamp=False):
     return lp, s, rep.asdict()
 
 
-def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False):
+def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False, log1p=False):
     """Steps a1-a3: first row c, eigenvalues lambda, lambda+, sqrt(lambda+), report."""
-    c = embed_row(n, kind, amp, scale, beta, cell, table)
+    c = embed_row(n, kind, amp, scale, beta, cell, table, log1p)
     lam = eigenvalues(n, c)
     lp, s, rep = psd(n, c, lam, clamp)
     return {"c": c, "lambda": lam, "lambda_plus": lp, "sqrt_lambda": s, "report": rep}
@@ -280,3 +287,80 @@ def mean_cov(pk):
     cov = np.zeros((nb, nb))
     _lib_handle().or_mean_cov(_ptr(pk), F, nb, _ptr(mean), _ptr(cov))
     return mean, cov
+
+
+# ---------------------------------------------------------------- counts in cells (section 3.4)
+def cic_histogram(counts, f, nbins):
+    """P(N) = #{i : f_i != 0, N_i = N}, N < nbins, per map (rows of counts)."""
+    counts = np.asarray(counts).reshape(len(counts), -1)
+    keep = np.ones(counts.shape[1], bool) if f is None else (np.asarray(f).ravel() != 0)
+    out = np.zeros((counts.shape[0], nbins), dtype=np.float64)
+    for r, c in enumerate(counts):
+        v = c[keep]
+        v = v[(v >= 0) & (v < nbins)]
+        out[r] = np.bincount(v, minlength=nbins)[:nbins]
+    return out
+
+
+def cic_prediction(sigma2, nbar, f, nbins):
+    """<P(N)> = int dA N(A; -s^2/2, s^2) e^{NA}/N! sum_{f_i != 0} (nbar f_i)^N
+    e^{-nbar f_i e^A} (section 3.4), for N < nbins, each N by adaptive
+    quadrature (scipy.integrate.quad) over A in -s^2/2 +- 14 s, with a break
+    point at the peak of the Poisson factor, A = ln((N + 1/2) / mean(nbar f))."""
+    import math
+
+    from scipy import integrate
+    nb = nbar * (np.ones(1) if f is None else np.asarray(f, dtype=np.float64).ravel())
+    nb = nb[nb > 0]
+    lnb = np.log(nb)
+    sd = math.sqrt(sigma2)
+    lo, hi = -sigma2 / 2 - 14 * sd, -sigma2 / 2 + 14 * sd
+    out = np.zeros(nbins)
+    for N in range(nbins):
+        lg = math.lgamma(N + 1)
+
+        def integrand(A):
+            gauss = math.exp(-(A + sigma2 / 2) ** 2 / (2 * sigma2)) / math.sqrt(2 * math.pi * sigma2)
+            return gauss * float(np.sum(np.exp(N * (A + lnb) - nb * math.exp(A) - lg)))
+
+        peak = min(max(math.log((N + 0.5) / nb.mean()), lo + 1e-9), hi - 1e-9)
+        out[N] = integrate.quad(integrand, lo, hi, points=[peak], limit=400, epsabs=0.0, epsrel=1e-12)[0]
+    return out
+
+
+def astar(counts, f, nbar, sigma2):
+    """A*(N) of eq. (As): the root of e^A nbar f_i s^2 + A = s^2 (N - 1/2), by
+    bisection (the left side increases with A); 0 where f_i = 0."""
+    counts = np.asarray(counts, dtype=np.float64)
+    fb = np.ones(counts.shape[-1]) if f is None else np.asarray(f, dtype=np.float64).ravel()
+    k = nbar * fb * sigma2
+    c = sigma2 * (counts - 0.5)
+    hi = c.copy()                        # e^A k >= 0, so the root is <= c
+    lo = c - 60.0 - np.abs(c)            # k e^lo + lo - c < 0 there
+    kk = np.broadcast_to(k, counts.shape)
+    mask = kk > 0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        g = kk * np.exp(mid) + mid - c
+        lo = np.where(g < 0, mid, lo)
+        hi = np.where(g < 0, hi, mid)
+    return np.where(mask, 0.5 * (lo + hi), 0.0)
+
+
+# ---------------------------------------------------------------- cumulative information (section 3.3)
+def cumulative_information(mean, cov):
+    """I(<= b) = sum_{b1, b2 <= b} [C_b^{-1}]_{b1 b2}, C_{12} = cov_{12} / (mean_1 mean_2)
+    over the bins up to b with a positive mean (eq. (cuminfo)); bins without
+    modes repeat the previous value.  Each prefix matrix is inverted directly."""
+    mean = np.asarray(mean, dtype=np.float64)
+    cov = np.asarray(cov, dtype=np.float64)
+    keep = np.flatnonzero(mean > 0)
+    out = np.zeros(len(mean))
+    run = 0.0
+    for b in range(len(mean)):
+        sel = keep[keep <= b]
+        if len(sel) and sel[-1] == b:
+            Cb = cov[np.ix_(sel, sel)] / np.outer(mean[sel], mean[sel])
+            run = float(np.sum(np.linalg.inv(Cb)))
+        out[b] = run
+    return out

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "CF_OK", 1: "CF_ERR_ARG", 2: "CF_ERR_NOT_PSD", 3: "CF_ERR_NOM
                 8: "CF_ERR_NOT_FOUND"}
 CF_F64, CF_F32, CF_BF16_TC, CF_F16_TC = 0, 1, 2, 3
 CF_XI_GAUSSIAN, CF_XI_GEN_CAUCHY, CF_XI_EXPONENTIAL, CF_XI_TABLE = 0, 1, 2, 3
-CF_EMBED_CLAMP, CF_EMBED_SKIP_ERROR = 1, 2
+CF_EMBED_CLAMP, CF_EMBED_SKIP_ERROR, CF_EMBED_LOG1P = 1, 2, 4
 CF_BINS_LINEAR, CF_BINS_LOG, CF_BINS_EDGES = 0, 1, 2
 
 
@@ -123,6 +123,15 @@ _sigs = {
                      C.c_size_t, _S],
     "cf_sample_noalloc": [_P, C.c_uint64, C.c_uint64, C.c_int32, _P, _S],
     "cf_tc_faults": [_S, C.POINTER(C.c_uint32)],
+    "cf_cic_histogram": [_P, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P, _P, _S],
+    "cf_cic_prediction": [C.c_double, C.c_double, _P, C.c_int64, C.c_int32, _P, _S],
+    "cf_astar": [_P, _P, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, _S],
+    "cf_cumulative_information": [_P, _P, C.c_int32, _P, _P, C.c_size_t, _S],
+    "cf_plan_create": [_P, C.c_uint64, C.c_uint64, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _S,
+                       C.POINTER(_P)],
+    "cf_plan_launch": [_P, _S],
+    "cf_plan_seek": [_P, C.c_uint64, _S],
+    "cf_plan_destroy": [_P],
     "cf_tune_sample": [_P, C.c_int32, C.c_int32, _P, C.c_size_t, _P, _S, C.POINTER(C.c_int32),
                        C.POINTER(C.c_double)],
     "cf_lognormal_poisson": [_P, C.c_int32, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, C.c_uint64,
@@ -305,6 +314,56 @@ def cf_tune_sample(emb, dtype, R, ws, ws_bytes, fields_scratch, stream=None):
     _check(_lib.cf_tune_sample(emb.handle, dtype, R, _ptr(ws), ws_bytes, _ptr(fields_scratch), _stream(stream),
                                C.byref(c), C.byref(ms)), "cf_tune_sample")
     return c.value, ms.value
+
+
+def cf_cic_histogram(counts, cells, nfields, f, nbins, hist_out, mean=None, cov=None, stream=None):
+    _check(_lib.cf_cic_histogram(_ptr(counts), cells, nfields, _ptr(f), nbins, _ptr(hist_out), _ptr(mean), _ptr(cov),
+                                 _stream(stream)), "cf_cic_histogram")
+
+
+def cf_cic_prediction(sigma2_A, nbar, f, cells, nbins, pred_out, stream=None):
+    _check(_lib.cf_cic_prediction(sigma2_A, nbar, _ptr(f), cells, nbins, _ptr(pred_out), _stream(stream)),
+           "cf_cic_prediction")
+
+
+def cf_astar(counts, f, cells, nfields, nbar, sigma2_A, out, stream=None):
+    _check(_lib.cf_astar(_ptr(counts), _ptr(f), cells, nfields, nbar, sigma2_A, _ptr(out), _stream(stream)),
+           "cf_astar")
+
+
+class Plan:
+    """A captured graph of the binary32 per-realization path (cf_plan_*)."""
+
+    def __init__(self, emb, seed, r0, R, fields, lp=None, bins=None, pk=None, nmodes=None, mean=None, cov=None,
+                 pk_counts=None, mean_counts=None, cov_counts=None, stream=None):
+        h = _P()
+        lpp = C.byref(lp) if lp is not None else None
+        bp = C.byref(bins) if bins is not None else None
+        _check(_lib.cf_plan_create(emb.handle, seed, r0, R, lpp, bp, _ptr(fields), _ptr(pk), _ptr(nmodes), _ptr(mean),
+                                   _ptr(cov), _ptr(pk_counts), _ptr(mean_counts), _ptr(cov_counts), _stream(stream),
+                                   C.byref(h)), "cf_plan_create")
+        self.handle = h
+        self._keep = (emb, lp, bins)
+
+    def launch(self, stream=None):
+        _check(_lib.cf_plan_launch(self.handle, _stream(stream)), "cf_plan_launch")
+
+    def seek(self, r0, stream=None):
+        _check(_lib.cf_plan_seek(self.handle, r0, _stream(stream)), "cf_plan_seek")
+
+    def close(self):
+        if self.handle:
+            _lib.cf_plan_destroy(self.handle)
+            self.handle = None
+
+
+def cumulative_information_workspace_size(nbins):
+    return 8 * (nbins * nbins + nbins) + 4 * nbins
+
+
+def cf_cumulative_information(mean, cov, nbins, info_out, ws, ws_bytes, stream=None):
+    _check(_lib.cf_cumulative_information(_ptr(mean), _ptr(cov), nbins, _ptr(info_out), _ptr(ws), ws_bytes,
+                                          _stream(stream)), "cf_cumulative_information")
 
 
 def cf_tc_faults(stream=None):

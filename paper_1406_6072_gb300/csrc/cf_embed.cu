@@ -12,7 +12,7 @@ namespace cf {
 // xi depends on |lag_i| only, so one thread evaluates xi once per point of
 // [0, n_0] x ... and writes it to the 2^d mirror positions m_i = l_i and
 // M_i - l_i (one position when l_i is 0 or n_i).
-__global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, double beta,
+__global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, double beta, int log1p_xi,
                            double* __restrict__ c, C2<double>* __restrict__ z) {
     const long long q0 = g.n[0] + 1, q1 = g.ndim > 1 ? g.n[1] + 1 : 1, q2 = g.ndim > 2 ? g.n[2] + 1 : 1;
     const long long total = q0 * q1 * q2;
@@ -32,6 +32,7 @@ __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, doubl
             v = amp * pow(1.0 + r2 / (scale * scale), -beta);
         else
             v = amp * exp(-sqrt(r2) / scale);
+        if (log1p_xi) v = log1p(v);  // eq. (Lncov): Gaussian covariance from the density correlation
         // mirror positions
         const int na = g.ndim;
         const int nm0 = (l0 == 0 || l0 == g.n[0]) ? 1 : 2;
@@ -50,6 +51,12 @@ __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, doubl
             }
         }
     }
+}
+
+__global__ void k_log1p_inplace(double* __restrict__ c, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        c[i] = log1p(c[i]);
 }
 
 __global__ void k_real_to_complex(const double* __restrict__ a, double* __restrict__ c_copy,
@@ -548,16 +555,21 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
     sc.s = (cudaStream_t)stream;
     CF_TRY(alloc_scratch(sc, gi.mtotal));
     const int blocks = grid_blocks(gi.mtotal, kRedThreads, kRedBlocks);
+    const int log1p_xi = (flags & CF_EMBED_LOG1P) ? 1 : 0;
     if (xi->kind == CF_XI_TABLE) {
-        if (xi->table_on_device) {
+        if (xi->table_on_device && !log1p_xi) {
             k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(xi->table, sc.c, sc.z, gi.mtotal);
         } else {
-            CF_CUDA(cudaMemcpyAsync(sc.c, xi->table, sizeof(double) * gi.mtotal, cudaMemcpyHostToDevice, sc.s));
+            CF_CUDA(cudaMemcpyAsync(sc.c, xi->table, sizeof(double) * gi.mtotal,
+                                    xi->table_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sc.s));
+            if (log1p_xi) k_log1p_inplace<<<blocks, kRedThreads, 0, sc.s>>>(sc.c, gi.mtotal);
             k_real_to_complex<<<blocks, kRedThreads, 0, sc.s>>>(sc.c, nullptr, sc.z, gi.mtotal);
         }
     } else {
+        if (log1p_xi && !(xi->amp > -1.0)) return fail(CF_ERR_ARG, "CF_EMBED_LOG1P needs amp > -1");
         ScopedKernelTimer kt(sc.s, "embed_fill");
-        k_fill_row<<<blocks, kRedThreads, 0, sc.s>>>(gi, xi->kind, xi->amp, xi->scale, xi->beta, sc.c, sc.z);
+        k_fill_row<<<blocks, kRedThreads, 0, sc.s>>>(gi, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi, sc.c,
+                                                     sc.z);
     }
     CF_CHECK_LAUNCH();
     if (xi->kind != CF_XI_TABLE) {

@@ -52,6 +52,8 @@ cf_status ensure_device_init();
 // Stream-ordered allocation from the library's pool on the current device
 // (release with cudaFreeAsync).
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+// Mean over rows and unbiased covariance (1/(nrows-1)) of x [nrows][ncols]; either output may be null.
+cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* mean, double* cov, cudaStream_t s);
 // Entry-point prologue: makes the device of stream s current (the legacy
 // default stream keeps the current device) and runs the one-time set-up.
 cf_status enter(cudaStream_t s);

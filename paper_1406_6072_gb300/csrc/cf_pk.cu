@@ -479,7 +479,11 @@ static cf_status get_bins(const PkPlan& P, char* ws, cudaStream_t s, const int16
     std::lock_guard<std::mutex> lk(g_bin_mu);
     for (auto& c : g_bin_cache) {
         if (c.device == dev && c.ndim == P.g.ndim && c.n0 == P.g.n[0] && c.nbins == P.nbins && c.edges == edges) {
-            CF_CUDA(cudaStreamWaitEvent(s, c.ready, 0));
+            // a capturing stream may only wait on an event from outside the
+            // capture as an external dependency (an event-wait node)
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            CF_CUDA(cudaStreamIsCapturing(s, &cs));
+            CF_CUDA(cudaStreamWaitEvent(s, c.ready, cs == cudaStreamCaptureStatusNone ? 0 : cudaEventWaitExternal));
             *bin_of = c.bin_of;
             *nmodes = c.nmodes;
             return CF_OK;
@@ -611,6 +615,20 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
             if (cov) k_pk_cov<<<dim3(P.nbins, P.nbins), 256, 0, s>>>(pk_out, mu, nfields, P.nbins, cov);
         }
     }
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+// Mean over rows and unbiased covariance of x [nrows][ncols] (binary64); used
+// for the power spectra and for the counts-in-cells histograms.
+cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* mean, double* cov, cudaStream_t s) {
+    if (!mean && !cov) return CF_OK;
+    double* mu = mean;
+    if (!mu && pool_malloc((void**)&mu, sizeof(double) * (size_t)ncols, s) != cudaSuccess)
+        return fail(CF_ERR_NOMEM, "scratch for the mean failed");
+    k_pk_mean<<<ncols, 256, 0, s>>>(x, nrows, ncols, mu);
+    if (cov) k_pk_cov<<<dim3(ncols, ncols), 256, 0, s>>>(x, mu, nrows, ncols, cov);
+    if (!mean) cudaFreeAsync(mu, s);
     CF_CHECK_LAUNCH();
     return CF_OK;
 }

@@ -95,6 +95,9 @@ bool sync_check_enabled() {
 }
 
 cf_status enter(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return ensure_device_init();  // a capturing stream may not be queried; it is the current device's
     if (s) {
         int dev = -1;
         cudaError_t e = cudaStreamGetDevice(s, &dev);
@@ -349,6 +352,8 @@ cudaEvent_t take_event() {
 ScopedKernelTimer::ScopedKernelTimer(cudaStream_t s, const char* name, long long variant) : s_(s) {
     std::lock_guard<std::mutex> lk(g_tmu);
     if (!g_timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;  // graph capture
     if (variant >= 0)
         snprintf(name_, sizeof name_, "%s<%lld>", name, variant);
     else

@@ -226,7 +226,7 @@ extern "C" cf_status cf_serve_submit(cf_server* sv, const cf_request* req, uint6
     const cf_status st = sv->sched->submit(*req, ticket);
     if (st == CF_ERR_ARG)
         return fail(st, "invalid request (1 <= R <= max_batch_realizations, amp > 0, scale > 0, parametric xi "
-                        "required)");
+                        "required, no CF_EMBED_LOG1P)");
     if (st == CF_ERR_BUSY) return fail(st, "queue full or server stopping");
     return st;
 }

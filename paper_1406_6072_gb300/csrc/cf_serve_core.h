@@ -130,6 +130,7 @@ class Scheduler {
             if (r.grid.n[a] < 1) return CF_ERR_ARG;
         if (r.r0 + (uint64_t)r.R > (1ull << 32)) return CF_ERR_ARG;
         if (r.R > cfg_.max_batch_realizations) return CF_ERR_ARG;  // a request runs in one launch
+        if (r.embed_flags & CF_EMBED_LOG1P) return CF_ERR_ARG;      // not linear in the amplitude
         std::lock_guard<std::mutex> lk(mu_);
         if (stopping_) return CF_ERR_BUSY;
         if ((int)queue_.size() >= cfg_.queue_capacity) {

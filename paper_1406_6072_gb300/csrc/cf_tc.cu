@@ -34,19 +34,31 @@
 namespace cf {
 namespace {
 
-constexpr int kWgRows = 1024;                // A rows per warpgroup and stage
-constexpr int kTiles = kWgRows / 128;        // M = 128 tiles per warpgroup
+constexpr int kCtaRows = 2048;               // A rows per block and stage (all warpgroups)
 // A: the 4 core matrices of a row group (K = 32) are contiguous (LBO = 128),
 // row groups 528 bytes apart (16 bytes of padding shift rows r and r + 8 by
 // four banks).  Every descriptor's reach stays inside the operand whichever
 // of the two strides is taken along K.
 constexpr int kLBO = 128;                    // K-direction core-matrix stride
 constexpr int kSBO = 4 * 128 + 16;           // row-direction core-matrix stride
-constexpr int kABytes = (kWgRows / 8) * kSBO;
 constexpr int kBBytes = 32 * 32 * 2;         // one 32 x 32 16-bit matrix
-constexpr int kThreads = 256;                // two warpgroups, each with its own lines
-constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 64;
-constexpr uint32_t kTmemCols = 512;          // 256 per warpgroup: 8 tiles x 32 columns
+constexpr uint32_t kTmemCols = 512;          // (kCtaRows / 128) tiles x 32 columns
+
+// Geometry of a block of WGS warpgroups: each owns kWgRows rows of A (its
+// lines), kTiles M = 128 tiles and kTiles x 32 tensor-memory columns.  The
+// warpgroups' operands are kABytes + 16 apart, so that the same offset in two
+// of them falls four banks apart.
+template <int WGS>
+struct Geo {
+    static constexpr int kWgRows = kCtaRows / WGS;
+    static constexpr int kTiles = kWgRows / 128;
+    static constexpr int kABytes = (kWgRows / 8) * kSBO;
+    static constexpr int kAStride = kABytes + 16;
+    static constexpr int kThreads = 128 * WGS;
+    static constexpr int kBOff = WGS * kAStride;
+    static constexpr int kBarOff = kBOff + 2 * kBBytes;
+    static constexpr int kSmem = kBarOff + 8 * WGS + 16;
+};
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per tensor-core wait
 
 __device__ unsigned int g_tc_faults;         // waits that ran out of time
@@ -135,14 +147,14 @@ __device__ void build_dft16(unsigned char* bhi, unsigned char* blo, const C2<flo
     }
 }
 
-// One stage of the warpgroup's 8 tiles: D_t = A_t * (B_hi + B_lo), N outputs.
-template <int N, bool BF16>
+// One stage of the warpgroup's tiles: D_t = A_t * (B_hi + B_lo), N outputs.
+template <int N, bool BF16, int TILES>
 __device__ __forceinline__ void issue_stage(uint32_t a_addr, uint32_t bhi, uint32_t blo, uint32_t tmem,
                                             uint32_t bar) {
     constexpr uint32_t idesc = tc::idesc_f16(128, N, BF16);
     tc::fence_after_sync();
 #pragma unroll 1
-    for (int t = 0; t < kTiles; ++t) {
+    for (int t = 0; t < TILES; ++t) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const uint64_t ad = tc::sdesc(a_addr + (uint32_t)(t * 16 * kSBO + c * 2 * kLBO), kLBO, kSBO);
@@ -204,10 +216,11 @@ __device__ __forceinline__ int out_point(int lrow, int klast) {
 
 // Runs the S stages of one warpgroup on its A (loaded, fenced, synchronised),
 // calling sink(line, point, re, im) for every kept output.
-template <int S, bool BF16, class Sink>
+template <int S, bool BF16, int WGS, class Sink>
 __device__ __forceinline__ void run_stages(unsigned char* A, uint32_t a_addr, uint32_t bhi, uint32_t blo,
                                            uint32_t tmem, uint32_t bar, uint32_t& phase,
                                            const C2<float>* __restrict__ tw, int wg, Sink&& sink) {
+    constexpr int kTiles = Geo<WGS>::kTiles;
     constexpr int L = S == 3 ? 4096 : 256;
     constexpr int RPL = L / 16;
     const int wtid = threadIdx.x & 127;
@@ -218,9 +231,9 @@ __device__ __forceinline__ void run_stages(unsigned char* A, uint32_t a_addr, ui
         const bool last = stage == S;
         if (wtid == 0) {
             if (last)
-                issue_stage<16, BF16>(a_addr, bhi, blo, tmem, bar);
+                issue_stage<16, BF16, kTiles>(a_addr, bhi, blo, tmem, bar);
             else
-                issue_stage<32, BF16>(a_addr, bhi, blo, tmem, bar);
+                issue_stage<32, BF16, kTiles>(a_addr, bhi, blo, tmem, bar);
         }
         wait_phase(bar, phase);
         phase ^= 1u;
@@ -260,16 +273,15 @@ struct TcShared {
 
 // Common prologue: barriers, tensor memory, DFT matrices.  Returns this
 // warpgroup's view.
-template <bool BF16>
+template <bool BF16, int WGS>
 __device__ __forceinline__ TcShared tc_prologue(unsigned char* smraw, const C2<float>* __restrict__ tw, int wg) {
-    unsigned char* A0 = smraw;
-    unsigned char* Bh = smraw + 2 * kABytes;
+    using Gm = Geo<WGS>;
+    unsigned char* Bh = smraw + Gm::kBOff;
     unsigned char* Bl = Bh + kBBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Bl + kBBytes);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + Gm::kBarOff);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + WGS);
     if (threadIdx.x == 0) {
-        tc::mbar_init(tc::smem_u32(&bars[0]), 1);
-        tc::mbar_init(tc::smem_u32(&bars[1]), 1);
+        for (int w = 0; w < WGS; ++w) tc::mbar_init(tc::smem_u32(&bars[w]), 1);
         tc::fence_mbar_init();
     }
     __syncwarp();
@@ -283,18 +295,18 @@ __device__ __forceinline__ TcShared tc_prologue(unsigned char* smraw, const C2<f
     __syncthreads();
     tc::fence_after_sync();
     TcShared s;
-    s.A = A0 + wg * kABytes;
+    s.A = smraw + wg * Gm::kAStride;
     s.a_addr = tc::smem_u32(s.A);
     s.bhi = tc::smem_u32(Bh);
     s.blo = tc::smem_u32(Bl);
-    s.tmem = *tslot + (uint32_t)(256 * wg);
+    s.tmem = *tslot + (uint32_t)(Gm::kTiles * 32 * wg);
     s.bar = tc::smem_u32(&bars[wg]);
     return s;
 }
 
+template <int WGS>
 __device__ __forceinline__ void tc_epilogue(unsigned char* smraw) {
-    const uint32_t* tslot =
-        reinterpret_cast<const uint32_t*>(smraw + 2 * kABytes + 2 * kBBytes + 2 * sizeof(uint64_t));
+    const uint32_t* tslot = reinterpret_cast<const uint32_t*>(smraw + Geo<WGS>::kBarOff + 8 * WGS);
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -305,96 +317,127 @@ __device__ __forceinline__ void tc_epilogue(unsigned char* smraw) {
 
 // ---------------------------------------------------------------- pass 1
 // Rows of the embedded grid (L = M1): noise, scale, transform, keep n1 = L/2.
-// Block: 2 * LPW consecutive rows of realization r0 + blockIdx.y.
-template <int S, bool BF16>
-__global__ void __launch_bounds__(kThreads, 1)
+// Block: WGS * LPW consecutive rows of realization r0 + blockIdx.y, LPW per
+// warpgroup.
+template <int S, bool BF16, int WGS>
+__global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     k_tc_rows(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
               long long nrows, uint32_t* __restrict__ inter, const double* __restrict__ sumsq, double factor,
               const C2<float>* __restrict__ tw) {
     constexpr int L = S == 3 ? 4096 : 256;
     constexpr int RPL = L / 16;
-    constexpr int LPW = kWgRows / RPL;
+    constexpr int LPW = Geo<WGS>::kWgRows / RPL;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const int wg = threadIdx.x >> 7, wtid = threadIdx.x & 127;
-    const TcShared sh = tc_prologue<BF16>(tc_smem, tw, wg);
+    const TcShared sh = tc_prologue<BF16, WGS>(tc_smem, tw, wg);
     const float alpha = input_scale(sumsq, factor, false);
     const uint32_t r = r0 + blockIdx.y;
-    const long long row0 = (long long)blockIdx.x * (2 * LPW) + wg * LPW;
-    // loader: pairs (col, col + L/2) of each line share one Philox call
-#pragma unroll 1
-    for (int q = wtid; q < LPW * (L / 2); q += 128) {
-        const int g = q / (L / 2), col = q % (L / 2);
+    const long long row0 = (long long)blockIdx.x * (WGS * LPW) + wg * LPW;
+    // loader: columns col and col + L/2 share one Philox call.  Within a warp,
+    // lanes take rows j + (lane & 7) of one row group and column groups
+    // (lane >> 3) + 4 b of the A operand (col = row + RPL * group): 32 banks.
+#pragma unroll 2
+    for (int t = wtid; t < LPW * (L / 2); t += 128) {
+        const int g = t / (L / 2), e = t % (L / 2);
+        const int lane = e & 31, w = e >> 5;
+        const int rr = (lane & 7) + 8 * (w % (RPL / 8));
+        const int grp = (lane >> 3) + 4 * (w / (RPL / 8));
+        const int col = rr + RPL * grp;
         const long long row = row0 + g;
         C2<float> lo, hi;
         noise_pair_f32((unsigned long long)row * (L / 2) + col, r, key0, key1, lo, hi);
         const float* srow = s + (size_t)row * L;
         const C2<float> xl = cscale(cscale(lo, srow[col] * amp_scale), alpha);
         const C2<float> xh = cscale(cscale(hi, srow[col + L / 2] * amp_scale), alpha);
-        const int ch = col + L / 2;
-        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + col % RPL, 2 * (col / RPL))) = pack2<BF16>(xl.x, xl.y);
-        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + ch % RPL, 2 * (ch / RPL))) = pack2<BF16>(xh.x, xh.y);
+        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * grp)) = pack2<BF16>(xl.x, xl.y);
+        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * (grp + 8))) = pack2<BF16>(xh.x, xh.y);
     }
     tc::fence_proxy_async_smem();
     tc::bar_sync(1 + wg, 128);
     uint32_t phase = 0;
     uint32_t* out = inter + ((size_t)blockIdx.y * nrows + row0) * (L / 2);
-    run_stages<S, BF16>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
-                        [&](int line, int p, float re, float im) {
-                            out[(size_t)line * (L / 2) + p] = pack2<BF16>(re, im);
-                        });
-    tc_epilogue(tc_smem);
+    run_stages<S, BF16, WGS>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
+                             [&](int line, int p, float re, float im) {
+                                 out[(size_t)line * (L / 2) + p] = pack2<BF16>(re, im);
+                             });
+    tc_epilogue<WGS>(tc_smem);
 }
 
 // ---------------------------------------------------------------- pass 2
 // Columns of the intermediate [M0][n1] (L = M0): transform, keep n0 = L/2,
-// write field 2r (Re) and 2r + 1 (Im) times 1/alpha.
-template <int S, bool BF16>
-__global__ void __launch_bounds__(kThreads, 1)
+// write field 2r (Re) and 2r + 1 (Im) times 1/alpha.  Block: LC = WGS * LPW
+// adjacent columns, loaded by the whole block (LC consecutive 4-byte words of
+// a row per group of lanes).
+template <int S, bool BF16, int WGS>
+__global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     k_tc_cols(const uint32_t* __restrict__ inter, long long n1, float* __restrict__ fields, long long cells,
               const double* __restrict__ sumsq, double factor, const C2<float>* __restrict__ tw) {
     constexpr int L = S == 3 ? 4096 : 256;
     constexpr int RPL = L / 16;
-    constexpr int LPW = kWgRows / RPL;
+    constexpr int LPW = Geo<WGS>::kWgRows / RPL;
+    constexpr int LC = WGS * LPW;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    const int wg = threadIdx.x >> 7, wtid = threadIdx.x & 127;
-    const TcShared sh = tc_prologue<BF16>(tc_smem, tw, wg);
+    const int wg = threadIdx.x >> 7;
+    const TcShared sh = tc_prologue<BF16, WGS>(tc_smem, tw, wg);
     const float inv_alpha = input_scale(sumsq, factor, true);
-    const long long c0 = (long long)blockIdx.x * (2 * LPW) + wg * LPW;
+    const long long cta0 = (long long)blockIdx.x * LC;
     const uint32_t* in = inter + (size_t)blockIdx.y * L * n1;
-#pragma unroll 1
-    for (int q = wtid; q < LPW * L; q += 128) {
-        const int g = q % LPW, n = q / LPW;
-        const uint32_t v = in[(size_t)n * n1 + c0 + g];
-        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + n % RPL, 2 * (n / RPL))) = v;
+    if constexpr (LC == 8) {
+        // lane & 7 -> column (warpgroup operand 4 banks apart), lane >> 3 ->
+        // point group: 32 banks per store, 32-byte row segments per load
+#pragma unroll 4
+        for (int t = threadIdx.x; t < LC * L; t += Geo<WGS>::kThreads) {
+            const int li = t & 7, j = t >> 3;
+            const int grp = (j & 3) + 4 * (j / (4 * RPL));
+            const int n = RPL * grp + ((j >> 2) % RPL);
+            const uint32_t v = in[(size_t)n * n1 + cta0 + li];
+            unsigned char* A = tc_smem + (li / LPW) * Geo<WGS>::kAStride;
+            *reinterpret_cast<uint32_t*>(A + a_off((li % LPW) * RPL + n % RPL, 2 * (n / RPL))) = v;
+        }
+    } else {
+#pragma unroll 4
+        for (int t = threadIdx.x; t < LC * L; t += Geo<WGS>::kThreads) {
+            const int li = t % LC, n = t / LC;
+            const uint32_t v = in[(size_t)n * n1 + cta0 + li];
+            unsigned char* A = tc_smem + (li / LPW) * Geo<WGS>::kAStride;
+            *reinterpret_cast<uint32_t*>(A + a_off((li % LPW) * RPL + n % RPL, 2 * (n / RPL))) = v;
+        }
     }
     tc::fence_proxy_async_smem();
-    tc::bar_sync(1 + wg, 128);
+    __syncthreads();
     uint32_t phase = 0;
     float* f0 = fields + (size_t)blockIdx.y * 2 * cells;
-    run_stages<S, BF16>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
-                        [&](int line, int p, float re, float im) {
-                            const size_t o = (size_t)p * n1 + c0 + line;
-                            f0[o] = re * inv_alpha;
-                            f0[o + cells] = im * inv_alpha;
-                        });
-    tc_epilogue(tc_smem);
+    const long long c0 = cta0 + wg * LPW;
+    run_stages<S, BF16, WGS>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
+                             [&](int line, int p, float re, float im) {
+                                 const size_t o = (size_t)p * n1 + c0 + line;
+                                 f0[o] = re * inv_alpha;
+                                 f0[o + cells] = im * inv_alpha;
+                             });
+    tc_epilogue<WGS>(tc_smem);
 }
+
+#ifndef CF_TC_WGS
+#define CF_TC_WGS 8  // warpgroups per block (2, 4 or 8): build-time tunable
+#endif
 
 template <bool BF16>
 cf_status launch_tc(int S, bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
                     uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
                     long long cells, const double* sumsq, double factor) {
+    constexpr int WGS = CF_TC_WGS;
+    using Gm = Geo<WGS>;
     const C2<float>* tw = twiddles_f32();
     if (rows) {
-        auto kern = S == 3 ? k_tc_rows<3, BF16> : k_tc_rows<2, BF16>;
-        CF_TRY(prepare_smem(kern, kSmem));
+        auto kern = S == 3 ? k_tc_rows<3, BF16, WGS> : k_tc_rows<2, BF16, WGS>;
+        CF_TRY(prepare_smem(kern, Gm::kSmem));
         ScopedKernelTimer kt(st, BF16 ? "tc_rows_bf16" : "tc_rows_f16", S == 3 ? 4096 : 256);
-        kern<<<grid, kThreads, kSmem, st>>>(s, amp, key0, key1, r0, nrows, inter, sumsq, factor, tw);
+        kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(s, amp, key0, key1, r0, nrows, inter, sumsq, factor, tw);
     } else {
-        auto kern = S == 3 ? k_tc_cols<3, BF16> : k_tc_cols<2, BF16>;
-        CF_TRY(prepare_smem(kern, kSmem));
+        auto kern = S == 3 ? k_tc_cols<3, BF16, WGS> : k_tc_cols<2, BF16, WGS>;
+        CF_TRY(prepare_smem(kern, Gm::kSmem));
         ScopedKernelTimer kt(st, BF16 ? "tc_cols_bf16" : "tc_cols_f16", S == 3 ? 4096 : 256);
-        kern<<<grid, kThreads, kSmem, st>>>(inter, n1, fields, cells, sumsq, factor, tw);
+        kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(inter, n1, fields, cells, sumsq, factor, tw);
     }
     CF_CHECK_LAUNCH();
     return CF_OK;
@@ -404,8 +447,8 @@ int stages_of(long long L) { return L == 4096 ? 3 : (L == 256 ? 2 : 0); }
 
 }  // namespace
 
-// Lines per block of a pass with line length L (two warpgroups).
-static long long tc_lines_per_block(long long L) { return 2 * (kWgRows / (L / 16)); }
+// Lines per block of a pass with line length L (all warpgroups).
+static long long tc_lines_per_block(long long L) { return kCtaRows / (L / 16); }
 
 cf_status tc_check_grid(const GridInfo& g) {
     if (g.ndim != 2 || !stages_of(g.m[0]) || !stages_of(g.m[1]))

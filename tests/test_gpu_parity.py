@@ -117,6 +117,32 @@ def test_embedding_from_table(orc, on_device):
     emb.close()
 
 
+@pytest.mark.parametrize("table,on_device", [(False, False), (True, False), (True, True)])
+def test_embedding_log1p_input(orc, table, on_device):
+    """CF_EMBED_LOG1P (eq. (Lncov)): the embedded covariance is ln(1 + xi),
+    parametric and tabulated xi."""
+    n = (32, 64)
+    o = orc.embed(list(n), 1, 0.14, 4.0, 0.4, clamp=True, log1p=True)
+    if table:
+        tab = torch.from_numpy(np.ascontiguousarray(orc.embed_row(list(n), 1, 0.14, 4.0, 0.4)))
+        if on_device:
+            tab = tab.to(DEV)
+        xi = cf.make_xi(cf.CF_XI_TABLE, table=tab)
+    else:
+        xi = cf.make_xi(1, 0.14, 4.0, 0.4)
+    emb = cf.cf_embed(cf.make_grid(n), xi, cf.CF_EMBED_CLAMP | cf.CF_EMBED_LOG1P)
+    lam = torch.empty(o["lambda"].shape, dtype=torch.float64, device=DEV)
+    cf.cf_embedding_lambda(emb, lam)
+    torch.cuda.synchronize()
+    lmax = o["lambda"].max()
+    assert np.max(np.abs(lam.cpu().numpy() - o["lambda"])) <= 1e-12 * lmax
+    assert emb.report["n_negative"] == o["report"]["n_negative"]
+    emb.close()
+    with pytest.raises(cf.CfError) as ei:
+        cf.cf_embed(cf.make_grid(n), cf.make_xi(1, -1.5, 4.0, 0.4), cf.CF_EMBED_LOG1P)
+    assert ei.value.status == cf.CF_ERR_ARG
+
+
 def test_not_psd_is_reported(orc):
     g = cf.make_grid((64, 64))
     with pytest.raises(cf.CfError) as ei:

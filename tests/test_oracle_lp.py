@@ -106,16 +106,76 @@ def test_counts_in_cells_mixture_prediction(orc):
     G = W.gaussian_field_values((R, f.size), seed=14, scale=math.sqrt(sigma2))
     _, counts, _ = orc.lognormal_poisson(G, sigma2, nbar, f=f, seed=15)
     hist = np.stack([np.bincount(c[f > 0], minlength=60)[:42] for c in counts])
-    # Gauss-Hermite: A = -s^2/2 + sqrt(2 s^2) x
-    x, w = np.polynomial.hermite.hermgauss(80)
-    A = -sigma2 / 2 + math.sqrt(2 * sigma2) * x
-    pred = np.zeros(42)
-    for N in range(42):
-        terms = np.exp(N * A[:, None] + N * np.log(nb[None, :]) - nb[None, :] * np.exp(A[:, None])
-                       - math.lgamma(N + 1))
-        pred[N] = np.sum(w[:, None] * terms) / math.sqrt(math.pi)
+    pred = orc.cic_prediction(sigma2, nbar, f, 42)
+    assert np.array_equal(orc.cic_histogram(counts, f, 42), hist)
     mean_hist = hist.mean(0)
     assert pred.sum() == pytest.approx(nb.size, rel=1e-3)  # all mass within N <= 41
     sig = np.sqrt(np.maximum(pred, 1.0) / R)
     z = (mean_hist - pred) / sig
     assert np.max(np.abs(z)) < 6.0, z
+
+
+def test_log1p_input_gives_the_density_correlation(orc):
+    """Section 3.1, eq. (Lncov): a Gaussian field whose covariance is
+    ln(1 + xi_delta) gives delta = exp(G - sigma^2/2) - 1 with correlation
+    function xi_delta (E[e^{G_i + G_j}] = e^{sigma^2 + c_ij}).  Checked on
+    sampled fields against the input xi_delta, at several lags."""
+    n = (8, 8)
+    amp, scale = 0.6, 2.0
+    e = orc.embed(list(n), W.XI_EXPONENTIAL, amp, scale, log1p=True)
+    assert e["report"]["n_negative"] == 0
+    c = e["c"]
+    assert c[0, 0] == pytest.approx(math.log1p(amp), rel=1e-15)
+    assert c[0, 3] == pytest.approx(math.log1p(amp * math.exp(-3 / scale)), rel=1e-14)
+    R = 30000
+    G = orc.sample(n, e["sqrt_lambda"], 21, 0, R, 0).reshape(2 * R, n[0], n[1])
+    sigma2 = math.log1p(amp)
+    delta = np.exp(G - sigma2 / 2) - 1
+    for lag in [(0, 0), (0, 1), (1, 1), (0, 3), (2, 3)]:
+        a = delta[:, : n[0] - lag[0], : n[1] - lag[1]]
+        b = delta[:, lag[0]:, lag[1]:]
+        prod = (a * b).reshape(2 * R, -1).mean(1)  # one value per field (cells correlated)
+        est = prod.mean()
+        err = prod.std() / math.sqrt(prod.size)
+        expect = amp * math.exp(-math.hypot(*lag) / scale)
+        assert abs(est - expect) < 5 * err, (lag, est, expect, err)
+
+
+def test_cic_prediction_small_variance_limit(orc):
+    """sigma_A^2 -> 0: the mixture reduces to a sum of Poisson laws with the
+    cells' own intensities (scipy.stats.poisson)."""
+    f = W.survey_mask((16, 16), seed=30).ravel()
+    nbar = 3.5
+    pred = orc.cic_prediction(1e-10, nbar, f, 30)
+    nb = nbar * f[f > 0]
+    direct = stats.poisson.pmf(np.arange(30)[:, None], nb[None, :]).sum(1)
+    assert np.allclose(pred, direct, rtol=1e-6, atol=1e-12)
+    big = orc.cic_prediction(0.3, nbar, f, 60)
+    assert big.sum() == pytest.approx((f > 0).sum(), rel=1e-6)  # probability of all N
+
+
+def test_cic_histogram_brute_force(orc):
+    rng = np.random.default_rng(31)
+    counts = rng.integers(0, 9, size=(3, 40))
+    f = rng.choice([0.0, 0.5, 1.0], size=40)
+    h = orc.cic_histogram(counts, f, 6)
+    for r in range(3):
+        for N in range(6):
+            assert h[r, N] == sum(1 for i in range(40) if f[i] != 0 and counts[r, i] == N)
+
+
+def test_astar_matches_lambert_w(orc):
+    """Eq. (As) in closed form: A* = c - W(k e^c), c = s^2 (N - 1/2),
+    k = nbar f s^2 (scipy's Lambert W), and A* -> ln(N / nbar) for large N."""
+    from scipy.special import lambertw
+    s2, nbar = 0.13, 9.68
+    f = np.array([1.0, 0.7, 0.0, 0.25])
+    N = np.arange(0, 60)[:, None] * np.ones((1, 4), dtype=int)
+    a = orc.astar(N, f, nbar, s2)
+    c = s2 * (N - 0.5)
+    k = nbar * f * s2
+    with np.errstate(divide="ignore"):
+        ref = np.where(f > 0, c - np.real(lambertw(k * np.exp(c))), 0.0)
+    assert np.max(np.abs(a - ref)) < 1e-12
+    big = orc.astar(np.array([[4000]]), None, nbar, s2)[0, 0]
+    assert abs(big - math.log(4000 / nbar)) < 0.02

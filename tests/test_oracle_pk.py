@@ -128,6 +128,26 @@ def test_gaussian_information_is_half_the_modes(orc):
     C = cov / np.outer(mean, mean)
     info = np.linalg.inv(C).sum()
     assert info == pytest.approx(nm.sum() / 2, rel=0.08)
+    cum = orc.cumulative_information(mean, cov)
+    assert cum[-1] == pytest.approx(info, rel=1e-12)
+    assert np.allclose(cum, np.cumsum(nm) / 2, rtol=0.1)
+
+
+def test_cumulative_information_closed_forms(orc):
+    """Eq. (cuminfo) on matrices with a known inverse: diagonal C gives the
+    running sum of 1/C_bb; a 2 x 2 block [[a, c], [c, d]] gives
+    (a + d - 2c) / (ad - c^2); a bin with zero mean is skipped."""
+    mean = np.array([2.0, 0.0, 1.0, 4.0])
+    cdiag = np.array([0.5, 1.0, 0.25, 0.125])
+    cov = np.diag(cdiag) * np.outer(mean, mean)
+    cum = orc.cumulative_information(mean, cov)
+    assert np.allclose(cum, [2.0, 2.0, 6.0, 14.0], rtol=1e-13)
+    a, c, d = 0.4, 0.1, 0.3
+    m2 = np.array([3.0, 5.0])
+    cov2 = np.array([[a, c], [c, d]]) * np.outer(m2, m2)
+    cum2 = orc.cumulative_information(m2, cov2)
+    assert cum2[0] == pytest.approx(1 / a, rel=1e-13)
+    assert cum2[1] == pytest.approx((a + d - 2 * c) / (a * d - c * c), rel=1e-13)
 
 
 def test_counts_to_delta(orc):
