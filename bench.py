@@ -182,7 +182,10 @@ def roofline(wl, R, timing, steps, hbm_peak, peak_kind, sm_mhz):
     costs = kernel_costs(wl, R, chunks)
     dom = max(per_kernel.items(), key=lambda kv: kv[1][1])[0]
     if dom not in costs:
-        dom = max(costs, key=lambda k: per_kernel.get(k, [0, 0.0])[1])
+        timed = [k for k in costs if per_kernel.get(k, [0, 0.0])[1] > 0]
+        if not timed:
+            return None, per_kernel  # no cost model for this path (binary64 workload)
+        dom = max(timed, key=lambda k: per_kernel[k][1])
     launches, ms = per_kernel[dom]
     avg_s = ms / launches * 1e-3
     ops = costs[dom]["ops"] * steps / launches
