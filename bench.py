@@ -547,7 +547,7 @@ def run_serving(args):
 
 
 # --------------------------------------------------------------------- our arm
-def e2e_run(pipe, wl, steps, warmup, rank):
+def e2e_run(pipe, wl, steps, warmup, rank, world=1):
     """Same metric through the public API with host buffers: the xi table is
     copied from pinned host memory each step, the fields, counts and spectra
     are read back into pinned host memory each step."""
@@ -555,6 +555,7 @@ def e2e_run(pipe, wl, steps, warmup, rank):
     import torch
 
     import paper_1406_6072_gb300.cf as cf
+    from paper_1406_6072_gb300 import replicas
     m = wl.m
     ax = [np.arange(v) for v in m]
     lag = [np.where(a < n, a, a - 2 * n).astype(np.float64) * c for a, n, c in zip(ax, wl.n, wl.cell)]
@@ -574,7 +575,7 @@ def e2e_run(pipe, wl, steps, warmup, rank):
     def one(k):
         d_table.copy_(h_table, non_blocking=True)
         pipe.embed(xi)
-        pipe.sample(r0=(rank * 100000 + k) * pipe.R)
+        pipe.sample(r0=replicas.realization_start(rank, world, k, pipe.R))
         pipe.spectra()
         h_fields.copy_(pipe.fields, non_blocking=True)
         h_counts.copy_(pipe.counts, non_blocking=True)
@@ -610,7 +611,7 @@ def main():
         return run_graph(args)
     import torch
 
-    from paper_1406_6072_gb300 import cf
+    from paper_1406_6072_gb300 import cf, replicas
     from paper_1406_6072_gb300 import workloads as W
     from paper_1406_6072_gb300.pipeline import FieldPipeline
 
@@ -640,7 +641,7 @@ def main():
             tuned = {"chunk": chunk, "ms_per_realization": tms}
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
-            pipe.step(r0=(rank * 100000 + k) * R)
+            pipe.step(r0=replicas.realization_start(rank, world, k, R))
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
@@ -651,7 +652,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(args.steps):
-            pipe.step(r0=(rank * 100000 + args.warmup + k) * R)
+            pipe.step(r0=replicas.realization_start(rank, world, args.warmup + k, R))
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -659,10 +660,7 @@ def main():
         cf.cf_kernel_timing(0)
         clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replicas.max_over_ranks(ms, dist, dev)
     cells_all = pipe.cells_per_step * world
     value = cells_all / (ms_max * 1e-3)
     hbm_peak, peak_kind = measured_peaks()
@@ -671,14 +669,12 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        r = e2e_run(pipe, wl, max(3, args.steps // 2), 2, rank)
+        r = e2e_run(pipe, wl, max(3, args.steps // 2), 2, rank, world)
         if r is not None:
             e_ms, h2d, d2h = r
-            te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            if dist is not None:
-                dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            e2e = {"value": cells_all / (float(te.item()) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h), "ms_per_step": float(te.item())}
+            e_max = replicas.max_over_ranks(e_ms, dist, dev)
+            e2e = {"value": cells_all / (e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h), "ms_per_step": e_max}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_sample_realizations)
