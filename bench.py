@@ -47,6 +47,8 @@ def parse_args():
     p.add_argument("--cpu-sample-realizations", type=int, default=8)
     p.add_argument("--serve-requests", type=int, default=10000)
     p.add_argument("--tune", action="store_true", help="autotune the sampler's chunk schedule before warm-up")
+    p.add_argument("--mock-realizations", type=int, default=None,
+                   help="mock_n128 workload: realizations per method (default 2000)")
     p.add_argument("--graph", action="store_true",
                    help="time replays of a captured plan (embedding computed once, per-realization path replayed)")
     p.add_argument("--precision", default="all", choices=["all", "f64", "f32", "bf16_tc", "f16_tc"],
@@ -349,6 +351,122 @@ def run_sweep(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- section 3.3 / 3.4 experiment
+def run_mock(args):
+    """Synthetic analogue of the paper's CFHTLS analysis on a 128^2 map
+    (workload mock_n128): cumulative information I(<= l) of the lognormal map
+    rho = 1 + delta from the exact circulant embedding and from k-space
+    sampling in periodic boxes of 1, 2 and 4 times the map (DC mode zeroed),
+    section 3.3; and, for the exact sampler with the survey mask, the
+    counts-in-cells histogram against the Poisson-lognormal prediction and the
+    spectra of delta_g and of A* (section 3.4).  All steps are library calls."""
+    import numpy as np
+    import torch
+
+    from paper_1406_6072_gb300 import cf
+    from paper_1406_6072_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.CONFIGS["mock_n128"]
+    n = tuple(wl.n)
+    cells = wl.cells_per_field
+    Rtot = wl.R if args.mock_realizations is None else args.mock_realizations
+    chunk = min(250, Rtot)
+    Rtot = -(-Rtot // chunk) * chunk  # whole chunks
+    nb = wl.nbins
+    bins = cf.make_bins(nb, cf.CF_BINS_LOG, 1.0, n[0] / 2)
+    grid = cf.make_grid(n)
+    xi = cf.make_xi(wl.xi_kind, wl.amp, wl.scale, wl.beta)
+    flags = cf.CF_EMBED_CLAMP | cf.CF_EMBED_LOG1P
+    mask = torch.from_numpy(W.survey_mask(n, seed=wl.seed + 7)).to(dev)
+    s = torch.cuda.Stream(dev)
+    out = {"workload": wl.name, "text": wl.text, "realizations": Rtot}
+
+    def spectra_of(emb, big_n, masked):
+        F = 2 * Rtot
+        pk_all = torch.empty((F, nb), dtype=torch.float64, device=dev)
+        pkg_all = torch.empty_like(pk_all) if masked else None
+        ast_all = torch.empty_like(pk_all) if masked else None
+        hist_all = torch.empty((F, 42), dtype=torch.float64, device=dev) if masked else None
+        wsb = cf.cf_sample_workspace_size(emb, chunk, cf.CF_F32)
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+        fields = torch.empty((chunk, 2) + big_n, dtype=torch.float32, device=dev)
+        delta = torch.empty_like(fields)
+        counts = torch.empty((chunk, 2) + big_n, dtype=torch.int32, device=dev)
+        dcorner = torch.empty((chunk, 2) + n, dtype=torch.float32, device=dev)
+        astar = torch.empty((chunk, 2) + n, dtype=torch.float32, device=dev)
+        pkb = cf.cf_power_spectrum_workspace_size(grid, 2 * chunk, bins, cf.CF_F32)
+        pkws = torch.empty(pkb, dtype=torch.uint8, device=dev)
+        nm = torch.empty(nb, dtype=torch.int64, device=dev)
+        for c0 in range(0, Rtot, chunk):
+            lp = cf.make_lp(wl.sigma2, wl.nbar, counts, wl.seed + 1000, f=mask if masked else None, delta_out=delta)
+            cf.cf_sample_lp(emb, wl.seed, c0, chunk, cf.CF_F32, fields, lp, ws, wsb, s)
+            d = delta
+            if big_n != n:
+                cf.cf_copy_corner(delta, cf.CF_F32, cf.make_grid(big_n), grid, 2 * chunk, dcorner, s)
+                d = dcorner
+            sl = slice(2 * c0, 2 * c0 + 2 * chunk)
+            cf.cf_power_spectrum(d, cf.CF_F32, grid, 2 * chunk, bins, pk_all[sl], nm, None, None, pkws, pkb, s)
+            if masked:
+                cf.cf_power_spectrum_counts(counts, mask, grid, 2 * chunk, bins, pkg_all[sl], nm, None, None, pkws,
+                                            pkb, s)
+                cf.cf_astar(counts, mask, cells, 2 * chunk, wl.nbar, wl.sigma2, astar, s)
+                cf.cf_power_spectrum(astar, cf.CF_F32, grid, 2 * chunk, bins, ast_all[sl], nm, None, None, pkws,
+                                     pkb, s)
+                cf.cf_cic_histogram(counts, cells, 2 * chunk, mask, 42, hist_all[sl], None, None, s)
+        return pk_all, pkg_all, ast_all, hist_all
+
+    def info(pk_all):
+        F = pk_all.shape[0]
+        mean = torch.empty(nb, dtype=torch.float64, device=dev)
+        cov = torch.empty((nb, nb), dtype=torch.float64, device=dev)
+        cf.cf_mean_cov(pk_all, F, nb, mean, cov, s)
+        I = torch.empty(nb, dtype=torch.float64, device=dev)
+        wsb = cf.cumulative_information_workspace_size(nb)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        cf.cf_cumulative_information(mean, cov, nb, I, ws, wsb, s)
+        torch.cuda.synchronize()
+        return mean.cpu().numpy(), I.cpu().numpy()
+
+    t0 = time.perf_counter()
+    methods = {}
+    with torch.cuda.stream(s):
+        emb = cf.cf_embed(grid, xi, flags, s)
+        pk, pkg, pka, hist = spectra_of(emb, n, False)
+        mean, I = info(pk)
+        methods["circulant"] = {"I": I.tolist(), "pk_mean": mean.tolist(), "embed_report": emb.report}
+        emb.close()
+        for bf in (1, 2, 4):
+            emb = cf.cf_embed_periodic(grid, xi, bf, 2, 4, flags, s)
+            big_n = tuple(2 * v for v in n) if bf == 4 else n
+            pk, _, _, _ = spectra_of(emb, big_n, False)
+            mean, I = info(pk)
+            methods["box%d" % bf] = {"I": I.tolist(), "pk_mean": mean.tolist()}
+            emb.close()
+        # section 3.4 with the mask: counts in cells, delta_g and A* spectra
+        emb = cf.cf_embed(grid, xi, flags, s)
+        pk, pkg, pka, hist = spectra_of(emb, n, True)
+        hm = torch.empty(42, dtype=torch.float64, device=dev)
+        hc = torch.empty((42, 42), dtype=torch.float64, device=dev)
+        cf.cf_mean_cov(hist, hist.shape[0], 42, hm, hc, s)
+        pred = torch.empty(42, dtype=torch.float64, device=dev)
+        cf.cf_cic_prediction(wl.sigma2, wl.nbar, mask, cells, 42, pred, s)
+        mg, Ig = info(pkg)
+        ma, Ia = info(pka)
+        torch.cuda.synchronize()
+        emb.close()
+    hm, pred, hvar = hm.cpu().numpy(), pred.cpu().numpy(), torch.diagonal(hc).cpu().numpy()
+    F = hist.shape[0]
+    z = (hm - pred) / np.sqrt(np.maximum(hvar, 1e-12) / F)  # empirical per-bin scatter over the maps
+    out["cumulative_information"] = methods
+    out["counts_in_cells"] = {"mean_histogram": hm.tolist(), "prediction": pred.tolist(),
+                              "max_abs_z": float(np.max(np.abs(z))), "fields": F}
+    out["delta_g"] = {"pk_mean": mg.tolist(), "I": Ig.tolist()}
+    out["astar"] = {"pk_mean": ma.tolist(), "I": Ia.tolist()}
+    out["seconds"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------- cuFFT reference
 def cufft_reference(wl, R, stream, steps=10):
     """Context only: the inverse transforms of the same embedded grids by
@@ -548,14 +666,18 @@ def run_serving(args):
 
 # --------------------------------------------------------------------- our arm
 def e2e_run(pipe, wl, steps, warmup, rank, world=1):
-    """Same metric through the public API with host buffers: the xi table is
-    copied from pinned host memory each step, the fields, counts and spectra
-    are read back into pinned host memory each step."""
+    """Same metric through the public API with host buffers: each step copies
+    the xi table from pinned host memory, embeds it, samples, computes the
+    spectra and reads the fields, counts and spectra back into pinned host
+    memory.  Two pipelines on two streams alternate, so that one step's
+    device-to-host copies overlap the next step's compute (the host memory of
+    each pipeline is reused every other step, after its copies finished)."""
     import numpy as np
     import torch
 
     import paper_1406_6072_gb300.cf as cf
     from paper_1406_6072_gb300 import replicas
+    from paper_1406_6072_gb300.pipeline import FieldPipeline
     m = wl.m
     ax = [np.arange(v) for v in m]
     lag = [np.where(a < n, a, a - 2 * n).astype(np.float64) * c for a, n, c in zip(ax, wl.n, wl.cell)]
@@ -564,38 +686,40 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
     if table is None:
         return None
     h_table = torch.from_numpy(np.ascontiguousarray(table)).pin_memory()
-    d_table = torch.empty_like(h_table, device=pipe.dev)
-    h_fields = torch.empty(pipe.fields.shape, dtype=pipe.fields.dtype).pin_memory()
-    h_counts = torch.empty(pipe.counts.shape, dtype=torch.int32).pin_memory()
-    outs = [pipe.pk, pipe.mean, pipe.cov, pipe.pkg, pipe.meang, pipe.covg]
-    h_outs = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
-    s = pipe.stream
-    xi = cf.make_xi(cf.CF_XI_TABLE, table=d_table, table_on_device=1)
+    other = FieldPipeline(wl, pipe.dev, stream=torch.cuda.Stream(pipe.dev))
+    lanes = []
+    for p in (pipe, other):
+        d_table = torch.empty_like(h_table, device=p.dev)
+        outs = [p.fields, p.counts, p.pk, p.mean, p.cov, p.pkg, p.meang, p.covg]
+        h_outs = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+        xi = cf.make_xi(cf.CF_XI_TABLE, table=d_table, table_on_device=1)
+        lanes.append({"p": p, "d_table": d_table, "outs": outs, "h_outs": h_outs, "xi": xi,
+                      "done": torch.cuda.Event()})
 
     def one(k):
-        d_table.copy_(h_table, non_blocking=True)
-        pipe.embed(xi)
-        pipe.sample(r0=replicas.realization_start(rank, world, k, pipe.R))
-        pipe.spectra()
-        h_fields.copy_(pipe.fields, non_blocking=True)
-        h_counts.copy_(pipe.counts, non_blocking=True)
-        for h, d in zip(h_outs, outs):
-            h.copy_(d, non_blocking=True)
+        ln = lanes[k % 2]
+        p = ln["p"]
+        with torch.cuda.stream(p.stream):
+            ln["done"].synchronize()  # this pipeline's previous host copies are complete
+            ln["d_table"].copy_(h_table, non_blocking=True)
+            p.embed(ln["xi"])
+            p.sample(r0=replicas.realization_start(rank, world, k, p.R))
+            p.spectra()
+            for h, d in zip(ln["h_outs"], ln["outs"]):
+                h.copy_(d, non_blocking=True)
+            ln["done"].record(p.stream)
 
-    with torch.cuda.stream(s):
-        for k in range(warmup):
-            one(k)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for k in range(steps):
-            one(1000 + k)
-        e1.record(s)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    for k in range(warmup):
+        one(k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        one(1000 + k)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    other.close()
     h2d = h_table.numel() * 8
-    d2h = h_fields.numel() * h_fields.element_size() + h_counts.numel() * 4 + sum(h.numel() * 8 for h in h_outs)
+    d2h = sum(h.numel() * h.element_size() for h in lanes[0]["h_outs"])
     return ms, h2d, d2h
 
 
@@ -609,6 +733,8 @@ def main():
         return run_sweep(args)
     if args.graph:
         return run_graph(args)
+    if args.workload == "mock_n128":
+        return run_mock(args)
     import torch
 
     from paper_1406_6072_gb300 import cf, replicas

@@ -150,6 +150,22 @@ CF_API cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags, cf_
 CF_API cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
                                cf_stream_t s, cf_embedding** out, cf_embed_report* rep);
 
+/* k-space (periodic box) sampler of section 3.3, eq. (Periodicboxmodes): the
+ * survey grid g (n per axis) is observed inside a periodic box of side
+ * B = box_factor * n (1, 2 or 4) whose modes k = 2 pi m / (B cell) have
+ * variance P(k) / cell^d, P the continuous Fourier transform of xi (of
+ * ln(1 + xi) with CF_EMBED_LOG1P), and the DC mode is zero.  P is the Fourier
+ * sum of xi on a grid of spacing cell / resolution over resolution * extent * B
+ * points per axis (both 1..16, powers of two; the product must stay <= 4096):
+ * aliasing sits at k = 2 pi resolution / cell and xi is truncated at
+ * |r| = extent B cell / 2.  The returned embedding samples like cf_embed's:
+ * cf_sample gives fields of n per axis for box_factor 1 and 2 and of 2n for
+ * box_factor 4 (the survey is then the first n per axis).  No covariance-error
+ * pass (the target is the periodised covariance).  Parametric xi only. */
+CF_API cf_status cf_embed_periodic(const cf_grid* g, const cf_xi* xi, int32_t box_factor, int32_t extent,
+                                   int32_t resolution, uint32_t flags, cf_stream_t s, cf_embedding** out,
+                                   cf_embed_report* report);
+
 /* Frees an embedding without waiting on the host: the memory is released on
  * a library-owned stream after the last work that any library call enqueued
  * on it (on any stream) has finished. */
@@ -252,6 +268,19 @@ CF_API cf_status cf_cic_prediction(double sigma2_A, double nbar, const float* f,
  * of every map (binary32 out [nfields][cells]; 0 where f = 0). */
 CF_API cf_status cf_astar(const int32_t* counts, const float* f, int64_t cells, int64_t nfields, double nbar,
                           double sigma2_A, float* out, cf_stream_t s);
+
+/* Copies the first g_out->n[a] cells of every axis of each of nfields fields
+ * laid out on g_in (e.g. the survey corner of a box-sampled field); binary32
+ * or binary64, device pointers. */
+CF_API cf_status cf_copy_corner(const void* in, cf_dtype dt, const cf_grid* g_in, const cf_grid* g_out,
+                                int64_t nfields, void* out, cf_stream_t s);
+
+/* Mean over rows [ncols] and unbiased covariance (1/(nrows - 1)) [ncols][ncols]
+ * of x [nrows][ncols] (binary64, device); either output may be NULL.  The
+ * estimator used by cf_power_spectrum and cf_cic_histogram, for spectra
+ * gathered over several calls. */
+CF_API cf_status cf_mean_cov(const double* x, int64_t nrows, int32_t ncols, double* mean_or_null,
+                             double* cov_or_null, cf_stream_t s);
 
 /* Cumulative information of section 3.3, eq. (cuminfo), from the mean [nbins]
  * and covariance [nbins][nbins] of binned power spectra (cf_power_spectrum):

@@ -364,3 +364,39 @@ def cumulative_information(mean, cov):
             run = float(np.sum(np.linalg.inv(Cb)))
         out[b] = run
     return out
+
+
+# ---------------------------------------------------------------- periodic box (section 3.3)
+def periodic_lambda(n, kind, amp, scale, beta, box_factor, extent, resolution, log1p=False):
+    """Eigenvalues of the k-space sampler of eq. (Periodicboxmodes) on the
+    sampler's embedding grid (2n per axis, or 4n for box_factor 4): a box of
+    side B = box_factor n with modes k = 2 pi m / B of variance P(k) (cell 1),
+    P the Fourier sum of xi on a grid of spacing 1/resolution and extent
+    extent B, the DC mode zero; for box_factor 1 the modes sit on the even
+    frequencies of the 2n grid with weight 2^d."""
+    d = len(n)
+    nb = [resolution * extent * box_factor * v // 2 for v in n]
+    c = embed_row(nb, kind, amp, scale, beta, cell=[1.0 / resolution] * d, log1p=log1p)
+    lam_big = eigenvalues(nb, c)
+    Mb = lam_big.shape
+    ne = [2 * v if box_factor == 4 else v for v in n]
+    Me = [2 * v for v in ne]
+    idx = np.indices(Me)
+    zero = np.zeros(Me, dtype=bool)
+    dc = np.ones(Me, dtype=bool)
+    big_index = []
+    for a in range(d):
+        m = idx[a]
+        if box_factor == 1:
+            zero |= (m % 2) == 1
+            m = m // 2
+            B = Me[a] // 2
+        else:
+            B = Me[a]
+        f = np.where(m < B // 2, m, m - B)
+        dc &= f == 0
+        big_index.append((extent * f) % Mb[a])
+    scale_ = (1.0 / resolution) ** d * (2.0 ** d if box_factor == 1 else 1.0)
+    lam = lam_big[tuple(big_index)] * scale_
+    lam[zero | dc] = 0.0
+    return lam

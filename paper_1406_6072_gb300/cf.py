@@ -123,6 +123,9 @@ _sigs = {
                      C.c_size_t, _S],
     "cf_sample_noalloc": [_P, C.c_uint64, C.c_uint64, C.c_int32, _P, _S],
     "cf_tc_faults": [_S, C.POINTER(C.c_uint32)],
+    "cf_embed_periodic": [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, _S, C.POINTER(_P), _P],
+    "cf_copy_corner": [_P, C.c_int32, _P, _P, C.c_int64, _P, _S],
+    "cf_mean_cov": [_P, C.c_int64, C.c_int32, _P, _P, _S],
     "cf_cic_histogram": [_P, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P, _P, _S],
     "cf_cic_prediction": [C.c_double, C.c_double, _P, C.c_int64, C.c_int32, _P, _S],
     "cf_astar": [_P, _P, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, _S],
@@ -253,6 +256,24 @@ def cf_embed(grid, xi, flags=0, stream=None):
         raise err
     _check(st, "cf_embed")
     return Embedding(h.value, rep.asdict())
+
+
+def cf_embed_periodic(grid, xi, box_factor, extent=2, resolution=4, flags=0, stream=None):
+    """Periodic-box (k-space) sampler embedding; see include/cf.h."""
+    h = _P()
+    rep = cf_embed_report()
+    _check(_lib.cf_embed_periodic(C.byref(grid), C.byref(xi), box_factor, extent, resolution, flags, _stream(stream),
+                                  C.byref(h), C.byref(rep)), "cf_embed_periodic")
+    return Embedding(h.value, rep.asdict())
+
+
+def cf_mean_cov(x, nrows, ncols, mean=None, cov=None, stream=None):
+    _check(_lib.cf_mean_cov(_ptr(x), nrows, ncols, _ptr(mean), _ptr(cov), _stream(stream)), "cf_mean_cov")
+
+
+def cf_copy_corner(inp, dtype, grid_in, grid_out, nfields, out, stream=None):
+    _check(_lib.cf_copy_corner(_ptr(inp), dtype, C.byref(grid_in), C.byref(grid_out), nfields, _ptr(out),
+                               _stream(stream)), "cf_copy_corner")
 
 
 def cf_embed_from_lambda(grid, lam, flags=0, stream=None):

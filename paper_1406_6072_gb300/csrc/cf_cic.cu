@@ -262,3 +262,65 @@ extern "C" cf_status cf_cumulative_information(const double* mean, const double*
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
+
+// ---------------------------------------------------------------- sub-box copy
+// The first n_out[a] cells of every axis of each field (e.g. the survey corner
+// of a box-sampled field, section 3.3).
+namespace cf {
+namespace {
+template <typename T>
+__global__ void k_copy_corner(const T* __restrict__ in, GridInfo gi, GridInfo go, long long nfields,
+                              T* __restrict__ out) {
+    const long long total = go.ncell * nfields;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx % go.ncell;
+        const long long fld = idx / go.ncell;
+        long long src = 0, stride = 1;
+        for (int a = go.ndim - 1; a >= 0; --a) {
+            const long long x = rem % go.n[a];
+            rem /= go.n[a];
+            src += x * stride;
+            stride *= gi.n[a];
+        }
+        out[idx] = in[fld * gi.ncell + src];
+    }
+}
+}  // namespace
+}  // namespace cf
+
+extern "C" cf_status cf_copy_corner(const void* in, cf_dtype dt, const cf_grid* g_in, const cf_grid* g_out,
+                                    int64_t nfields, void* out, cf_stream_t s) {
+    clear_error();
+    if (!in || !out || !g_in || !g_out) return fail(CF_ERR_ARG, "NULL argument");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
+    if (g_in->ndim != g_out->ndim || g_in->ndim < 1 || g_in->ndim > 3) return fail(CF_ERR_ARG, "grid dimensions");
+    GridInfo gi{}, go{};
+    gi.ndim = go.ndim = g_in->ndim;
+    gi.ncell = go.ncell = 1;
+    for (int a = 0; a < g_in->ndim; ++a) {
+        if (g_out->n[a] < 1 || g_out->n[a] > g_in->n[a]) return fail(CF_ERR_ARG, "output larger than input");
+        gi.n[a] = g_in->n[a];
+        go.n[a] = g_out->n[a];
+        gi.ncell *= gi.n[a];
+        go.ncell *= go.n[a];
+    }
+    if (nfields < 1) return fail(CF_ERR_ARG, "nfields must be >= 1");
+    CF_TRY(enter((cudaStream_t)s));
+    const int blocks = grid_blocks(go.ncell * nfields, 256);
+    if (dt == CF_F32)
+        k_copy_corner<float><<<blocks, 256, 0, (cudaStream_t)s>>>((const float*)in, gi, go, nfields, (float*)out);
+    else
+        k_copy_corner<double><<<blocks, 256, 0, (cudaStream_t)s>>>((const double*)in, gi, go, nfields, (double*)out);
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+extern "C" cf_status cf_mean_cov(const double* x, int64_t nrows, int32_t ncols, double* mean_or_null,
+                                 double* cov_or_null, cf_stream_t s) {
+    clear_error();
+    if (!x) return fail(CF_ERR_ARG, "x is NULL");
+    if (nrows < 1 || ncols < 1) return fail(CF_ERR_ARG, "nrows and ncols must be >= 1");
+    CF_TRY(enter((cudaStream_t)s));
+    return launch_mean_cov(x, nrows, ncols, mean_or_null, cov_or_null, (cudaStream_t)s);
+}

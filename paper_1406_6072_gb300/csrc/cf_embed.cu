@@ -582,6 +582,105 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
     return finish_embedding(gi, sc, flags, nullptr, false, out, rep);
 }
 
+// ---------------------------------------------------------------- periodic box (section 3.3)
+// Eigenvalues of the k-space (periodic box) sampler of eq. (Periodicboxmodes):
+// the box of side B = factor * n carries modes k = 2 pi m / B with variance
+// P(k) / cell^d, P the continuous Fourier transform of the covariance, the
+// DC mode set to zero.  P is approximated on a fine, large grid `big` (cell
+// 1/q, extent o B): lambda_big[o f] / q^d with f the signed frequency.  The
+// sampler's embedding grid e has side 2n (factor 1 and 2) or 4n (factor 4);
+// for factor 1 the box modes sit on the even frequencies of e with weight
+// 2^d (a field with only even frequencies on 2n is n-periodic).
+__global__ void k_periodic_lambda(const double* __restrict__ big, GridInfo gbig, GridInfo ge, int factor, int o,
+                                  double scale, double* __restrict__ lam) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ge.mtotal;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long rem = idx, bidx = 0, bstride = 1;
+        bool zero = false, dc = true;
+        for (int a = ge.ndim - 1; a >= 0; --a) {
+            long long m = rem % ge.m[a];
+            rem /= ge.m[a];
+            if (factor == 1) {
+                if (m & 1) zero = true;
+                m >>= 1;
+            }
+            const long long B = factor == 1 ? ge.m[a] / 2 : ge.m[a];
+            const long long f = m < B / 2 ? m : m - B;  // signed box frequency
+            if (f != 0) dc = false;
+            long long bi = (o * f) % gbig.m[a];
+            if (bi < 0) bi += gbig.m[a];
+            bidx += bi * bstride;
+            bstride *= gbig.m[a];
+        }
+        lam[idx] = (zero || dc) ? 0.0 : big[bidx] * scale;
+    }
+}
+
+extern "C" cf_status cf_embed_periodic(const cf_grid* g, const cf_xi* xi, int32_t box_factor, int32_t extent,
+                                       int32_t resolution, uint32_t flags, cf_stream_t stream, cf_embedding** out,
+                                       cf_embed_report* rep) {
+    clear_error();
+    if (!out) return fail(CF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !xi) return fail(CF_ERR_ARG, "grid and xi are required");
+    if (xi->kind < CF_XI_GAUSSIAN || xi->kind > CF_XI_EXPONENTIAL)
+        return fail(CF_ERR_ARG, "the periodic box needs a parametric xi");
+    if (!(xi->scale > 0.0)) return fail(CF_ERR_ARG, "xi scale must be > 0");
+    if (box_factor != 1 && box_factor != 2 && box_factor != 4) return fail(CF_ERR_ARG, "box_factor must be 1, 2 or 4");
+    if (extent < 1 || extent > 16 || (extent & (extent - 1))) return fail(CF_ERR_ARG, "extent must be 1, 2, 4, 8 or 16");
+    if (resolution < 1 || resolution > 16 || (resolution & (resolution - 1)))
+        return fail(CF_ERR_ARG, "resolution must be 1, 2, 4, 8 or 16");
+    GridInfo gs;
+    CF_TRY(check_grid(g, &gs));
+    const int log1p_xi = (flags & CF_EMBED_LOG1P) ? 1 : 0;
+    if (log1p_xi && !(xi->amp > -1.0)) return fail(CF_ERR_ARG, "CF_EMBED_LOG1P needs amp > -1");
+    // embedding grid of the sampler and the fine, large grid of the spectrum
+    cf_grid ge_in = *g, gb_in = *g;
+    for (int a = 0; a < gs.ndim; ++a) {
+        ge_in.n[a] = box_factor == 4 ? 2 * g->n[a] : g->n[a];
+        gb_in.n[a] = (int64_t)resolution * extent * box_factor * g->n[a] / 2;
+        gb_in.cell[a] = g->cell[a] / (double)resolution;
+    }
+    GridInfo ge, gb;
+    CF_TRY(check_grid(&ge_in, &ge));
+    CF_TRY(check_grid(&gb_in, &gb));
+    CF_TRY(enter((cudaStream_t)stream));
+    const cudaStream_t s = (cudaStream_t)stream;
+    double* lam_e = nullptr;
+    if (pool_malloc((void**)&lam_e, sizeof(double) * (size_t)ge.mtotal, s) != cudaSuccess)
+        return fail(CF_ERR_NOMEM, "device allocation of the box eigenvalues failed");
+    {
+        EmbedScratch bs;
+        bs.s = s;
+        cf_status st = alloc_scratch(bs, gb.mtotal);
+        if (st != CF_OK) {
+            cudaFreeAsync(lam_e, s);
+            return st;
+        }
+        const int blocks = grid_blocks(gb.mtotal, kRedThreads, kRedBlocks);
+        {
+            ScopedKernelTimer kt(s, "embed_fill");
+            k_fill_row<<<blocks, kRedThreads, 0, s>>>(gb, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi, bs.c,
+                                                      bs.z);
+        }
+        CF_CHECK_LAUNCH();
+        double* full = (double*)bs.z;
+        CF_TRY(even_dft(bs.c, gb, 1.0, full + gb.mtotal, full, s));
+        double scale = 1.0;
+        for (int a = 0; a < gs.ndim; ++a) scale /= (double)resolution;
+        if (box_factor == 1) scale *= (double)(1 << gs.ndim);
+        k_periodic_lambda<<<grid_blocks(ge.mtotal, 256, 4096), 256, 0, s>>>(full, gb, ge, box_factor, extent, scale,
+                                                                            lam_e);
+        CF_CHECK_LAUNCH();
+    }
+    EmbedScratch sc;
+    sc.s = s;
+    cf_status st = alloc_scratch(sc, ge.mtotal);
+    if (st == CF_OK) st = finish_embedding(ge, sc, flags | CF_EMBED_SKIP_ERROR, lam_e, true, out, rep);
+    cudaFreeAsync(lam_e, s);
+    return st;
+}
+
 extern "C" cf_status cf_embed_from_lambda(const cf_grid* g, const double* lambda, uint32_t flags,
                                           cf_stream_t stream, cf_embedding** out, cf_embed_report* rep) {
     clear_error();

@@ -71,6 +71,12 @@ CONFIGS = {
         sigma2=1.0, nbar=0.5, nbins=48,
         text="3D 128^3 survey in 256^3, xi = exp(-r/6), binary32, batch of 8 realizations, "
              "lognormal + Poisson nbar=0.5, 48 spherical shells, seed 3"),
+    "mock_n128": Workload(
+        "mock_n128", (128, 128), XI_GEN_CAUCHY, 0.14, 4.0, 0.4, "f32", 2000, 6, True,
+        sigma2=float(np.log1p(0.14)), nbar=9.68, nbins=20,
+        text="2D 128^2 survey in 256^2 (the paper's map size), density correlation "
+             "omega = 0.14/(1+(r/4)^2)^0.4 embedded as ln(1+omega), lognormal sigma_A^2 = ln 1.14, "
+             "Poisson nbar = 9.68 with a survey mask, 20 log-spaced bins, 2000 realizations, seed 6"),
     "cauchy2d_n2048_sweep": Workload(
         "cauchy2d_n2048_sweep", (2048, 2048), XI_GEN_CAUCHY, 0.8, 16.0, 0.4, "f32", 32, 4, True,
         nbins=64,

@@ -344,3 +344,32 @@ def test_power_spectrum_counts_parity(orc, n, F, masked):
     assert np.array_equal(nm.cpu().numpy(), onm)
     assert np.allclose(pk.cpu().numpy(), opk, rtol=2e-5, atol=1e-7 * opk.max())
     assert np.allclose(mean.cpu().numpy(), opk.mean(0), rtol=2e-5)
+
+
+@pytest.mark.parametrize("box_factor,log1p", [(1, False), (2, True), (4, False)])
+def test_periodic_box_embedding(orc, box_factor, log1p):
+    """cf_embed_periodic: the box eigenvalues equal the oracle's (section 3.3)."""
+    n = (32, 64)
+    flags = cf.CF_EMBED_CLAMP | (cf.CF_EMBED_LOG1P if log1p else 0)
+    emb = cf.cf_embed_periodic(cf.make_grid(n), cf.make_xi(cf.CF_XI_GEN_CAUCHY, 0.5, 4.0, 0.4), box_factor, 2, 4,
+                               flags)
+    ref = orc.periodic_lambda(n, cf.CF_XI_GEN_CAUCHY, 0.5, 4.0, 0.4, box_factor, 2, 4, log1p=log1p)
+    lam = torch.empty(ref.shape, dtype=torch.float64, device=DEV)
+    cf.cf_embedding_lambda(emb, lam)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(lam.cpu().numpy() - ref)) <= 1e-12 * np.abs(ref).max()
+    # the sampler runs on it: fields of n (2n for box_factor 4) per axis
+    R = 2
+    out_n = tuple(2 * v for v in n) if box_factor == 4 else n
+    wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=DEV)
+    fields = torch.empty((R, 2) + out_n, dtype=torch.float32, device=DEV)
+    cf.cf_sample(emb, 3, 0, R, cf.CF_F32, fields, ws, wsb)
+    torch.cuda.synchronize()
+    assert torch.isfinite(fields).all()
+    if box_factor == 4:  # the survey corner of the 2n field
+        corner = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+        cf.cf_copy_corner(fields, cf.CF_F32, cf.make_grid(out_n), cf.make_grid(n), 2 * R, corner)
+        torch.cuda.synchronize()
+        assert torch.equal(corner, fields[:, :, : n[0], : n[1]])
+    emb.close()

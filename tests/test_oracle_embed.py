@@ -181,3 +181,29 @@ def test_threshold_zeroes_tiny_eigenvalues(orc):
     lp, s, rep = orc.psd(n, c, lam, clamp=True)
     assert list(lp) == [10.0, 0.0, 0.0, 5e-11, 0.0, 3.0, 0.0, 2.0]
     assert np.array_equal(s, np.sqrt(lp))
+
+
+@pytest.mark.parametrize("box_factor", [1, 2, 4])
+def test_periodic_box_spectrum_matches_continuous_transform(orc, box_factor):
+    """Section 3.3, eq. (Periodicboxmodes): for the Gaussian family the
+    continuous spectrum is P(k) = amp 2 pi s^2 exp(-k^2 s^2 / 2) (2D); the box
+    modes k = 2 pi m / B carry it, the DC mode is zero, and for box_factor 1
+    the modes sit on the even frequencies of the 2n grid with weight 4."""
+    n, s, amp = (32, 32), 3.0, 0.7
+    lam = orc.periodic_lambda(n, 0, amp, s, 0.0, box_factor, 2, 4)
+    Me = lam.shape
+    B = [(v // 2 if box_factor == 1 else v) for v in Me]
+    idx = np.indices(Me)
+    k2 = np.zeros(Me)
+    on = np.ones(Me, dtype=bool)
+    for a in range(2):
+        m = idx[a]
+        if box_factor == 1:
+            on &= m % 2 == 0
+            m = m // 2
+        f = np.where(m < B[a] // 2, m, m - B[a])
+        k2 = k2 + (2 * np.pi * f / B[a]) ** 2
+    P = amp * 2 * np.pi * s * s * np.exp(-k2 * s * s / 2) * (4.0 if box_factor == 1 else 1.0)
+    P[~on] = 0.0
+    P[0, 0] = 0.0
+    assert np.max(np.abs(lam - P)) <= 1e-12 * P.max()
