@@ -14,10 +14,17 @@ from .workloads import Workload
 
 
 class FieldPipeline:
-    def __init__(self, wl: Workload, device="cuda:0", stream=None, R=None, with_pk=True):
+    """Buffers and calls of one step.  With `embed_stream`, embeddings run on
+    that stream: the embedding of the next step (a binary64 job) then overlaps
+    the sampler and spectra of the current one, which stay on `stream`; an
+    embedding is released in stream order after its last use, so replacing it
+    while its sampler is still queued is safe."""
+
+    def __init__(self, wl: Workload, device="cuda:0", stream=None, R=None, with_pk=True, embed_stream=None):
         self.wl = wl
         self.dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        self.embed_stream = embed_stream if embed_stream is not None else self.stream
         self.R = wl.R if R is None else R
         self.dtype = cf.CF_F32 if wl.dtype == "f32" else cf.CF_F64
         self.tdtype = torch.float32 if wl.dtype == "f32" else torch.float64
@@ -49,7 +56,7 @@ class FieldPipeline:
     def embed(self, xi=None):
         if self.emb is not None:
             self.emb.close()
-        self.emb = cf.cf_embed(self.grid, xi or self.xi, self.flags, self.stream)
+        self.emb = cf.cf_embed(self.grid, xi or self.xi, self.flags, self.embed_stream)
         need = cf.cf_sample_workspace_size(self.emb, self.R, self.dtype)
         if self.ws is None or need > self.ws_bytes:
             self.ws_bytes = need
