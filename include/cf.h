@@ -70,7 +70,8 @@ typedef enum {
     CF_F64 = 0,      /* binary64 noise, transforms and fields                         */
     CF_F32 = 1,      /* binary32 noise, transforms and fields (eigenvalues stay FP64) */
     CF_BF16_TC = 2,  /* binary32 noise; bf16 DFT-matrix tensor-core stages with binary32
-                        accumulation; binary32 fields (cf_sample only, 2D, sides 256/4096) */
+                        accumulation; binary32 fields (cf_sample only, 2D, embedded
+                        sides 256, 512, 1024, 2048 or 4096) */
     CF_F16_TC = 3    /* as CF_BF16_TC with fp16 stage inputs                               */
 } cf_dtype;
 

@@ -315,74 +315,136 @@ __device__ __forceinline__ void tc_epilogue(unsigned char* smraw) {
     }
 }
 
+// ---------------------------------------------------------------- first radix
+// Lines of L = RF * LS points with RF in {2, 4, 8} (LS = 256) start with a
+// radix-RF decimation-in-frequency stage in binary32: for each n' < LS the
+// inputs x[n' + LS j], j < RF, give y_k = sum_j x_j w_RF^{jk}, multiplied by
+// w_L^{n' k}, which is point n' of sub-line k; the tensor-core stages then
+// transform the RF sub-lines of LS points, and output p' of sub-line k is
+// X[k + RF p'].  Keeping the first L/2 outputs keeps p' < LS/2 of every
+// sub-line.
+template <int RF>
+__device__ __forceinline__ void first_radix(C2<float> (&x)[RF], int np, const C2<float>* __restrict__ tw) {
+    if constexpr (RF > 1) {
+        dftR<RF, +1>(x);
+        constexpr int L = RF * 256;
+#pragma unroll
+        for (int k = 1; k < RF; ++k) x[k] = cmulf(x[k], tw[(np * k * (TWN / L)) & (TWN - 1)]);
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ C2<float> unpack2(uint32_t u) {
+    if constexpr (BF16) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+        return mk(f.x, f.y);
+    } else {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+        return mk(f.x, f.y);
+    }
+}
+
 // ---------------------------------------------------------------- pass 1
-// Rows of the embedded grid (L = M1): noise, scale, transform, keep n1 = L/2.
-// Block: WGS * LPW consecutive rows of realization r0 + blockIdx.y, LPW per
-// warpgroup.
-template <int S, bool BF16, int WGS>
+// Rows of the embedded grid (L = M1 = RF * LS): noise, scale, transform, keep
+// n1 = L/2.  Block: WGS * LPW consecutive rows of realization r0 + blockIdx.y,
+// LPW per warpgroup (RF sub-lines each).
+template <int S, int RF, bool BF16, int WGS>
 __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     k_tc_rows(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
               long long nrows, uint32_t* __restrict__ inter, const double* __restrict__ sumsq, double factor,
               const C2<float>* __restrict__ tw) {
-    constexpr int L = S == 3 ? 4096 : 256;
-    constexpr int RPL = L / 16;
-    constexpr int LPW = Geo<WGS>::kWgRows / RPL;
+    constexpr int LS = S == 3 ? 4096 : 256;
+    constexpr int L = RF * LS;
+    constexpr int RPL = LS / 16;
+    constexpr int SLPW = Geo<WGS>::kWgRows / RPL;  // sub-lines per warpgroup
+    constexpr int LPW = SLPW / RF;                  // lines per warpgroup
+    static_assert(LPW >= 1, "line does not fit a warpgroup");
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const int wg = threadIdx.x >> 7, wtid = threadIdx.x & 127;
     const TcShared sh = tc_prologue<BF16, WGS>(tc_smem, tw, wg);
     const float alpha = input_scale(sumsq, factor, false);
     const uint32_t r = r0 + blockIdx.y;
     const long long row0 = (long long)blockIdx.x * (WGS * LPW) + wg * LPW;
-    // loader: columns col and col + L/2 share one Philox call.  Within a warp,
-    // lanes take rows j + (lane & 7) of one row group and column groups
-    // (lane >> 3) + 4 b of the A operand (col = row + RPL * group): 32 banks.
+    if constexpr (RF == 1) {
+        // columns col and col + L/2 share one Philox call.  Within a warp,
+        // lanes take rows j + (lane & 7) of one row group and column groups
+        // (lane >> 3) + 4 b of the A operand (col = row + RPL * group): 32 banks.
 #pragma unroll 2
-    for (int t = wtid; t < LPW * (L / 2); t += 128) {
-        const int g = t / (L / 2), e = t % (L / 2);
-        const int lane = e & 31, w = e >> 5;
-        const int rr = (lane & 7) + 8 * (w % (RPL / 8));
-        const int grp = (lane >> 3) + 4 * (w / (RPL / 8));
-        const int col = rr + RPL * grp;
-        const long long row = row0 + g;
-        C2<float> lo, hi;
-        noise_pair_f32((unsigned long long)row * (L / 2) + col, r, key0, key1, lo, hi);
-        const float* srow = s + (size_t)row * L;
-        const C2<float> xl = cscale(cscale(lo, srow[col] * amp_scale), alpha);
-        const C2<float> xh = cscale(cscale(hi, srow[col + L / 2] * amp_scale), alpha);
-        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * grp)) = pack2<BF16>(xl.x, xl.y);
-        *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * (grp + 8))) = pack2<BF16>(xh.x, xh.y);
+        for (int t = wtid; t < LPW * (L / 2); t += 128) {
+            const int g = t / (L / 2), e = t % (L / 2);
+            const int lane = e & 31, w = e >> 5;
+            const int rr = (lane & 7) + 8 * (w % (RPL / 8));
+            const int grp = (lane >> 3) + 4 * (w / (RPL / 8));
+            const int col = rr + RPL * grp;
+            const long long row = row0 + g;
+            C2<float> lo, hi;
+            noise_pair_f32((unsigned long long)row * (L / 2) + col, r, key0, key1, lo, hi);
+            const float* srow = s + (size_t)row * L;
+            const C2<float> xl = cscale(cscale(lo, srow[col] * amp_scale), alpha);
+            const C2<float> xh = cscale(cscale(hi, srow[col + L / 2] * amp_scale), alpha);
+            *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * grp)) = pack2<BF16>(xl.x, xl.y);
+            *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * (grp + 8))) = pack2<BF16>(xh.x, xh.y);
+        }
+    } else {
+        // task (line g, point n' of the sub-lines): the RF inputs n' + LS j;
+        // inputs j and j + RF/2 are a Philox pair (their columns differ by L/2)
+#pragma unroll 1
+        for (int t = wtid; t < LPW * LS; t += 128) {
+            const int g = t / LS, e = t % LS;
+            const int lane = e & 31, w = e >> 5;
+            const int np = (lane & 7) + 8 * (w & 1) + 16 * ((lane >> 3) + 4 * (w >> 1));
+            const long long row = row0 + g;
+            const float* srow = s + (size_t)row * L;
+            C2<float> x[RF];
+#pragma unroll
+            for (int j = 0; j < RF / 2; ++j) {
+                const int col = np + LS * j;
+                C2<float> lo, hi;
+                noise_pair_f32((unsigned long long)row * (L / 2) + col, r, key0, key1, lo, hi);
+                x[j] = cscale(cscale(lo, srow[col] * amp_scale), alpha);
+                x[j + RF / 2] = cscale(cscale(hi, srow[col + L / 2] * amp_scale), alpha);
+            }
+            first_radix<RF>(x, np, tw);
+#pragma unroll
+            for (int k = 0; k < RF; ++k)
+                *reinterpret_cast<uint32_t*>(sh.A + a_off((g * RF + k) * RPL + np % RPL, 2 * (np / RPL))) =
+                    pack2<BF16>(x[k].x, x[k].y);
+        }
     }
     tc::fence_proxy_async_smem();
     tc::bar_sync(1 + wg, 128);
     uint32_t phase = 0;
     uint32_t* out = inter + ((size_t)blockIdx.y * nrows + row0) * (L / 2);
     run_stages<S, BF16, WGS>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
-                             [&](int line, int p, float re, float im) {
-                                 out[(size_t)line * (L / 2) + p] = pack2<BF16>(re, im);
+                             [&](int sl, int p, float re, float im) {
+                                 const int g = sl / RF, q = sl % RF + RF * p;
+                                 out[(size_t)g * (L / 2) + q] = pack2<BF16>(re, im);
                              });
     tc_epilogue<WGS>(tc_smem);
 }
 
 // ---------------------------------------------------------------- pass 2
-// Columns of the intermediate [M0][n1] (L = M0): transform, keep n0 = L/2,
-// write field 2r (Re) and 2r + 1 (Im) times 1/alpha.  Block: LC = WGS * LPW
-// adjacent columns, loaded by the whole block (LC consecutive 4-byte words of
-// a row per group of lanes).
-template <int S, bool BF16, int WGS>
+// Columns of the intermediate [M0][n1] (L = M0 = RF * LS): transform, keep
+// n0 = L/2, write field 2r (Re) and 2r + 1 (Im) times 1/alpha.  Block:
+// LC = WGS * LPW adjacent columns, loaded by the whole block.
+template <int S, int RF, bool BF16, int WGS>
 __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     k_tc_cols(const uint32_t* __restrict__ inter, long long n1, float* __restrict__ fields, long long cells,
               const double* __restrict__ sumsq, double factor, const C2<float>* __restrict__ tw) {
-    constexpr int L = S == 3 ? 4096 : 256;
-    constexpr int RPL = L / 16;
-    constexpr int LPW = Geo<WGS>::kWgRows / RPL;
+    constexpr int LS = S == 3 ? 4096 : 256;
+    constexpr int L = RF * LS;
+    constexpr int RPL = LS / 16;
+    constexpr int SLPW = Geo<WGS>::kWgRows / RPL;
+    constexpr int LPW = SLPW / RF;
     constexpr int LC = WGS * LPW;
+    static_assert(LPW >= 1, "line does not fit a warpgroup");
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const int wg = threadIdx.x >> 7;
     const TcShared sh = tc_prologue<BF16, WGS>(tc_smem, tw, wg);
     const float inv_alpha = input_scale(sumsq, factor, true);
     const long long cta0 = (long long)blockIdx.x * LC;
     const uint32_t* in = inter + (size_t)blockIdx.y * L * n1;
-    if constexpr (LC == 8) {
+    if constexpr (RF == 1 && LC == 8) {
         // lane & 7 -> column (warpgroup operand 4 banks apart), lane >> 3 ->
         // point group: 32 banks per store, 32-byte row segments per load
 #pragma unroll 4
@@ -394,13 +456,28 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
             unsigned char* A = tc_smem + (li / LPW) * Geo<WGS>::kAStride;
             *reinterpret_cast<uint32_t*>(A + a_off((li % LPW) * RPL + n % RPL, 2 * (n / RPL))) = v;
         }
-    } else {
+    } else if constexpr (RF == 1) {
 #pragma unroll 4
         for (int t = threadIdx.x; t < LC * L; t += Geo<WGS>::kThreads) {
             const int li = t % LC, n = t / LC;
             const uint32_t v = in[(size_t)n * n1 + cta0 + li];
             unsigned char* A = tc_smem + (li / LPW) * Geo<WGS>::kAStride;
             *reinterpret_cast<uint32_t*>(A + a_off((li % LPW) * RPL + n % RPL, 2 * (n / RPL))) = v;
+        }
+    } else {
+        // task (column li, point n'): the RF inputs n' + LS j of the column
+#pragma unroll 2
+        for (int t = threadIdx.x; t < LC * LS; t += Geo<WGS>::kThreads) {
+            const int li = t % LC, np = t / LC;
+            C2<float> x[RF];
+#pragma unroll
+            for (int j = 0; j < RF; ++j) x[j] = unpack2<BF16>(in[(size_t)(np + LS * j) * n1 + cta0 + li]);
+            first_radix<RF>(x, np, tw);
+            unsigned char* A = tc_smem + (li / LPW) * Geo<WGS>::kAStride;
+#pragma unroll
+            for (int k = 0; k < RF; ++k)
+                *reinterpret_cast<uint32_t*>(A + a_off(((li % LPW) * RF + k) * RPL + np % RPL, 2 * (np / RPL))) =
+                    pack2<BF16>(x[k].x, x[k].y);
         }
     }
     tc::fence_proxy_async_smem();
@@ -409,8 +486,9 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     float* f0 = fields + (size_t)blockIdx.y * 2 * cells;
     const long long c0 = cta0 + wg * LPW;
     run_stages<S, BF16, WGS>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
-                             [&](int line, int p, float re, float im) {
-                                 const size_t o = (size_t)p * n1 + c0 + line;
+                             [&](int sl, int p, float re, float im) {
+                                 const int g = sl / RF, q = sl % RF + RF * p;
+                                 const size_t o = (size_t)q * n1 + c0 + g;
                                  f0[o] = re * inv_alpha;
                                  f0[o + cells] = im * inv_alpha;
                              });
@@ -421,39 +499,60 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
 #define CF_TC_WGS 8  // warpgroups per block (2, 4 or 8): build-time tunable
 #endif
 
-template <bool BF16>
-cf_status launch_tc(int S, bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
-                    uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
-                    long long cells, const double* sumsq, double factor) {
+template <bool BF16, int S, int RF>
+cf_status launch_tc_shape(bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
+                          uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
+                          long long cells, const double* sumsq, double factor) {
     constexpr int WGS = CF_TC_WGS;
     using Gm = Geo<WGS>;
+    constexpr int L = RF * (S == 3 ? 4096 : 256);
     const C2<float>* tw = twiddles_f32();
     if (rows) {
-        auto kern = S == 3 ? k_tc_rows<3, BF16, WGS> : k_tc_rows<2, BF16, WGS>;
+        auto kern = k_tc_rows<S, RF, BF16, WGS>;
         CF_TRY(prepare_smem(kern, Gm::kSmem));
-        ScopedKernelTimer kt(st, BF16 ? "tc_rows_bf16" : "tc_rows_f16", S == 3 ? 4096 : 256);
+        ScopedKernelTimer kt(st, BF16 ? "tc_rows_bf16" : "tc_rows_f16", L);
         kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(s, amp, key0, key1, r0, nrows, inter, sumsq, factor, tw);
     } else {
-        auto kern = S == 3 ? k_tc_cols<3, BF16, WGS> : k_tc_cols<2, BF16, WGS>;
+        auto kern = k_tc_cols<S, RF, BF16, WGS>;
         CF_TRY(prepare_smem(kern, Gm::kSmem));
-        ScopedKernelTimer kt(st, BF16 ? "tc_cols_bf16" : "tc_cols_f16", S == 3 ? 4096 : 256);
+        ScopedKernelTimer kt(st, BF16 ? "tc_cols_bf16" : "tc_cols_f16", L);
         kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(inter, n1, fields, cells, sumsq, factor, tw);
     }
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
 
-int stages_of(long long L) { return L == 4096 ? 3 : (L == 256 ? 2 : 0); }
+template <bool BF16>
+cf_status launch_tc(long long L, bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
+                    uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
+                    long long cells, const double* sumsq, double factor) {
+    switch (L) {
+    case 4096: return launch_tc_shape<BF16, 3, 1>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
+                                                  cells, sumsq, factor);
+    case 2048: return launch_tc_shape<BF16, 2, 8>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
+                                                  cells, sumsq, factor);
+    case 1024: return launch_tc_shape<BF16, 2, 4>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
+                                                  cells, sumsq, factor);
+    case 512: return launch_tc_shape<BF16, 2, 2>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
+                                                 cells, sumsq, factor);
+    case 256: return launch_tc_shape<BF16, 2, 1>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
+                                                 cells, sumsq, factor);
+    default: return fail(CF_ERR_UNSUPPORTED, "tensor-core line length %lld", L);
+    }
+}
+
+bool tc_length_ok(long long L) { return L == 256 || L == 512 || L == 1024 || L == 2048 || L == 4096; }
 
 }  // namespace
 
-// Lines per block of a pass with line length L (all warpgroups).
+// Lines per block of a pass with line length L (all warpgroups): the block
+// holds kCtaRows A rows, L/16 per line.
 static long long tc_lines_per_block(long long L) { return kCtaRows / (L / 16); }
 
 cf_status tc_check_grid(const GridInfo& g) {
-    if (g.ndim != 2 || !stages_of(g.m[0]) || !stages_of(g.m[1]))
+    if (g.ndim != 2 || !tc_length_ok(g.m[0]) || !tc_length_ok(g.m[1]))
         return fail(CF_ERR_UNSUPPORTED,
-                    "tensor-core modes need a 2D grid with embedded sides 256 or 4096 (got %dD, %lld x %lld)",
+                    "tensor-core modes need a 2D grid with embedded sides 256..4096 (got %dD, %lld x %lld)",
                     g.ndim, g.m[0], g.ndim > 1 ? g.m[1] : 0);
     return CF_OK;
 }
@@ -471,7 +570,6 @@ cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0
     const double* sumsq = e->sumsq;
     const double factor = 2.0 * (double)g.m[1] * amp_scale * amp_scale / (double)g.mtotal;
     uint32_t* inter = (uint32_t*)ws;
-    const int S0 = stages_of(g.m[0]), S1 = stages_of(g.m[1]);
     const long long cells = g.ncell;
     for (int c0 = 0; c0 < R; c0 += chunk) {
         const int nr = (R - c0) < chunk ? (R - c0) : chunk;
@@ -480,14 +578,14 @@ cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0
         const uint32_t rr = (uint32_t)(r0 + (uint64_t)c0);
         float* f = fields + (size_t)c0 * 2 * (size_t)cells;
         if (bf16) {
-            CF_TRY(launch_tc<true>(S1, true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32),
+            CF_TRY(launch_tc<true>(g.m[1], true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32),
                                    rr, g.m[0], inter, g.n[1], nullptr, cells, sumsq, factor));
-            CF_TRY(launch_tc<true>(S0, false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
+            CF_TRY(launch_tc<true>(g.m[0], false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
                                    factor));
         } else {
-            CF_TRY(launch_tc<false>(S1, true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed,
+            CF_TRY(launch_tc<false>(g.m[1], true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed,
                                     (uint32_t)(seed >> 32), rr, g.m[0], inter, g.n[1], nullptr, cells, sumsq, factor));
-            CF_TRY(launch_tc<false>(S0, false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
+            CF_TRY(launch_tc<false>(g.m[0], false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
                                     factor));
         }
     }

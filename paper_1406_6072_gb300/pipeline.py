@@ -52,6 +52,13 @@ class FieldPipeline:
                 self.pkg = torch.empty_like(self.pk)
                 self.meang = torch.empty_like(self.mean)
                 self.covg = torch.empty_like(self.cov)
+                # the count maps' spectra run beside the fields' on a second
+                # stream, with their own workspace and mode counts
+                self.pk_ws_g = torch.empty(self.pk_ws_bytes, dtype=torch.uint8, device=self.dev)
+                self.nmodes_g = torch.empty_like(self.nmodes)
+                self.stream_g = torch.cuda.Stream(self.dev)
+                self.ev_sampled = torch.cuda.Event()
+                self.ev_counts_done = torch.cuda.Event()
 
     def embed(self, xi=None):
         if self.emb is not None:
@@ -89,11 +96,18 @@ class FieldPipeline:
         if not self.with_pk:
             return
         F = 2 * self.R
+        if self.with_lp:
+            self.ev_sampled.record(self.stream)
+            self.stream_g.wait_event(self.ev_sampled)
+            cf.cf_power_spectrum_counts(self.counts, None, self.grid, F, self.bins, self.pkg, self.nmodes_g,
+                                        self.meang, self.covg, self.pk_ws_g, self.pk_ws_bytes, self.stream_g)
+            self.ev_counts_done.record(self.stream_g)
         cf.cf_power_spectrum(self.fields, self.dtype, self.grid, F, self.bins, self.pk, self.nmodes, self.mean,
                              self.cov, self.pk_ws, self.pk_ws_bytes, self.stream)
         if self.with_lp:
-            cf.cf_power_spectrum_counts(self.counts, None, self.grid, F, self.bins, self.pkg, self.nmodes,
-                                        self.meang, self.covg, self.pk_ws, self.pk_ws_bytes, self.stream)
+            # the step ends on the main stream once both spectra are done (the
+            # next sampling overwrites the count maps)
+            self.stream.wait_event(self.ev_counts_done)
 
     def step(self, r0=0):
         """Embed + sample (+ lognormal/Poisson) + spectra for realizations [r0, r0+R)."""

@@ -35,12 +35,17 @@ def _tc_fields(emb, seed, r0, R, dt, n, ws_bytes=None):
 
 
 def _stages(n):
-    return max(3 if 2 * v == 4096 else 2 for v in n)
+    # rounding stages per axis: 2 radix-16 stages for 256 points, 3 for 4096,
+    # and a binary32 first radix (2, 4 or 8) before 2 radix-16 stages otherwise
+    return max(2 if 2 * v == 256 else 3 for v in n)
 
 
 CASES = [((128, 128), cf.CF_XI_GAUSSIAN, 4.0, 0.0, False),
          ((128, 2048), cf.CF_XI_EXPONENTIAL, 6.0, 0.0, False),
-         ((2048, 128), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True)]
+         ((2048, 128), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True),
+         ((256, 512), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True),    # first radix 2 and 4
+         ((1024, 128), cf.CF_XI_EXPONENTIAL, 5.0, 0.0, False),  # first radix 8
+         ((512, 512), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True)]     # the 2D 512^2 workload's grid
 
 
 @pytest.mark.parametrize("dt", [cf.CF_BF16_TC, cf.CF_F16_TC])
@@ -119,7 +124,7 @@ def test_tc_deterministic_and_chunk_independent():
 
 
 def test_tc_unsupported_and_errors():
-    emb = cf.cf_embed(cf.make_grid((512, 512)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))
+    emb = cf.cf_embed(cf.make_grid((64, 64)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))  # sides 128: too short
     with pytest.raises(cf.CfError) as ei:
         cf.cf_sample_workspace_size(emb, 1, cf.CF_BF16_TC)
     assert ei.value.status == cf.CF_ERR_UNSUPPORTED
