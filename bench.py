@@ -44,6 +44,7 @@ def parse_args():
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cufft-reference", action="store_true", help="skip the cuFFT reference timing")
     p.add_argument("--cpu-sample-realizations", type=int, default=8)
     p.add_argument("--serve-requests", type=int, default=10000)
     p.add_argument("--tune", action="store_true", help="autotune the sampler's chunk schedule before warm-up")
@@ -815,7 +816,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_sample_realizations)
-    cufft = cufft_reference(wl, R, stream) if rank == 0 else None
+    cufft = cufft_reference(wl, R, stream) if rank == 0 and not args.no_cufft_reference else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

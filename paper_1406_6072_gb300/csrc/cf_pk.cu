@@ -78,12 +78,13 @@ struct PkColsCfg : TileCfg<T, L, CF_PKC_E, CF_PKC_THREADS, CF_PKC_MINB> {
     static constexpr int C = TileCfg<T, L, CF_PKC_E, CF_PKC_THREADS, CF_PKC_MINB>::LINES;
 };
 
-template <typename T, int L>
+template <typename T, int L, int KIND>
 __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MINB)
-    k_pk_rows(const void* __restrict__ fields, int kind, const float* __restrict__ f,
+    k_pk_rows(const void* __restrict__ fields, int kind_unused, const float* __restrict__ f,
               unsigned long long* __restrict__ ntot, double* __restrict__ fsum, long long rows, long long cells,
               long long nfields, long long f0, C2<T>* __restrict__ out, const C2<T>* __restrict__ tw) {
     using Cfg = PkRowsCfg<T, L>;
+    constexpr int kind = KIND;  // compile-time: the loads of the loader are not behind branches
     using G = typename Cfg::G;
     constexpr int E = G::E;
     constexpr int STEP = L / E;
@@ -103,19 +104,21 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
     double fs = 0.0;
     auto value = [&](long long fld, long long p, unsigned long long& ncount) -> T {
         const size_t at = (size_t)fld * cells + (size_t)rw * L + p;
-        if (kind == PK_FLOAT) return (T)((const float*)fields)[at];
-        if (kind == PK_DOUBLE) return (T)((const double*)fields)[at];
-        const long long cell = rw * L + p;
-        if (kind == PK_MASK) {
-            const float fi = f[cell];
+        if constexpr (kind == PK_FLOAT) {
+            return (T)((const float*)fields)[at];
+        } else if constexpr (kind == PK_DOUBLE) {
+            return (T)((const double*)fields)[at];
+        } else if constexpr (kind == PK_MASK) {
+            const float fi = f[rw * L + p];
             if (valid) fs += (double)fi;
             return fi != 0.0f ? (T)1 : (T)0;
+        } else {
+            const int32_t N = ((const int32_t*)fields)[at];
+            if (valid) ncount += (unsigned long long)(long long)N;
+            if (!f) return (T)N;
+            const T fi = (T)f[rw * L + p];
+            return fi != (T)0 ? (T)N / fi : (T)0;
         }
-        const int32_t N = ((const int32_t*)fields)[at];
-        if (valid) ncount += (unsigned long long)(long long)N;
-        if (!f) return (T)N;
-        const T fi = (T)f[cell];
-        return fi != (T)0 ? (T)N / fi : (T)0;
     };
     C2<T> v[E];
 #pragma unroll
@@ -124,18 +127,37 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
         const T va = value(fa, p, na);
         v[q] = mk(va, hasb ? value(fb, p, nb) : (T)0);
     }
-    if (kind == PK_COUNTS || kind == PK_MASK) {
+    if constexpr (kind == PK_COUNTS || kind == PK_MASK) {
+        // totals of the block (all its lines belong to fields fa, fb): warp
+        // sums, then one atomic per block and field (not one per warp: the
+        // blocks of a field would all queue on one address)
+        constexpr int NW = Cfg::THREADS / 32;
+        __shared__ unsigned long long s_na[NW], s_nb[NW];
+        __shared__ double s_fs[NW];
         for (int o = 16; o > 0; o >>= 1) {
             na += __shfl_down_sync(0xffffffffu, na, o);
             nb += __shfl_down_sync(0xffffffffu, nb, o);
             fs += __shfl_down_sync(0xffffffffu, fs, o);
         }
         if ((threadIdx.x & 31) == 0) {
+            s_na[threadIdx.x >> 5] = na;
+            s_nb[threadIdx.x >> 5] = nb;
+            s_fs[threadIdx.x >> 5] = fs;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long ta = 0, tb = 0;
+            double tf = 0.0;
+            for (int w = 0; w < NW; ++w) {
+                ta += s_na[w];
+                tb += s_nb[w];
+                tf += s_fs[w];
+            }
             if (kind == PK_COUNTS) {
-                if (na) atomicAdd(&ntot[fa], na);
-                if (nb) atomicAdd(&ntot[fb], nb);
-            } else if (fs != 0.0) {
-                atomicAdd(fsum, fs);
+                if (ta) atomicAdd(&ntot[fa], ta);
+                if (tb) atomicAdd(&ntot[fb], tb);
+            } else if (tf != 0.0) {
+                atomicAdd(fsum, tf);
             }
         }
     }
@@ -514,7 +536,16 @@ static cf_status launch_pk_rows(const void* fields, int kind, const float* f, un
                                 double* fsum, const PkPlan& P, long long nfields, long long f0, long long nchunk,
                                 C2<T>* out, cudaStream_t s) {
     using Cfg = PkRowsCfg<T, L>;
-    auto kern = k_pk_rows<T, L>;
+    using Kern = decltype(&k_pk_rows<T, L, PK_FLOAT>);
+    Kern kern = nullptr;
+    if constexpr (sizeof(T) == 8) {
+        if (kind == PK_DOUBLE) kern = k_pk_rows<T, L, PK_DOUBLE>;
+    } else {
+        if (kind == PK_FLOAT) kern = k_pk_rows<T, L, PK_FLOAT>;
+        else if (kind == PK_COUNTS) kern = k_pk_rows<T, L, PK_COUNTS>;
+        else if (kind == PK_MASK) kern = k_pk_rows<T, L, PK_MASK>;
+    }
+    if (!kern) return fail(CF_ERR_UNSUPPORTED, "power-spectrum input kind %d with this precision", kind);
     CF_TRY(prepare_smem(kern, Cfg::SMEM));
     dim3 grid((unsigned)((P.rows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)((nchunk + 1) / 2));
     ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_rows_f32" : "pk_rows_f64", L);

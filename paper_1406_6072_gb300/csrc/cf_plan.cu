@@ -170,7 +170,13 @@ extern "C" cf_status cf_plan_create(const cf_embedding* e, uint64_t seed, uint64
     }
     cudaStream_t cap = nullptr;
     PLAN_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    PLAN_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    {
+        const cudaError_t eb = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+        if (eb != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return bail(fail(CF_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(eb)));
+        }
+    }
     const cf_status body = plan_body(p, a, cap);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cap, &graph);

@@ -35,28 +35,31 @@ class CudaBackend : public cfserve::Backend {
   public:
     CudaBackend(int device, int nslots, int max_real) : device_(device), max_real_(max_real) {
         cudaSetDevice(device_);
-        cudaStreamCreateWithFlags(&embed_stream_, cudaStreamNonBlocking);
+        ok_ = cudaStreamCreateWithFlags(&embed_stream_, cudaStreamNonBlocking) == cudaSuccess;
         slots_.resize(nslots);
         for (auto& s : slots_) {
-            cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
-            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
-            cudaMallocHost((void**)&s.host_desc, sizeof(RealDesc) * (size_t)max_real);
-            cudaMalloc((void**)&s.dev_desc, sizeof(RealDesc) * (size_t)max_real);
+            ok_ = ok_ && cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess;
+            ok_ = ok_ && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess;
+            ok_ = ok_ && cudaMallocHost((void**)&s.host_desc, sizeof(RealDesc) * (size_t)max_real) == cudaSuccess;
+            ok_ = ok_ && cudaMalloc((void**)&s.dev_desc, sizeof(RealDesc) * (size_t)max_real) == cudaSuccess;
             s.capacity = max_real;
         }
     }
+
+    // every stream, event and descriptor buffer was created
+    bool ok() const { return ok_; }
 
     ~CudaBackend() override {
         cudaSetDevice(device_);
         cudaDeviceSynchronize();
         for (auto& s : slots_) {
             if (s.ws) cudaFree(s.ws);
-            cudaFree(s.dev_desc);
-            cudaFreeHost(s.host_desc);
-            cudaEventDestroy(s.done);
-            cudaStreamDestroy(s.stream);
+            if (s.dev_desc) cudaFree(s.dev_desc);
+            if (s.host_desc) cudaFreeHost(s.host_desc);
+            if (s.done) cudaEventDestroy(s.done);
+            if (s.stream) cudaStreamDestroy(s.stream);
         }
-        cudaStreamDestroy(embed_stream_);
+        if (embed_stream_) cudaStreamDestroy(embed_stream_);
     }
 
     static GridInfo grid_of(const cf_request& r) {
@@ -187,6 +190,7 @@ class CudaBackend : public cfserve::Backend {
   private:
     int device_;
     int max_real_;
+    bool ok_ = false;
     cudaStream_t embed_stream_ = nullptr;
     std::vector<CudaSlot> slots_;
     std::map<cfserve::Job*, cudaStream_t> result_stream_;
@@ -213,7 +217,11 @@ extern "C" cf_status cf_serve_create(const cf_serve_cfg* cfg, cf_server** out) {
     CF_TRY(ensure_device_init());
     cf_server* sv = new cf_server();
     sv->backend.reset(new CudaBackend(cfg->device, cfg->max_inflight, cfg->max_batch_realizations));
-    CF_CUDA(cudaGetLastError());
+    if (!sv->backend->ok()) {
+        delete sv;
+        cudaGetLastError();
+        return fail(CF_ERR_NOMEM, "serving streams or descriptor buffers could not be created");
+    }
     sv->sched.reset(new cfserve::Scheduler(*cfg, sv->backend.get()));
     *out = sv;
     return CF_OK;

@@ -483,15 +483,26 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     tc::fence_proxy_async_smem();
     __syncthreads();
     uint32_t phase = 0;
-    float* f0 = fields + (size_t)blockIdx.y * 2 * cells;
-    const long long c0 = cta0 + wg * LPW;
+    // the last stage's outputs go to this warpgroup's operand buffer (its MMAs
+    // have completed): stage[sl][p], p < LS/2, as (re, im) ...
+    float2* stage = reinterpret_cast<float2*>(sh.A);
     run_stages<S, BF16, WGS>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
                              [&](int sl, int p, float re, float im) {
-                                 const int g = sl / RF, q = sl % RF + RF * p;
-                                 const size_t o = (size_t)q * n1 + c0 + g;
-                                 f0[o] = re * inv_alpha;
-                                 f0[o + cells] = im * inv_alpha;
+                                 stage[sl * (LS / 2) + p] = make_float2(re, im);
                              });
+    __syncthreads();
+    // ... then the block writes rows q < L/2 of its LC adjacent columns
+    float* f0 = fields + (size_t)blockIdx.y * 2 * cells;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < LC * (L / 2); t += Geo<WGS>::kThreads) {
+        const int li = t % LC, q = t / LC;
+        const int sl = (li % LPW) * RF + q % RF, p = q / RF;
+        const float2* st = reinterpret_cast<const float2*>(tc_smem + (li / LPW) * Geo<WGS>::kAStride);
+        const float2 v = st[sl * (LS / 2) + p];
+        const size_t o = (size_t)q * n1 + cta0 + li;
+        f0[o] = v.x * inv_alpha;
+        f0[o + cells] = v.y * inv_alpha;
+    }
     tc_epilogue<WGS>(tc_smem);
 }
 
