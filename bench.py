@@ -245,6 +245,35 @@ def cpu_baseline(wl, realizations):
                                                              "x".join(map(str, wl.n)), dt)}
 
 
+def _oracle_worker(task):
+    """One host process of the all-cores baseline: the oracle on `realizations`
+    realizations starting at r0 (its own embedding included)."""
+    name, realizations, r0 = task
+    from paper_1406_6072_gb300 import workloads as W
+    cells, dt, _ = oracle_sample_run(W.CONFIGS[name], realizations, r0)
+    return cells
+
+
+def cpu_baseline_all_cores(wl, per_core):
+    """The same oracle run on every host core at once, parallel over
+    realizations (one process per core, started with spawn), wall time."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    tasks = [(wl.name, per_core, c * per_core) for c in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [(wl.name, 1, 10 ** 6 + c) for c in range(cores)])  # start-up outside the clock
+        t0 = time.perf_counter()
+        cells = sum(pool.map(_oracle_worker, tasks))
+        dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d processes x %d realization(s) of %s, each with its own embedding, wall %.1f s"
+                      % (cores, per_core, wl.name, dt)}
+
+
 def run_reference(args):
     from paper_1406_6072_gb300 import workloads as W
     rank = int(os.environ.get("RANK", "0"))
@@ -650,6 +679,19 @@ def run_serving(args):
     seq_wall = time.perf_counter() - t_all
     lat = np.sort(np.asarray(lat))
     served = rates["1.0x"]
+    # CPU baseline: the oracle, one request at a time, on the same subsample
+    # (in order) until 30 s have passed; realizations/s over what it finished
+    import oracle
+    oracle.build()
+    o_reals, o_done, t_o = 0, 0, time.perf_counter()
+    for q in sub:
+        e = oracle.embed(list(q["n"]), q["xi_kind"], q["amp"], q["scale"], q["beta"], clamp=True)
+        oracle.sample(q["n"], e["sqrt_lambda"], q["seed"], 0, q["R"], 0)
+        o_reals += q["R"]
+        o_done += 1
+        if time.perf_counter() - t_o > 30.0:
+            break
+    o_wall = time.perf_counter() - t_o
     line = {"metric": "served realizations/s, mixed 2D/3D request stream (Poisson arrivals at capacity)",
             "value": served["realizations_per_s"], "unit": "realizations/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -660,7 +702,10 @@ def run_serving(args):
             "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"], "rates": rates,
             "sequential_f64": {"requests": len(sub), "realizations_per_s": reals / seq_wall,
                                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                               "note": "one request at a time: cf_embed + binary64 cf_sample, synchronised"}}
+                               "note": "one request at a time: cf_embed + binary64 cf_sample, synchronised"},
+            "cpu_baseline": {"value": o_reals / o_wall, "unit": "realizations/s", "cores": 1, "kind": "oracle",
+                             "sample": "the first %d requests of the same 200-request subsample (%d realizations), "
+                                       "embedding + binary64 fields per request, %.1f s" % (o_done, o_reals, o_wall)}}
     print(json.dumps(line))
     return 0
 
@@ -813,9 +858,10 @@ def main():
             e_max = replicas.max_over_ranks(e_ms, dist, dev)
             e2e = {"value": cells_all / (e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e_max}
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_sample_realizations)
+        cpu_all = cpu_baseline_all_cores(wl, 2)
     cufft = cufft_reference(wl, R, stream) if rank == 0 and not args.no_cufft_reference else None
     if rank == 0:
         line = {
@@ -827,7 +873,8 @@ def main():
                        "l2": "each step writes %d MiB of fields and counts (> 129 MB L2)"
                              % (2 * pipe.cells_per_step * 4 >> 20),
                        "parallelism": "replicas x%d" % world, "tuned_chunk": tuned},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+            "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report, "cufft_reference": cufft,
             "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(per_kernel.items())},
         }

@@ -121,11 +121,47 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
         }
     };
     C2<T> v[E];
+    if constexpr (kind == PK_COUNTS) {
+        // all loads first (no branch between them), then totals and the mask
+        int32_t Na[E], Nb[E];
+        const int32_t* ca = (const int32_t*)fields + (size_t)fa * cells + (size_t)rw * L;
+        const int32_t* cb = (const int32_t*)fields + (size_t)(hasb ? fb : fa) * cells + (size_t)rw * L;
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-        const long long p = j + q * STEP;
-        const T va = value(fa, p, na);
-        v[q] = mk(va, hasb ? value(fb, p, nb) : (T)0);
+        for (int q = 0; q < E; ++q) {
+            Na[q] = ca[j + q * STEP];
+            Nb[q] = cb[j + q * STEP];
+        }
+        if (!hasb) {
+#pragma unroll
+            for (int q = 0; q < E; ++q) Nb[q] = 0;
+        }
+        if (valid) {
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                na += (unsigned long long)(long long)Na[q];
+                nb += (unsigned long long)(long long)Nb[q];
+            }
+        }
+        if (f) {
+            float fq[E];
+#pragma unroll
+            for (int q = 0; q < E; ++q) fq[q] = f[rw * L + j + q * STEP];
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const T fi = (T)fq[q];
+                v[q] = fi != (T)0 ? mk((T)Na[q] / fi, (T)Nb[q] / fi) : mk((T)0, (T)0);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < E; ++q) v[q] = mk((T)Na[q], (T)Nb[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const long long p = j + q * STEP;
+            const T va = value(fa, p, na);
+            v[q] = mk(va, hasb ? value(fb, p, nb) : (T)0);
+        }
     }
     if constexpr (kind == PK_COUNTS || kind == PK_MASK) {
         // totals of the block (all its lines belong to fields fa, fb): warp
@@ -536,7 +572,7 @@ static cf_status launch_pk_rows(const void* fields, int kind, const float* f, un
                                 double* fsum, const PkPlan& P, long long nfields, long long f0, long long nchunk,
                                 C2<T>* out, cudaStream_t s) {
     using Cfg = PkRowsCfg<T, L>;
-    using Kern = decltype(&k_pk_rows<T, L, PK_FLOAT>);
+    using Kern = decltype(&k_pk_rows<T, L, sizeof(T) == 8 ? PK_DOUBLE : PK_FLOAT>);
     Kern kern = nullptr;
     if constexpr (sizeof(T) == 8) {
         if (kind == PK_DOUBLE) kern = k_pk_rows<T, L, PK_DOUBLE>;
