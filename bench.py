@@ -308,7 +308,8 @@ def run_reference(args):
 
 # --------------------------------------------------------------- precision sweep
 def run_sweep(args):
-    """2D 2048^2 survey in 4096^2, 32 realizations per step: sampler + power
+    """Precision sweep: the 2D 2048^2 survey in 4096^2 (32 realizations per
+    step) or the 3D 256^3 survey in 512^3 (4 per step), sampler + power
     spectrum in binary64, binary32 and the bf16 / fp16 tensor-core modes, the
     same seeds for all.  Reports cells/s per precision (embedding cached, as
     in a sweep over precisions of one spectrum); the error of each precision
@@ -319,7 +320,7 @@ def run_sweep(args):
     from paper_1406_6072_gb300 import workloads as W
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    wl = W.CONFIGS["cauchy2d_n2048_sweep"]
+    wl = W.CONFIGS[args.workload]
     stream = torch.cuda.Stream(dev)
     grid = cf.make_grid(wl.n)
     R, F = wl.R, 2 * wl.R
@@ -373,7 +374,9 @@ def run_sweep(args):
         emb.close()
     clk = clocks.stop()
     head = "f32" if "f32" in out else next(iter(out))
-    line = {"metric": "cells/s per precision, 2D 2048^2 sampler + power spectrum", "value": out[head]["cells_per_s"],
+    side = "x".join(str(v) for v in wl.n)
+    line = {"metric": f"cells/s per precision, {wl.ndim}D {side} sampler + power spectrum",
+            "value": out[head]["cells_per_s"],
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "sweep", "data": "synthetic",
             "config": {"workload": wl.name, "text": wl.text, "realizations_per_step": R,
                        "note": "embedding cached across steps; errors vs the binary64 oracle: tests/test_gpu_tc.py"},
@@ -750,8 +753,9 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
         # copies have read the previous results
         ln = lanes[k % 2]
         p = ln["p"]
+        with torch.cuda.stream(p.embed_stream):
+            ln["d_table"].copy_(h_table, non_blocking=True)  # read by the embedding, in its stream order
         with torch.cuda.stream(p.stream):
-            ln["d_table"].copy_(h_table, non_blocking=True)
             p.embed(ln["xi"])
             p.stream.wait_event(ln["done"])
             p.sample(r0=replicas.realization_start(rank, world, k, p.R))
@@ -783,7 +787,7 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
-    if args.workload == "cauchy2d_n2048_sweep":
+    if args.workload.endswith("_sweep"):
         return run_sweep(args)
     if args.graph:
         return run_graph(args)

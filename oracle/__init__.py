@@ -75,10 +75,10 @@ def _lib_handle():
         lib.or_embed_row.argtypes = [C.c_int32, _P, _P, C.c_int32, C.c_double, C.c_double,
                                      C.c_double, _P, _P]
         lib.or_eigenvalues.argtypes = [C.c_int32, _P, _P, _P]
-        lib.or_psd.argtypes = [C.c_int32, _P, _P, _P, C.c_int32, _P, _P, C.POINTER(Report)]
-        lib.or_sample.argtypes = [C.c_int32, _P, _P, C.c_uint64, C.c_uint64, C.c_int32,
+        lib.or_psd.argtypes = [C.c_int32, _P, _P, _P, _P, C.c_int32, _P, _P, C.POINTER(Report)]
+        lib.or_sample.argtypes = [C.c_int32, _P, _P, _P, C.c_uint64, C.c_uint64, C.c_int32,
                                   C.c_int32, _P]
-        lib.or_sample_given_noise.argtypes = [C.c_int32, _P, _P, _P, _P]
+        lib.or_sample_given_noise.argtypes = [C.c_int32, _P, _P, _P, _P, _P]
         lib.or_poisson_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
         lib.or_poisson_uniform.restype = C.c_double
         lib.or_poisson_icdf.argtypes = [C.c_double, C.c_double, _P]
@@ -162,27 +162,40 @@ def fft_nd(x, sign):
 
 
 # ---------------------------------------------------------------- embedding
-def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, log1p=False):
-    """First row c of the circulant (step a1, section 2 eq. (grid)).  log1p:
-    xi is the correlation function of the lognormal density and the Gaussian
+def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, log1p=False, factor=2):
+    """First row c of the circulant (step a1, section 2 eq. (grid)) on the
+    embedded grid of `factor` times the survey side per axis (2: the paper's
+    box of twice the side; a larger box embeds the same way, section 2, Fig. 1:
+    any survey-sized sub-box of it has the target covariance).  log1p: xi is
+    the correlation function of the lognormal density and the Gaussian
     covariance is ln(1 + xi) (section 3.1, eq. (Lncov))."""
-    dims, d = _dims(n)
+    d = len(n)
     cellv = np.ones(3) if cell is None else np.asarray(list(cell) + [1.0] * (3 - len(cell)))
-    M = [2 * int(v) for v in n]
+    M = [int(factor) * int(v) for v in n]
+    mdims, _ = _dims(M)
     c = np.zeros(int(np.prod(M)), dtype=np.float64)
     tab = None if table is None else np.ascontiguousarray(table, dtype=np.float64).ravel()
-    _lib_handle().or_embed_row(d, _ptr(dims), _ptr(cellv), kind, amp, scale, beta, _ptr(tab),
+    _lib_handle().or_embed_row(d, _ptr(mdims), _ptr(cellv), kind, amp, scale, beta, _ptr(tab),
                                _ptr(c))
     if log1p:
         c = np.log1p(c)
     return c.reshape(M)
 
 
+def _mdims(n, a):
+    """Embedded sides: the shape of the M^d array `a` (survey sizes n)."""
+    a = np.asarray(a)
+    shape = a.shape if a.ndim == len(n) else (tuple(2 * int(v) for v in n) if a.ndim == 1 else a.shape)
+    if int(np.prod(shape)) != a.size or len(shape) != len(n):
+        raise ValueError("array does not have the embedded grid's shape")
+    return _dims(shape)[0]
+
+
 def eigenvalues(n, c):
-    dims, d = _dims(n)
+    d = len(n)
     c = np.ascontiguousarray(c, dtype=np.float64)
     lam = np.zeros(c.size, dtype=np.float64)
-    _lib_handle().or_eigenvalues(d, _ptr(dims), _ptr(c), _ptr(lam))
+    _lib_handle().or_eigenvalues(d, _ptr(_mdims(n, c)), _ptr(c), _ptr(lam))
     return lam.reshape(c.shape)
 
 
@@ -193,14 +206,14 @@ def psd(n, c, lam, clamp=False):
     lp = np.zeros_like(lam)
     s = np.zeros_like(lam)
     rep = Report()
-    _lib_handle().or_psd(d, _ptr(dims), _ptr(c), _ptr(lam), int(bool(clamp)), _ptr(lp), _ptr(s),
-                         C.byref(rep))
+    _lib_handle().or_psd(d, _ptr(dims), _ptr(_mdims(n, c)), _ptr(c), _ptr(lam), int(bool(clamp)), _ptr(lp),
+                         _ptr(s), C.byref(rep))
     return lp, s, rep.asdict()
 
 
-def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False, log1p=False):
+def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False, log1p=False, factor=2):
     """Steps a1-a3: first row c, eigenvalues lambda, lambda+, sqrt(lambda+), report."""
-    c = embed_row(n, kind, amp, scale, beta, cell, table, log1p)
+    c = embed_row(n, kind, amp, scale, beta, cell, table, log1p, factor)
     lam = eigenvalues(n, c)
     lp, s, rep = psd(n, c, lam, clamp)
     return {"c": c, "lambda": lam, "lambda_plus": lp, "sqrt_lambda": s, "report": rep}
@@ -212,7 +225,7 @@ def sample(n, s, seed, r0, R, dtype):
     dims, d = _dims(n)
     s = np.ascontiguousarray(s, dtype=np.float64)
     out = np.zeros((R, 2) + tuple(int(v) for v in n), dtype=np.float64)
-    _lib_handle().or_sample(d, _ptr(dims), _ptr(s), seed, r0, R, dtype, _ptr(out))
+    _lib_handle().or_sample(d, _ptr(dims), _ptr(_mdims(n, s)), _ptr(s), seed, r0, R, dtype, _ptr(out))
     return out
 
 
@@ -221,7 +234,7 @@ def sample_given_noise(n, s, eps):
     s = np.ascontiguousarray(s, dtype=np.float64)
     e = np.ascontiguousarray(np.stack([np.real(eps), np.imag(eps)], axis=-1), dtype=np.float64)
     w = np.zeros(tuple(int(v) for v in n) + (2,), dtype=np.float64)
-    _lib_handle().or_sample_given_noise(d, _ptr(dims), _ptr(s), _ptr(e), _ptr(w))
+    _lib_handle().or_sample_given_noise(d, _ptr(dims), _ptr(_mdims(n, s)), _ptr(s), _ptr(e), _ptr(w))
     return w[..., 0] + 1j * w[..., 1]
 
 

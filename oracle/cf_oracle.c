@@ -390,15 +390,11 @@ static double or_xi(int32_t kind, double amp, double scale, double beta, double 
     }
 }
 
-void or_embed_row(int32_t ndim, const int64_t* n, const double* cell, int32_t kind,
+void or_embed_row(int32_t ndim, const int64_t* M, const double* cell, int32_t kind,
                   double amp, double scale, double beta, const double* table, double* c)
 {
-    int64_t M[3] = {1, 1, 1};
     int64_t total = 1;
-    for (int d = 0; d < ndim; ++d) {
-        M[d] = 2 * n[d];
-        total *= M[d];
-    }
+    for (int d = 0; d < ndim; ++d) total *= M[d];
     for (int64_t idx = 0; idx < total; ++idx) {
         if (kind == OR_XI_TABLE) {
             c[idx] = table[idx];
@@ -409,7 +405,7 @@ void or_embed_row(int32_t ndim, const int64_t* n, const double* cell, int32_t ki
         for (int d = ndim - 1; d >= 0; --d) {
             int64_t m = rem % M[d];
             rem /= M[d];
-            int64_t lag = (m < n[d]) ? m : m - M[d];
+            int64_t lag = (2 * m < M[d]) ? m : m - M[d];
             double x = (double)lag * cell[d];
             r2 += x * x;
         }
@@ -417,14 +413,10 @@ void or_embed_row(int32_t ndim, const int64_t* n, const double* cell, int32_t ki
     }
 }
 
-void or_eigenvalues(int32_t ndim, const int64_t* n, const double* c, double* lambda)
+void or_eigenvalues(int32_t ndim, const int64_t* M, const double* c, double* lambda)
 {
-    int64_t M[3];
     int64_t total = 1;
-    for (int d = 0; d < ndim; ++d) {
-        M[d] = 2 * n[d];
-        total *= M[d];
-    }
+    for (int d = 0; d < ndim; ++d) total *= M[d];
     double* z = (double*)calloc((size_t)total * 2, sizeof(double));
     for (int64_t i = 0; i < total; ++i) z[2 * i] = c[i];
     or_fft_nd(z, ndim, M, -1);
@@ -434,15 +426,11 @@ void or_eigenvalues(int32_t ndim, const int64_t* n, const double* c, double* lam
 
 /* Section 2, eq. (condition) and the remark after eq. (Papos2): the method
  * needs every eigenvalue non-negative. */
-void or_psd(int32_t ndim, const int64_t* n, const double* c, const double* lambda,
+void or_psd(int32_t ndim, const int64_t* n, const int64_t* M, const double* c, const double* lambda,
             int32_t clamp, double* lambda_plus, double* sqrt_lambda, or_embed_report* rep)
 {
-    int64_t M[3];
     int64_t total = 1;
-    for (int d = 0; d < ndim; ++d) {
-        M[d] = 2 * n[d];
-        total *= M[d];
-    }
+    for (int d = 0; d < ndim; ++d) total *= M[d];
     memset(rep, 0, sizeof *rep);
     double lmin = lambda[0], lmax = lambda[0];
     for (int64_t i = 1; i < total; ++i) {
@@ -485,7 +473,8 @@ void or_psd(int32_t ndim, const int64_t* n, const double* c, const double* lambd
     rep->clamped = rep->n_negative > 0;
     if (rep->clamped) {
         /* realised covariance = inverse DFT of lambda+ / M^d, compared with
-         * the embedded row on survey lags (no axis index equal to n). */
+         * the embedded row on survey lags (|lag| < n on every axis: index
+         * m < n or m > M - n). */
         double* z = (double*)calloc((size_t)total * 2, sizeof(double));
         for (int64_t i = 0; i < total; ++i) z[2 * i] = lambda_plus[i];
         or_fft_nd(z, ndim, M, +1);
@@ -496,7 +485,7 @@ void or_psd(int32_t ndim, const int64_t* n, const double* c, const double* lambd
             for (int d = ndim - 1; d >= 0; --d) {
                 int64_t m = rem % M[d];
                 rem /= M[d];
-                if (m == n[d]) survey = 0;
+                if (m >= n[d] && m <= M[d] - n[d]) survey = 0;
             }
             if (!survey) continue;
             double e = fabs(z[2 * idx] / (double)total - c[idx]);
@@ -513,15 +502,11 @@ void or_psd(int32_t ndim, const int64_t* n, const double* c, const double* lambd
  * W_m = M^{-d/2} sum_k sqrt(lambda_k) eps_k exp(+2 pi i k.m/M), m_i < n_i;
  * Re W and Im W are two independent fields with covariance xi.
  * ==================================================================== */
-void or_sample_given_noise(int32_t ndim, const int64_t* n, const double* s,
+void or_sample_given_noise(int32_t ndim, const int64_t* n, const int64_t* M, const double* s,
                            const double* eps, double* w)
 {
-    int64_t M[3];
     int64_t total = 1;
-    for (int d = 0; d < ndim; ++d) {
-        M[d] = 2 * n[d];
-        total *= M[d];
-    }
+    for (int d = 0; d < ndim; ++d) total *= M[d];
     double* x = (double*)malloc(sizeof(double) * 2 * (size_t)total);
     for (int64_t k = 0; k < total; ++k) {
         x[2 * k] = s[k] * eps[2 * k];
@@ -546,19 +531,19 @@ void or_sample_given_noise(int32_t ndim, const int64_t* n, const double* s,
     free(x);
 }
 
-void or_sample(int32_t ndim, const int64_t* n, const double* s, uint64_t seed, uint64_t r0,
-               int32_t R, int32_t dtype, double* fields)
+void or_sample(int32_t ndim, const int64_t* n, const int64_t* M, const double* s, uint64_t seed,
+               uint64_t r0, int32_t R, int32_t dtype, double* fields)
 {
     int64_t total = 1, ncell = 1;
     for (int d = 0; d < ndim; ++d) {
-        total *= 2 * n[d];
+        total *= M[d];
         ncell *= n[d];
     }
     double* eps = (double*)malloc(sizeof(double) * 2 * (size_t)total);
     double* w = (double*)malloc(sizeof(double) * 2 * (size_t)ncell);
     for (int32_t rr = 0; rr < R; ++rr) {
-        or_draw_noise(seed, r0 + (uint64_t)rr, 1, total, 2 * n[ndim - 1], dtype, eps);
-        or_sample_given_noise(ndim, n, s, eps, w);
+        or_draw_noise(seed, r0 + (uint64_t)rr, 1, total, M[ndim - 1], dtype, eps);
+        or_sample_given_noise(ndim, n, M, s, eps, w);
         double* re = fields + (size_t)rr * 2 * (size_t)ncell;
         double* im = re + ncell;
         for (int64_t i = 0; i < ncell; ++i) {

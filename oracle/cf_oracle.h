@@ -54,23 +54,25 @@ typedef struct {
     int32_t clamped, status; /* status 0 ok, 2 not positive semi-definite */
 } or_embed_report;
 
-/* c: first row of the circulant (M^d doubles). n: survey sizes, M = 2n. */
-void or_embed_row(int32_t ndim, const int64_t* n, const double* cell, int32_t kind,
+/* c: first row of the circulant on the embedded grid M (M_i = 2 n_i for the
+ * paper's box of twice the survey side, or any larger even size), lag of
+ * index m_i: m_i for 2 m_i < M_i, m_i - M_i otherwise. */
+void or_embed_row(int32_t ndim, const int64_t* M, const double* cell, int32_t kind,
                   double amp, double scale, double beta, const double* table, double* c);
 /* lambda = unnormalised forward DFT of c (real part). */
-void or_eigenvalues(int32_t ndim, const int64_t* n, const double* c, double* lambda);
+void or_eigenvalues(int32_t ndim, const int64_t* M, const double* c, double* lambda);
 /* Positivity check, threshold tau = 1e-12 * lambda_max, lambda+ and sqrt(lambda+).
  * clamp != 0 sets negative eigenvalues to zero instead of failing.  When
  * clamped, the realised-covariance error on survey lags is computed. */
-void or_psd(int32_t ndim, const int64_t* n, const double* c, const double* lambda,
+void or_psd(int32_t ndim, const int64_t* n, const int64_t* M, const double* c, const double* lambda,
             int32_t clamp, double* lambda_plus, double* sqrt_lambda, or_embed_report* rep);
 
 /* ---- per-realization Gaussian fields, section 2 ----
  * s: sqrt(lambda+) on M^d.  fields: [R][2][N^d] doubles (Re, Im). */
-void or_sample(int32_t ndim, const int64_t* n, const double* s, uint64_t seed,
+void or_sample(int32_t ndim, const int64_t* n, const int64_t* M, const double* s, uint64_t seed,
                uint64_t r0, int32_t R, int32_t dtype, double* fields);
 /* Same map with the complex noise given explicitly: eps [M^d][2] -> W [N^d][2]. */
-void or_sample_given_noise(int32_t ndim, const int64_t* n, const double* s,
+void or_sample_given_noise(int32_t ndim, const int64_t* n, const int64_t* M, const double* s,
                            const double* eps, double* w);
 
 /* ---- lognormal transform and Poisson sampling, section 3.1 ---- */

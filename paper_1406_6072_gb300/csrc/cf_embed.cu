@@ -485,8 +485,7 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
         CF_CHECK_LAUNCH();
     }
     EmbedStats st{};
-    CF_CUDA(cudaMemcpyAsync(&st, sc.st, sizeof st, cudaMemcpyDeviceToHost, s));
-    CF_CUDA(cudaStreamSynchronize(s));
+    CF_TRY(read_back(&st, sc.st, sizeof st, s));
     cf_embed_report r{};
     r.lambda_min = st.lmin;
     r.lambda_max = st.lmax;

@@ -52,6 +52,13 @@ cf_status ensure_device_init();
 // Stream-ordered allocation from the library's pool on the current device
 // (release with cudaFreeAsync).
 cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+
+// Small results the host waits for (the embedding statistics) are stored by a
+// kernel into pinned, device-mapped host memory: the wait then ends when the
+// kernel does, instead of queueing its read-back behind bulk transfers on a
+// copy engine.  read_back() copies `bytes` (<= 256) from device memory `src`
+// into `dst` on the host, synchronising stream s.
+cf_status read_back(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // Mean over rows and unbiased covariance (1/(nrows-1)) of x [nrows][ncols]; either output may be null.
 cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* mean, double* cov, cudaStream_t s);
 // Entry-point prologue: makes the device of stream s current (the legacy

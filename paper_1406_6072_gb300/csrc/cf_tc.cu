@@ -16,10 +16,12 @@
 // entries act at nearly binary32 accuracy; the data are rounded to 16 bits
 // at every stage, which sets the error of these modes.
 //
-// 2D only: pass 1 draws the noise of one embedded row per line (the same
-// binary32 noise as CF_F32), scales it and transforms the last axis, keeping
-// n1 outputs (16-bit complex intermediate [M0][n1]); pass 2 transforms the
-// columns, keeping n0 outputs, and writes the Re/Im fields in binary32.
+// 2D: pass 1 draws the noise of one embedded row per line (the same binary32
+// noise as CF_F32), scales it and transforms the last axis, keeping n1
+// outputs (16-bit complex intermediate [M0][n1]); pass 2 transforms the
+// columns, keeping n0 outputs, and writes the Re/Im fields in binary32.  3D
+// adds a middle pass: the column kernel per slab along axis 1, writing the
+// next 16-bit intermediate [M0][n1][n2].
 // The inputs are pre-scaled by a power of two alpha chosen from sum(s^2)
 // (computed once per embedding) so the intermediate has unit mean square
 // (range of fp16); the fields are multiplied by 1/alpha at the end.
@@ -427,10 +429,11 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
 // Columns of the intermediate [M0][n1] (L = M0 = RF * LS): transform, keep
 // n0 = L/2, write field 2r (Re) and 2r + 1 (Im) times 1/alpha.  Block:
 // LC = WGS * LPW adjacent columns, loaded by the whole block.
-template <int S, int RF, bool BF16, int WGS>
+template <int S, int RF, bool BF16, int WGS, bool OUT16>
 __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     k_tc_cols(const uint32_t* __restrict__ inter, long long n1, float* __restrict__ fields, long long cells,
-              const double* __restrict__ sumsq, double factor, const C2<float>* __restrict__ tw) {
+              uint32_t* __restrict__ out16, const double* __restrict__ sumsq, double factor,
+              const C2<float>* __restrict__ tw) {
     constexpr int LS = S == 3 ? 4096 : 256;
     constexpr int L = RF * LS;
     constexpr int RPL = LS / 16;
@@ -491,8 +494,11 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
                                  stage[sl * (LS / 2) + p] = make_float2(re, im);
                              });
     __syncthreads();
-    // ... then the block writes rows q < L/2 of its LC adjacent columns
-    float* f0 = fields + (size_t)blockIdx.y * 2 * cells;
+    // ... then the block writes rows q < L/2 of its LC adjacent columns: the
+    // Re/Im fields times 1/alpha, or (OUT16, an inner axis of a 3D grid) the
+    // next 16-bit intermediate [slab][L/2][n1]
+    float* f0 = OUT16 ? nullptr : fields + (size_t)blockIdx.y * 2 * cells;
+    uint32_t* o16 = OUT16 ? out16 + (size_t)blockIdx.y * (L / 2) * n1 : nullptr;
 #pragma unroll 4
     for (int t = threadIdx.x; t < LC * (L / 2); t += Geo<WGS>::kThreads) {
         const int li = t % LC, q = t / LC;
@@ -500,8 +506,12 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
         const float2* st = reinterpret_cast<const float2*>(tc_smem + (li / LPW) * Geo<WGS>::kAStride);
         const float2 v = st[sl * (LS / 2) + p];
         const size_t o = (size_t)q * n1 + cta0 + li;
-        f0[o] = v.x * inv_alpha;
-        f0[o + cells] = v.y * inv_alpha;
+        if constexpr (OUT16) {
+            o16[o] = pack2<BF16>(v.x, v.y);
+        } else {
+            f0[o] = v.x * inv_alpha;
+            f0[o + cells] = v.y * inv_alpha;
+        }
     }
     tc_epilogue<WGS>(tc_smem);
 }
@@ -513,7 +523,7 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
 template <bool BF16, int S, int RF>
 cf_status launch_tc_shape(bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
                           uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
-                          long long cells, const double* sumsq, double factor) {
+                          long long cells, uint32_t* out16, const double* sumsq, double factor) {
     constexpr int WGS = CF_TC_WGS;
     using Gm = Geo<WGS>;
     constexpr int L = RF * (S == 3 ? 4096 : 256);
@@ -524,10 +534,10 @@ cf_status launch_tc_shape(bool rows, dim3 grid, cudaStream_t st, const float* s,
         ScopedKernelTimer kt(st, BF16 ? "tc_rows_bf16" : "tc_rows_f16", L);
         kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(s, amp, key0, key1, r0, nrows, inter, sumsq, factor, tw);
     } else {
-        auto kern = k_tc_cols<S, RF, BF16, WGS>;
+        auto kern = out16 ? k_tc_cols<S, RF, BF16, WGS, true> : k_tc_cols<S, RF, BF16, WGS, false>;
         CF_TRY(prepare_smem(kern, Gm::kSmem));
         ScopedKernelTimer kt(st, BF16 ? "tc_cols_bf16" : "tc_cols_f16", L);
-        kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(inter, n1, fields, cells, sumsq, factor, tw);
+        kern<<<grid, Gm::kThreads, Gm::kSmem, st>>>(inter, n1, fields, cells, out16, sumsq, factor, tw);
     }
     CF_CHECK_LAUNCH();
     return CF_OK;
@@ -536,18 +546,18 @@ cf_status launch_tc_shape(bool rows, dim3 grid, cudaStream_t st, const float* s,
 template <bool BF16>
 cf_status launch_tc(long long L, bool rows, dim3 grid, cudaStream_t st, const float* s, float amp, uint32_t key0,
                     uint32_t key1, uint32_t r0, long long nrows, uint32_t* inter, long long n1, float* fields,
-                    long long cells, const double* sumsq, double factor) {
+                    long long cells, uint32_t* out16, const double* sumsq, double factor) {
     switch (L) {
     case 4096: return launch_tc_shape<BF16, 3, 1>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
-                                                  cells, sumsq, factor);
+                                                  cells, out16, sumsq, factor);
     case 2048: return launch_tc_shape<BF16, 2, 8>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
-                                                  cells, sumsq, factor);
+                                                  cells, out16, sumsq, factor);
     case 1024: return launch_tc_shape<BF16, 2, 4>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
-                                                  cells, sumsq, factor);
+                                                  cells, out16, sumsq, factor);
     case 512: return launch_tc_shape<BF16, 2, 2>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
-                                                 cells, sumsq, factor);
+                                                 cells, out16, sumsq, factor);
     case 256: return launch_tc_shape<BF16, 2, 1>(rows, grid, st, s, amp, key0, key1, r0, nrows, inter, n1, fields,
-                                                 cells, sumsq, factor);
+                                                 cells, out16, sumsq, factor);
     default: return fail(CF_ERR_UNSUPPORTED, "tensor-core line length %lld", L);
     }
 }
@@ -561,14 +571,18 @@ bool tc_length_ok(long long L) { return L == 256 || L == 512 || L == 1024 || L =
 static long long tc_lines_per_block(long long L) { return kCtaRows / (L / 16); }
 
 cf_status tc_check_grid(const GridInfo& g) {
-    if (g.ndim != 2 || !tc_length_ok(g.m[0]) || !tc_length_ok(g.m[1]))
+    bool ok = g.ndim == 2 || g.ndim == 3;
+    for (int a = 0; ok && a < g.ndim; ++a) ok = tc_length_ok(g.m[a]);
+    if (!ok)
         return fail(CF_ERR_UNSUPPORTED,
-                    "tensor-core modes need a 2D grid with embedded sides 256..4096 (got %dD, %lld x %lld)",
-                    g.ndim, g.m[0], g.ndim > 1 ? g.m[1] : 0);
+                    "tensor-core modes need a 2D or 3D grid with embedded sides 256, 512, 1024, 2048 or 4096");
     return CF_OK;
 }
 
-size_t tc_bytes_per_realization(const GridInfo& g) { return 4 * (size_t)g.m[0] * (size_t)g.n[1]; }
+size_t tc_bytes_per_realization(const GridInfo& g) {
+    if (g.ndim == 2) return 4 * (size_t)g.m[0] * (size_t)g.n[1];
+    return 4 * ((size_t)g.m[0] * g.m[1] * g.n[2] + (size_t)g.m[0] * g.n[1] * g.n[2]);
+}
 size_t tc_header_bytes() { return 0; }
 
 // Fields [R][2][n0][n1] (binary32) of realizations r0.. through the tensor
@@ -579,25 +593,40 @@ cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0
     CF_TRY(tc_check_grid(g));
     CF_TRY(ensure_sumsq(const_cast<cf_embedding*>(e), st));
     const double* sumsq = e->sumsq;
-    const double factor = 2.0 * (double)g.m[1] * amp_scale * amp_scale / (double)g.mtotal;
+    const int d = g.ndim;
+    const double factor = 2.0 * (double)g.m[d - 1] * amp_scale * amp_scale / (double)g.mtotal;
+    if (d == 3 && (long long)chunk * g.m[0] > 65535) chunk = (int)(65535 / g.m[0]);
     uint32_t* inter = (uint32_t*)ws;
     const long long cells = g.ncell;
+    auto launch = [&](long long L, bool rows, dim3 grid, uint32_t rr, long long nrows, uint32_t* in, long long ncols,
+                      float* f, uint32_t* out16) -> cf_status {
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+        return bf16 ? launch_tc<true>(L, rows, grid, st, e->s32, (float)amp_scale, k0, k1, rr, nrows, in, ncols, f,
+                                      cells, out16, sumsq, factor)
+                    : launch_tc<false>(L, rows, grid, st, e->s32, (float)amp_scale, k0, k1, rr, nrows, in, ncols, f,
+                                       cells, out16, sumsq, factor);
+    };
     for (int c0 = 0; c0 < R; c0 += chunk) {
         const int nr = (R - c0) < chunk ? (R - c0) : chunk;
-        const dim3 g1((unsigned)(g.m[0] / tc_lines_per_block(g.m[1])), (unsigned)nr);
-        const dim3 g2((unsigned)(g.n[1] / tc_lines_per_block(g.m[0])), (unsigned)nr);
         const uint32_t rr = (uint32_t)(r0 + (uint64_t)c0);
         float* f = fields + (size_t)c0 * 2 * (size_t)cells;
-        if (bf16) {
-            CF_TRY(launch_tc<true>(g.m[1], true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                   rr, g.m[0], inter, g.n[1], nullptr, cells, sumsq, factor));
-            CF_TRY(launch_tc<true>(g.m[0], false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
-                                   factor));
+        if (d == 2) {
+            // rows (noise, axis 1) -> [M0][n1]; columns (axis 0) -> fields
+            const dim3 g1((unsigned)(g.m[0] / tc_lines_per_block(g.m[1])), (unsigned)nr);
+            const dim3 g2((unsigned)(g.n[1] / tc_lines_per_block(g.m[0])), (unsigned)nr);
+            CF_TRY(launch(g.m[1], true, g1, rr, g.m[0], inter, g.n[1], nullptr, nullptr));
+            CF_TRY(launch(g.m[0], false, g2, 0, 0, inter, g.n[1], f, nullptr));
         } else {
-            CF_TRY(launch_tc<false>(g.m[1], true, g1, st, e->s32, (float)amp_scale, (uint32_t)seed,
-                                    (uint32_t)(seed >> 32), rr, g.m[0], inter, g.n[1], nullptr, cells, sumsq, factor));
-            CF_TRY(launch_tc<false>(g.m[0], false, g2, st, nullptr, 0.f, 0, 0, 0, 0, inter, g.n[1], f, cells, sumsq,
-                                    factor));
+            // rows (noise, axis 2) -> [M0 M1][n2]; axis 1 per slab -> [M0][n1][n2];
+            // axis 0 -> fields
+            uint32_t* inter2 = inter + (size_t)nr * g.m[0] * g.m[1] * g.n[2];
+            const long long rows = g.m[0] * g.m[1];
+            const dim3 g1((unsigned)(rows / tc_lines_per_block(g.m[2])), (unsigned)nr);
+            const dim3 g2((unsigned)(g.n[2] / tc_lines_per_block(g.m[1])), (unsigned)(nr * g.m[0]));
+            const dim3 g3((unsigned)(g.n[1] * g.n[2] / tc_lines_per_block(g.m[0])), (unsigned)nr);
+            CF_TRY(launch(g.m[2], true, g1, rr, rows, inter, g.n[2], nullptr, nullptr));
+            CF_TRY(launch(g.m[1], false, g2, 0, 0, inter, g.n[2], nullptr, inter2));
+            CF_TRY(launch(g.m[0], false, g3, 0, 0, inter2, g.n[1] * g.n[2], f, nullptr));
         }
     }
     return CF_OK;

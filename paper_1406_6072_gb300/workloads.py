@@ -82,6 +82,10 @@ CONFIGS = {
         nbins=64,
         text="2D 2048^2 survey in 4096^2, xi = 0.8/(1+(r/16)^2)^0.4 (clamped), 32 realizations, "
              "precision sweep, seed 4"),
+    "exp3d_n256_sweep": Workload(
+        "exp3d_n256_sweep", (256, 256, 256), XI_EXPONENTIAL, 1.0, 8.0, 0.0, "f32", 4, 8, False,
+        nbins=64,
+        text="3D 256^3 survey in 512^3, xi = exp(-r/8), 4 realizations, precision sweep, seed 8"),
 }
 
 

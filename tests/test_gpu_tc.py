@@ -3,9 +3,9 @@
 These modes round the data to 16 bits before every DFT-matrix stage, so they
 are not bit-for-bit comparable with the oracle: the error against the oracle's
 binary64 fields (same binary32 noise) is bounded by the rounding analysis
-instead.  With unit roundoff u (bf16 2^-8, fp16 2^-11) and 2S roundings of
-the data (S radix-16 stages per axis), each contributing at most u relative
-(about u/sqrt(3) RMS), the relative L2 error stays below u*sqrt(2S).  The
+instead.  With unit roundoff u (bf16 2^-8, fp16 2^-11) and dS roundings of
+the data (S radix-16 stages per axis, d axes), each contributing at most u
+relative (about u/sqrt(3) RMS), the relative L2 error stays below u*sqrt(dS).  The
 error must also exceed u/64: a smaller one would mean the 16-bit stages did
 not run.  Every run also checks that no tensor-core wait ran out of time.
 """
@@ -34,10 +34,11 @@ def _tc_fields(emb, seed, r0, R, dt, n, ws_bytes=None):
     return out
 
 
-def _stages(n):
+def _roundings(n):
     # rounding stages per axis: 2 radix-16 stages for 256 points, 3 for 4096,
-    # and a binary32 first radix (2, 4 or 8) before 2 radix-16 stages otherwise
-    return max(2 if 2 * v == 256 else 3 for v in n)
+    # and a binary32 first radix (2, 4 or 8) before 2 radix-16 stages
+    # otherwise; every axis counts with the largest
+    return len(n) * max(2 if 2 * v == 256 else 3 for v in n)
 
 
 CASES = [((128, 128), cf.CF_XI_GAUSSIAN, 4.0, 0.0, False),
@@ -45,7 +46,10 @@ CASES = [((128, 128), cf.CF_XI_GAUSSIAN, 4.0, 0.0, False),
          ((2048, 128), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True),
          ((256, 512), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True),    # first radix 2 and 4
          ((1024, 128), cf.CF_XI_EXPONENTIAL, 5.0, 0.0, False),  # first radix 8
-         ((512, 512), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True)]     # the 2D 512^2 workload's grid
+         ((512, 512), cf.CF_XI_GEN_CAUCHY, 8.0, 0.4, True),     # the 2D 512^2 workload's grid
+         ((128, 128, 128), cf.CF_XI_EXPONENTIAL, 4.0, 0.0, True),  # 3D: three passes
+         ((256, 128, 128), cf.CF_XI_GEN_CAUCHY, 6.0, 0.4, True),   # 3D, first radix 2 on axis 0
+         ((128, 128, 512), cf.CF_XI_GAUSSIAN, 5.0, 0.0, True)]     # 3D, first radix 4 on the rows
 
 
 @pytest.mark.parametrize("dt", [cf.CF_BF16_TC, cf.CF_F16_TC])
@@ -58,11 +62,11 @@ def test_tc_fields_within_rounding_bound(orc, n, kind, scale, beta, clamp, dt):
     ref = orc.sample(n, o["sqrt_lambda"], seed, r0, R, 1)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     u = U[dt]
-    assert u / 64 < err <= u * np.sqrt(2 * _stages(n)), err
+    assert u / 64 < err <= u * np.sqrt(_roundings(n)), err
     # each realization separately (no cross-talk between lines, blocks or chunks)
     for r in range(R):
         e = np.linalg.norm(got[r] - ref[r]) / np.linalg.norm(ref[r])
-        assert e <= u * np.sqrt(2 * _stages(n)), (r, e)
+        assert e <= u * np.sqrt(_roundings(n)), (r, e)
     emb.close()
 
 
@@ -108,8 +112,8 @@ def test_precision_sweep_errors(orc):
     emb.close()
 
 
-def test_tc_deterministic_and_chunk_independent():
-    n = (128, 128)
+@pytest.mark.parametrize("n", [(128, 128), (128, 128, 128)])
+def test_tc_deterministic_and_chunk_independent(n):
     emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))
     for dt in (cf.CF_BF16_TC, cf.CF_F16_TC):
         a = _tc_fields(emb, 9, 10, 5, dt, n)
@@ -124,11 +128,12 @@ def test_tc_deterministic_and_chunk_independent():
 
 
 def test_tc_unsupported_and_errors():
-    emb = cf.cf_embed(cf.make_grid((64, 64)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))  # sides 128: too short
-    with pytest.raises(cf.CfError) as ei:
-        cf.cf_sample_workspace_size(emb, 1, cf.CF_BF16_TC)
-    assert ei.value.status == cf.CF_ERR_UNSUPPORTED
-    emb.close()
+    for n in ((64, 64), (128, 64, 128), (256,)):  # sides 128: too short; 1D
+        emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))
+        with pytest.raises(cf.CfError) as ei:
+            cf.cf_sample_workspace_size(emb, 1, cf.CF_BF16_TC)
+        assert ei.value.status == cf.CF_ERR_UNSUPPORTED
+        emb.close()
     emb = cf.cf_embed(cf.make_grid((128, 128)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))
     out = torch.empty((1, 2, 128, 128), dtype=torch.float32, device=DEV)
     ws = torch.empty(64, dtype=torch.uint8, device=DEV)
