@@ -529,6 +529,57 @@ def cufft_reference(wl, R, stream, steps=10):
                     % (R, "x".join(map(str, m)), "x".join(map(str, n)))}
 
 
+# --------------------------------------------------------------------- padding
+def run_padding(args):
+    """The 2D 512^2 workload's non-PSD generalised Cauchy spectrum embedded on
+    2, 4 and 8 times the survey side: the clamping report (negative mass,
+    realised-covariance error) against the cost of a whole step (embedding,
+    sampler with lognormal + Poisson, both power spectra)."""
+    import dataclasses
+
+    import torch
+
+    from paper_1406_6072_gb300 import cf
+    from paper_1406_6072_gb300 import workloads as W
+    from paper_1406_6072_gb300.pipeline import FieldPipeline
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    base = W.CONFIGS["cauchy2d_n512_padding"]
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for p in (2, 4, 8):
+        wl = dataclasses.replace(base, factor=p)
+        with torch.cuda.stream(stream):
+            pipe = FieldPipeline(wl, dev, stream=stream)
+            rep = pipe.embed()
+            steps = max(3, min(args.steps, 30))
+            for k in range(max(3, args.warmup)):
+                pipe.step(r0=k * wl.R)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(steps):
+                pipe.step(r0=(100 + k) * wl.R)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            pipe.close()
+        out[f"factor_{p}"] = {"embedded_side": p * wl.n[0], "ms_per_step": ms,
+                              "cells_per_s": pipe.cells_per_step / (ms * 1e-3),
+                              "cov_error": rep["cov_error"], "neg_mass": rep["neg_mass"],
+                              "lambda_min_over_max": rep["lambda_min"] / rep["lambda_max"],
+                              "n_negative": rep["n_negative"]}
+        del pipe
+    clk = clocks.stop()
+    line = {"metric": "clamping error and cells/s per embedding factor, 2D 512^2 step", "unit": UNIT,
+            "value": out["factor_2"]["cells_per_s"], "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": base.name, "text": base.text, "realizations_per_step": base.R},
+            "factors": out, "clocks": clk}
+    print(json.dumps(line))
+
+
 # --------------------------------------------------------------------- graph
 def run_graph(args):
     """The workload's per-realization path (sampler with lognormal + Poisson,
@@ -789,6 +840,8 @@ def main():
         return run_serving(args)
     if args.workload.endswith("_sweep"):
         return run_sweep(args)
+    if args.workload == "cauchy2d_n512_padding":
+        return run_padding(args)
     if args.graph:
         return run_graph(args)
     if args.workload == "mock_n128":

@@ -77,10 +77,21 @@ typedef enum {
 
 /* Survey grid (section 2, eq. (grid)): ndim in {1,2,3}; n[i] survey cells on
  * axis i (unused axes ignored); cell[i] the physical cell side (the L/N of
- * the paper), used for the lag r of xi and the volume of the power spectrum. */
+ * the paper), used for the lag r of xi and the volume of the power spectrum.
+ * embed_factor p: the periodic embedding grid has M_i points per axis, the
+ * smallest power of two >= p n_i (p = 0 or 2: the paper's box of twice the
+ * survey side, exactly 2 n_i when n_i is a power of two; 4 or 8: a larger box,
+ * in which every survey-sized sub-box still has the target covariance
+ * (section 2, Fig. 1) and whose spectrum is non-negative for more two-point
+ * functions, at about (p/2)^d times the work and memory).  Any n_i >= 1 is
+ * accepted (M_i <= 4096); the lag of embedded index m_i is m_i for
+ * 2 m_i < M_i and m_i - M_i otherwise, and the fields are the first n_i points
+ * per axis.  Calls that take fields only (lognormal / Poisson, counts in
+ * cells) ignore p; the power spectrum needs power-of-two n_i; the tensor-core
+ * modes and cf_embed_periodic need M_i = 2 n_i. */
 typedef struct {
     int32_t ndim;
-    int32_t pad_;
+    int32_t embed_factor;
     int64_t n[3];
     double cell[3];
 } cf_grid;

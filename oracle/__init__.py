@@ -162,16 +162,17 @@ def fft_nd(x, sign):
 
 
 # ---------------------------------------------------------------- embedding
-def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, log1p=False, factor=2):
+def embed_row(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, log1p=False, factor=2, M=None):
     """First row c of the circulant (step a1, section 2 eq. (grid)) on the
     embedded grid of `factor` times the survey side per axis (2: the paper's
     box of twice the side; a larger box embeds the same way, section 2, Fig. 1:
     any survey-sized sub-box of it has the target covariance).  log1p: xi is
     the correlation function of the lognormal density and the Gaussian
-    covariance is ln(1 + xi) (section 3.1, eq. (Lncov))."""
+    covariance is ln(1 + xi) (section 3.1, eq. (Lncov)).  M: explicit
+    embedded sides (any M_i >= 2 n_i), instead of factor * n."""
     d = len(n)
     cellv = np.ones(3) if cell is None else np.asarray(list(cell) + [1.0] * (3 - len(cell)))
-    M = [int(factor) * int(v) for v in n]
+    M = [int(factor) * int(v) for v in n] if M is None else [int(v) for v in M]
     mdims, _ = _dims(M)
     c = np.zeros(int(np.prod(M)), dtype=np.float64)
     tab = None if table is None else np.ascontiguousarray(table, dtype=np.float64).ravel()
@@ -211,9 +212,10 @@ def psd(n, c, lam, clamp=False):
     return lp, s, rep.asdict()
 
 
-def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False, log1p=False, factor=2):
+def embed(n, kind, amp=1.0, scale=1.0, beta=0.0, cell=None, table=None, clamp=False, log1p=False, factor=2,
+          M=None):
     """Steps a1-a3: first row c, eigenvalues lambda, lambda+, sqrt(lambda+), report."""
-    c = embed_row(n, kind, amp, scale, beta, cell, table, log1p, factor)
+    c = embed_row(n, kind, amp, scale, beta, cell, table, log1p, factor, M)
     lam = eigenvalues(n, c)
     lp, s, rep = psd(n, c, lam, clamp)
     return {"c": c, "lambda": lam, "lambda_plus": lp, "sqrt_lambda": s, "report": rep}

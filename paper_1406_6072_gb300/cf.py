@@ -43,7 +43,7 @@ class CfError(RuntimeError):
 
 # ----------------------------------------------------------------- structs
 class cf_grid(C.Structure):
-    _fields_ = [("ndim", C.c_int32), ("pad_", C.c_int32), ("n", C.c_int64 * 3), ("cell", C.c_double * 3)]
+    _fields_ = [("ndim", C.c_int32), ("embed_factor", C.c_int32), ("n", C.c_int64 * 3), ("cell", C.c_double * 3)]
 
 
 class cf_xi(C.Structure):
@@ -194,10 +194,13 @@ def _stream(s):
     return s.cuda_stream
 
 
-def make_grid(n, cell=None):
+def make_grid(n, cell=None, factor=2):
+    """Survey grid of n cells per axis; the embedding grid has factor * n
+    points per axis (2, 4 or 8)."""
     g = cf_grid()
     n = list(n)
     g.ndim = len(n)
+    g.embed_factor = int(factor)
     for a in range(3):
         g.n[a] = int(n[a]) if a < len(n) else 1
         g.cell[a] = float(cell[a]) if cell is not None and a < len(cell) else 1.0
@@ -443,9 +446,9 @@ def make_serve_cfg(device=0, max_inflight=4, queue_capacity=100000, cache_entrie
 
 
 def make_request(n, kind, amp, scale, beta=0.0, seed=0, r0=0, R=1, embed_flags=CF_EMBED_CLAMP, want_counts=False,
-                 sigma2=0.0, nbar=0.0, lp_seed=0, host_fields=None, host_counts=None, cell=None):
+                 sigma2=0.0, nbar=0.0, lp_seed=0, host_fields=None, host_counts=None, cell=None, factor=2):
     r = cf_request()
-    r.grid = make_grid(n, cell)
+    r.grid = make_grid(n, cell, factor)
     r.xi = make_xi(kind, amp, scale, beta)
     r.embed_flags, r.want_counts = embed_flags, int(bool(want_counts))
     r.seed, r.r0, r.R = seed, r0, R

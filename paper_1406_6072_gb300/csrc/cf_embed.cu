@@ -8,13 +8,14 @@
 namespace cf {
 
 // a1: first row of the circulant, c(m) = xi(|lag(m)|), lag(m_i) = m_i for
-// m_i < n_i and m_i - M_i otherwise (the grid of eq. (grid) runs -n..n-1).
-// xi depends on |lag_i| only, so one thread evaluates xi once per point of
-// [0, n_0] x ... and writes it to the 2^d mirror positions m_i = l_i and
-// M_i - l_i (one position when l_i is 0 or n_i).
+// 2 m_i < M_i and m_i - M_i otherwise (for M = 2n the grid of eq. (grid) runs
+// -n..n-1).  xi depends on |lag_i| only, so one thread evaluates xi once per
+// point of [0, M_0/2] x ... and writes it to the 2^d mirror positions m_i = l_i
+// and M_i - l_i (one position when l_i is 0 or M_i/2).
 __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, double beta, int log1p_xi,
                            double* __restrict__ c, C2<double>* __restrict__ z) {
-    const long long q0 = g.n[0] + 1, q1 = g.ndim > 1 ? g.n[1] + 1 : 1, q2 = g.ndim > 2 ? g.n[2] + 1 : 1;
+    const long long h0 = g.m[0] / 2, h1 = g.m[1] / 2, h2 = g.m[2] / 2;
+    const long long q0 = h0 + 1, q1 = g.ndim > 1 ? h1 + 1 : 1, q2 = g.ndim > 2 ? h2 + 1 : 1;
     const long long total = q0 * q1 * q2;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
@@ -35,9 +36,9 @@ __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, doubl
         if (log1p_xi) v = log1p(v);  // eq. (Lncov): Gaussian covariance from the density correlation
         // mirror positions
         const int na = g.ndim;
-        const int nm0 = (l0 == 0 || l0 == g.n[0]) ? 1 : 2;
-        const int nm1 = (na < 2 || l1 == 0 || l1 == g.n[1]) ? 1 : 2;
-        const int nm2 = (na < 3 || l2 == 0 || l2 == g.n[2]) ? 1 : 2;
+        const int nm0 = (l0 == 0 || l0 == h0) ? 1 : 2;
+        const int nm1 = (na < 2 || l1 == 0 || l1 == h1) ? 1 : 2;
+        const int nm2 = (na < 3 || l2 == 0 || l2 == h2) ? 1 : 2;
         for (int a0 = 0; a0 < nm0; ++a0) {
             const long long m0 = a0 ? g.m[0] - l0 : l0;
             for (int a1 = 0; a1 < nm1; ++a1) {
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(kRedThreads)
     }
 }
 
-// realised covariance error max |Re z/M^d - c| over survey lags (no index == n)
+// realised covariance error max |Re z/M^d - c| over survey lags (|lag_i| < n_i:
+// index m_i < n_i or m_i > M_i - n_i on every axis)
 __global__ void __launch_bounds__(kRedThreads)
     k_cov_error_partial(const C2<double>* __restrict__ z, const double* __restrict__ c, GridInfo g,
                         double inv_total, double* __restrict__ part) {
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kRedThreads)
         for (int a = g.ndim - 1; a >= 0; --a) {
             const long long m = rem % g.m[a];
             rem /= g.m[a];
-            if (m == g.n[a]) survey = false;
+            if (m >= g.n[a] && m <= g.m[a] - g.n[a]) survey = false;
         }
         if (survey) mx = fmax(mx, fabs(z[idx].x * inv_total - c[idx]));
     }
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kRedThreads)
         for (int a = g.ndim - 1; a >= 0; --a) {
             const long long m = rem % g.m[a];
             rem /= g.m[a];
-            if (m == g.n[a]) survey = false;
+            if (m >= g.n[a] && m <= g.m[a] - g.n[a]) survey = false;
         }
         if (survey) mx = fmax(mx, fabs(z[idx] - c[idx]));
     }
@@ -631,6 +633,9 @@ extern "C" cf_status cf_embed_periodic(const cf_grid* g, const cf_xi* xi, int32_
         return fail(CF_ERR_ARG, "resolution must be 1, 2, 4, 8 or 16");
     GridInfo gs;
     CF_TRY(check_grid(g, &gs));
+    for (int a = 0; a < gs.ndim; ++a)
+        if (gs.m[a] != 2 * gs.n[a])
+            return fail(CF_ERR_UNSUPPORTED, "the periodic box needs power-of-two n and embed_factor 0 or 2");
     const int log1p_xi = (flags & CF_EMBED_LOG1P) ? 1 : 0;
     if (log1p_xi && !(xi->amp > -1.0)) return fail(CF_ERR_ARG, "CF_EMBED_LOG1P needs amp > -1");
     // embedding grid of the sampler and the fine, large grid of the spectrum

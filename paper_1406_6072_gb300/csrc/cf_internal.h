@@ -94,6 +94,7 @@ class ScopedKernelTimer {
 // Validates a survey grid for the sampler; fills M and totals.
 struct GridInfo {
     int ndim;
+    int factor;        // embedded side / survey side (M = factor * n per axis)
     long long n[3];
     long long m[3];
     double cell[3];

@@ -87,9 +87,11 @@ struct FieldEpi {
 
 // --------------------------------------------------------------------------
 // Column pass: FFT along the middle axis of in[outer][L][inner] for a tile of
-// C consecutive inner indices per CTA.  mode 0: complex output
-// out[outer][KEEP][inner] (in place allowed when KEEP == L); mode 1: field
-// epilogue with realization = outer index and cell = point*inner + i.
+// C consecutive inner indices per CTA.  Outputs with point index < keep
+// (keep <= KEEP, which is L/2 or L at compile time) are produced.  mode 0:
+// complex output out[outer][keep][inner] (in place allowed when keep == L);
+// mode 1: field epilogue with realization = outer index and cell =
+// point*inner + i.
 // --------------------------------------------------------------------------
 // Build-time tunables of the CTA shapes, per kernel family: binary32 points
 // per thread (E), threads per CTA, and the minimum number of resident CTAs per
@@ -139,7 +141,7 @@ struct ColsCfg : TileCfg<T, L, CF_COLS_E, CF_COLS_THREADS, CF_COLS_MINB> {
 
 template <typename T, int L, int SIGN, int KEEP_HALF>
 __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
-    k_cols(const C2<T>* in, long long inner, C2<T>* out, int mode, FieldEpi<T> epi,
+    k_cols(const C2<T>* in, long long inner, int keep, C2<T>* out, int mode, FieldEpi<T> epi,
            const C2<T>* __restrict__ tw) {
     using Cfg = ColsCfg<T, L>;
     using G = typename Cfg::G;
@@ -156,9 +158,9 @@ __global__ void __launch_bounds__(ColsCfg<T, L>::THREADS, ColsCfg<T, L>::MINB)
 #pragma unroll
     for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)inner];
     auto sink = [&](int, int p, C2<T> val) {
-        if (!valid) return;
+        if (!valid || p >= keep) return;
         if (mode == 0)
-            out[((size_t)o * KEEP + p) * (size_t)inner + i] = val;
+            out[((size_t)o * keep + p) * (size_t)inner + i] = val;
         else
             epi((int)o, (long long)p * inner + i, val);
     };
@@ -233,11 +235,15 @@ inline const C2<float>* twiddles<float>() { return twiddles_f32(); }
 template <>
 inline const C2<double>* twiddles<double>() { return twiddles_f64(); }
 
-// Column pass launch over in[outer][L][inner].
+// Column pass launch over in[outer][L][inner]; keep = 0 keeps L/2 outputs
+// (KEEP_HALF) or L.
 template <typename T, int SIGN, int KEEP_HALF>
 inline cf_status launch_cols(long long L, const C2<T>* in, long long outer, long long inner, C2<T>* out,
-                             int mode, const FieldEpi<T>& epi, cudaStream_t s) {
+                             int mode, const FieldEpi<T>& epi, cudaStream_t s, long long keep = 0) {
     if (outer > 65535) return fail(CF_ERR_UNSUPPORTED, "column pass with %lld outer slices", outer);
+    const long long full = KEEP_HALF ? L / 2 : L;
+    if (keep == 0) keep = full;
+    if (keep < 1 || keep > full) return fail(CF_ERR_ARG, "column pass keeps %lld of %lld outputs", keep, L);
     return dispatch_line(L, [&](auto Lc) -> cf_status {
         constexpr int LL = decltype(Lc)::value;
         using Cfg = ColsCfg<T, LL>;
@@ -249,7 +255,7 @@ inline cf_status launch_cols(long long L, const C2<T>* in, long long outer, long
         char full[64];
         snprintf(full, sizeof full, "%s_%s", name, sizeof(T) == 4 ? "f32" : "f64");
         ScopedKernelTimer kt(s, full, LL);
-        kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(in, inner, out, mode, epi, twiddles<T>());
+        kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(in, inner, (int)keep, out, mode, epi, twiddles<T>());
         CF_CHECK_LAUNCH();
         return CF_OK;
     });

@@ -171,17 +171,21 @@ const C2<double>* twiddles_f64() { return g_tw64_ptr[current_device()]; }
 cf_status check_grid(const cf_grid* g, GridInfo* gi) {
     if (!g) return fail(CF_ERR_ARG, "grid is NULL");
     if (g->ndim < 1 || g->ndim > 3) return fail(CF_ERR_ARG, "ndim must be 1, 2 or 3 (got %d)", g->ndim);
+    const int p = g->embed_factor == 0 ? 2 : g->embed_factor;
+    if (p != 2 && p != 4 && p != 8) return fail(CF_ERR_ARG, "embed_factor must be 0, 2, 4 or 8 (got %d)", p);
     gi->ndim = g->ndim;
+    gi->factor = p;
     gi->ncell = 1;
     gi->mtotal = 1;
     for (int a = 0; a < 3; ++a) {
         if (a < g->ndim) {
             const long long n = (long long)g->n[a];
             if (n < 1) return fail(CF_ERR_ARG, "n[%d] = %lld must be >= 1", a, n);
-            const long long m = 2 * n;
-            if (!is_pow2(m) || m > kMaxLine)
-                return fail(CF_ERR_UNSUPPORTED, "embedding size 2*n[%d] = %lld must be a power of two <= %lld",
-                            a, m, kMaxLine);
+            long long m = 1;  // the smallest power of two >= p n
+            while (m < p * n && m <= kMaxLine) m <<= 1;
+            if (m > kMaxLine)
+                return fail(CF_ERR_UNSUPPORTED, "embedding size for n[%d] = %lld at factor %d exceeds %lld", a, n,
+                            p, kMaxLine);
             const double c = g->cell[a];
             if (!(c > 0.0)) return fail(CF_ERR_ARG, "cell[%d] must be > 0", a);
             gi->n[a] = n;
@@ -367,7 +371,7 @@ extern "C" cf_status cf_embedding_info(const cf_embedding* e, cf_grid* g, cf_emb
     if (!e) return fail(CF_ERR_ARG, "NULL embedding");
     if (g) {
         g->ndim = e->grid.ndim;
-        g->pad_ = 0;
+        g->embed_factor = e->grid.factor;
         for (int a = 0; a < 3; ++a) {
             g->n[a] = e->grid.n[a];
             g->cell[a] = e->grid.cell[a];

@@ -30,14 +30,15 @@ struct SRowsCfg : TileCfg<T, L, CF_SROWS_E, CF_SROWS_THREADS, CF_SROWS_MINB> {
 // --------------------------------------------------------------------------
 // Pass 1: rows along the last axis.  Each thread draws the noise of its E
 // first-stage points (Philox stream 0), scales it by sqrt(lambda+)/sqrt(M^d),
-// runs the inverse line transform, and keeps the first L/2 outputs (the
-// survey half).  Output: complex intermediate [chunk][nrows][L/2], or for a
-// one-dimensional grid the fields (and counts) directly.
+// runs the inverse line transform, and keeps the first `keep` outputs (the
+// survey's n <= L/2 points).  Output: complex intermediate
+// [chunk][nrows][keep], or for a one-dimensional grid the fields (and counts)
+// directly.
 // --------------------------------------------------------------------------
 template <typename T, int L>
 __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     k_sample_rows(const T* __restrict__ s, T amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
-                  long long nrows, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
+                  long long nrows, int keep, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
                   const C2<T>* __restrict__ tw, const RealDesc* __restrict__ desc) {
     using Cfg = SRowsCfg<T, L>;
     using G = typename Cfg::G;
@@ -85,17 +86,17 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
         }
     }
     auto sink = [&](int, int p, C2<T> val) {
-        if (!valid) return;
+        if (!valid || p >= keep) return;
         if (mode == 0)
-            out[((size_t)rl * nrows + row) * (L / 2) + p] = val;
+            out[((size_t)rl * nrows + row) * keep + p] = val;
         else
-            epi(rl, (long long)row * (L / 2) + p, val);
+            epi(rl, (long long)row * keep + p, val);
     };
     line_fft<T, L, +1, L / 2>(sm, RowLayout<E, G::PADDED>(), line, j, v, tw, sink);
 }
 
 template <typename T>
-static cf_status launch_sample_rows(long long L, const T* s, T amp_scale, uint64_t seed, uint32_t r0,
+static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_scale, uint64_t seed, uint32_t r0,
                                     int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
                                     cudaStream_t st, const RealDesc* desc = nullptr) {
     return dispatch_line(L, [&](auto Lc) -> cf_status {
@@ -106,7 +107,7 @@ static cf_status launch_sample_rows(long long L, const T* s, T amp_scale, uint64
         dim3 grid((unsigned)((nrows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)chunk);
         ScopedKernelTimer kt(st, sizeof(T) == 4 ? "sample_rows_f32" : "sample_rows_f64", LL);
         kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
-                                                     nrows, out, mode, epi, twiddles<T>(), desc);
+                                                     nrows, keep, out, mode, epi, twiddles<T>(), desc);
         CF_CHECK_LAUNCH();
         return CF_OK;
     });
@@ -206,17 +207,17 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
         const long long Ml = g.m[d - 1];
         const long long nrows = g.mtotal / Ml;
         if (d == 1) {
-            CF_TRY(launch_sample_rows<T>(Ml, s, (T)amp_scale, seed, rr0, nr, nrows, nullptr, 1, epi, st));
+            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, nullptr, 1, epi, st));
         } else if (d == 2) {
-            CF_TRY(launch_sample_rows<T>(Ml, s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
+            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
             // pass 2: columns of [chunk][M0][N1], keep N0, fields epilogue
-            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st)));
+            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0])));
         } else {
-            CF_TRY(launch_sample_rows<T>(Ml, s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
+            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
             // pass 2: axis 1 of [chunk*M0][M1][N2] -> [chunk*M0][N1][N2]
-            CF_TRY((launch_cols<T, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st)));
+            CF_TRY((launch_cols<T, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1])));
             // pass 3: axis 0 of [chunk][M0][N1*N2] -> fields
-            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st)));
+            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0])));
         }
     }
     record_use(const_cast<cf_embedding*>(e), st);
@@ -283,14 +284,14 @@ cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, v
         epi.cells = cells;
         epi.desc = desc + c0;
         if (d == 1) {
-            CF_TRY(launch_sample_rows<float>(Ml, nullptr, 1.0f, 0, 0, nr, nrows, nullptr, 1, epi, st, desc + c0));
+            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, nullptr, 1, epi, st, desc + c0));
         } else if (d == 2) {
-            CF_TRY(launch_sample_rows<float>(Ml, nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
-            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st)));
+            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
+            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0])));
         } else {
-            CF_TRY(launch_sample_rows<float>(Ml, nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
-            CF_TRY((launch_cols<float, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st)));
-            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st)));
+            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
+            CF_TRY((launch_cols<float, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1])));
+            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0])));
         }
     }
     return CF_OK;

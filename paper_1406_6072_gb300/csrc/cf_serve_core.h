@@ -82,9 +82,9 @@ inline double now_s() {
 // Shape key: requests with equal keys can share one launch.
 inline std::string shape_key(const cf_request& r) {
     char b[160];
-    snprintf(b, sizeof b, "%d:%lld:%lld:%lld:%d", r.grid.ndim, (long long)r.grid.n[0],
+    snprintf(b, sizeof b, "%d:%lld:%lld:%lld:%d:%d", r.grid.ndim, (long long)r.grid.n[0],
              (long long)(r.grid.ndim > 1 ? r.grid.n[1] : 1), (long long)(r.grid.ndim > 2 ? r.grid.n[2] : 1),
-             r.want_counts ? 1 : 0);
+             r.grid.embed_factor == 0 ? 2 : r.grid.embed_factor, r.want_counts ? 1 : 0);
     return b;
 }
 
@@ -92,8 +92,9 @@ inline std::string shape_key(const cf_request& r) {
 inline std::string spectrum_key(const cf_request& r) {
     char b[320];
     const int d = r.grid.ndim;
-    snprintf(b, sizeof b, "%d:%lld:%lld:%lld:%.17g:%.17g:%.17g:%d:%.17g:%.17g:%u", d, (long long)r.grid.n[0],
-             (long long)(d > 1 ? r.grid.n[1] : 1), (long long)(d > 2 ? r.grid.n[2] : 1), r.grid.cell[0],
+    snprintf(b, sizeof b, "%d:%lld:%lld:%lld:%d:%.17g:%.17g:%.17g:%d:%.17g:%.17g:%u", d, (long long)r.grid.n[0],
+             (long long)(d > 1 ? r.grid.n[1] : 1), (long long)(d > 2 ? r.grid.n[2] : 1),
+             r.grid.embed_factor == 0 ? 2 : r.grid.embed_factor, r.grid.cell[0],
              d > 1 ? r.grid.cell[1] : 1.0, d > 2 ? r.grid.cell[2] : 1.0, r.xi.kind, r.xi.scale,
              r.xi.kind == CF_XI_GEN_CAUCHY ? r.xi.beta : 0.0, r.embed_flags);
     return b;

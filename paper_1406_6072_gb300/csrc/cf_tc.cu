@@ -572,10 +572,10 @@ static long long tc_lines_per_block(long long L) { return kCtaRows / (L / 16); }
 
 cf_status tc_check_grid(const GridInfo& g) {
     bool ok = g.ndim == 2 || g.ndim == 3;
-    for (int a = 0; ok && a < g.ndim; ++a) ok = tc_length_ok(g.m[a]);
+    for (int a = 0; ok && a < g.ndim; ++a) ok = tc_length_ok(g.m[a]) && g.m[a] == 2 * g.n[a];
     if (!ok)
         return fail(CF_ERR_UNSUPPORTED,
-                    "tensor-core modes need a 2D or 3D grid with embedded sides 256, 512, 1024, 2048 or 4096");
+                    "tensor-core modes need a 2D or 3D grid with embedded sides 2n = 256..4096");
     return CF_OK;
 }
 

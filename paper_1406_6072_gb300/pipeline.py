@@ -28,7 +28,7 @@ class FieldPipeline:
         self.R = wl.R if R is None else R
         self.dtype = cf.CF_F32 if wl.dtype == "f32" else cf.CF_F64
         self.tdtype = torch.float32 if wl.dtype == "f32" else torch.float64
-        self.grid = cf.make_grid(wl.n, wl.cell[: wl.ndim])
+        self.grid = cf.make_grid(wl.n, wl.cell[: wl.ndim], wl.factor)
         self.xi = cf.make_xi(wl.xi_kind, wl.amp, wl.scale, wl.beta)
         self.flags = cf.CF_EMBED_CLAMP if wl.clamp else 0
         self.with_lp = wl.nbar is not None and self.dtype == cf.CF_F32

@@ -37,6 +37,7 @@ class Workload:
     nbins: int | None = None      # power-spectrum bins, linear in |n| over [0, n/2)
     cell: tuple = field(default=(1.0, 1.0, 1.0))
     text: str = ""
+    factor: int = 2                 # embedded side / survey side
 
     @property
     def ndim(self) -> int:
@@ -44,7 +45,7 @@ class Workload:
 
     @property
     def m(self) -> tuple:
-        return tuple(2 * v for v in self.n)
+        return tuple(self.factor * v for v in self.n)
 
     @property
     def cells_per_field(self) -> int:
@@ -82,6 +83,11 @@ CONFIGS = {
         nbins=64,
         text="2D 2048^2 survey in 4096^2, xi = 0.8/(1+(r/16)^2)^0.4 (clamped), 32 realizations, "
              "precision sweep, seed 4"),
+    "cauchy2d_n512_padding": Workload(
+        "cauchy2d_n512_padding", (512, 512), XI_GEN_CAUCHY, 0.8, 8.0, 0.4, "f32", 64, 2, True,
+        sigma2=0.8, nbar=2.0, nbins=64,
+        text="the 2D 512^2 workload embedded in 1024^2, 2048^2 and 4096^2 (factors 2, 4, 8): clamping "
+             "error against cost, 64 realizations, lognormal + Poisson, 64-bin spectra, seed 2"),
     "exp3d_n256_sweep": Workload(
         "exp3d_n256_sweep", (256, 256, 256), XI_EXPONENTIAL, 1.0, 8.0, 0.0, "f32", 4, 8, False,
         nbins=64,

@@ -48,10 +48,14 @@ def test_argument_errors_before_any_cuda_call(cfmod):
     rep = cfmod.cf_embed_report()
     xi = cfmod.make_xi(cfmod.CF_XI_GAUSSIAN, 1.0, 2.0)
     assert lib.cf_embed(None, C.byref(xi), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_ARG
-    g = cfmod.make_grid((3, 4))  # 2n = 6 is not a power of two
-    assert lib.cf_embed(C.byref(g), C.byref(xi), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_UNSUPPORTED
-    assert "power of two" in cfmod.cf_last_error()
+    g = cfmod.make_grid((3, 4), factor=3)  # embedding factors are 2, 4 or 8
+    assert lib.cf_embed(C.byref(g), C.byref(xi), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_ARG
+    assert "embed_factor" in cfmod.cf_last_error()
     g = cfmod.make_grid((4096, 4))  # 2n = 8192 too long
+    assert lib.cf_embed(C.byref(g), C.byref(xi), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_UNSUPPORTED
+    g = cfmod.make_grid((2049, 4))  # next power of two >= 2n is 8192
+    assert lib.cf_embed(C.byref(g), C.byref(xi), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_UNSUPPORTED
+    g = cfmod.make_grid((1024, 4), factor=8)
     assert lib.cf_embed(C.byref(g), C.byref(xi), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_UNSUPPORTED
     g4 = cfmod.make_grid((4, 4, 4, 4)[:3])
     g4.ndim = 4

@@ -207,3 +207,46 @@ def test_periodic_box_spectrum_matches_continuous_transform(orc, box_factor):
     P[~on] = 0.0
     P[0, 0] = 0.0
     assert np.max(np.abs(lam - P)) <= 1e-12 * P.max()
+
+
+# ---------------------------------------------------------------- larger embedding grids
+def _xi_closed_form(kind, amp, scale, beta, r):
+    if kind == 0:
+        return amp * np.exp(-r**2 / (2 * scale**2))
+    if kind == 1:
+        return amp * (1 + (r / scale) ** 2) ** (-beta)
+    return amp * np.exp(-r / scale)
+
+
+@pytest.mark.parametrize("n,p,kind", [([4], 4, 0), ([4], 8, 2), ([2, 3], 4, 1), ([2, 2, 1], 8, 0)])
+def test_padded_row_lags_and_spectrum(orc, n, p, kind):
+    """Embedding on p times the survey side: index m_i has lag m_i below M_i/2
+    and m_i - M_i from M_i/2 on (for p = 2 the paper's grid -n..n-1); the
+    eigenvalues are the row's DFT (direct sum)."""
+    c = orc.embed_row(n, kind, 0.9, 1.7, 0.4, factor=p)
+    M = tuple(p * v for v in n)
+    assert c.shape == M
+    for idx in np.ndindex(*M):
+        lag = np.array([m if 2 * m < Mi else m - Mi for m, Mi in zip(idx, M)], dtype=np.float64)
+        assert c[idx] == pytest.approx(_xi_closed_form(kind, 0.9, 1.7, 0.4, np.sqrt(np.sum(lag**2))), rel=1e-15)
+    lam = orc.eigenvalues(n, c)
+    direct = _direct_dft_real(c)
+    assert np.max(np.abs(lam - direct.real)) <= 1e-13 * np.sum(np.abs(c))
+
+
+def test_padding_reduces_the_clamping_error(orc):
+    """Wood and Chan's remedy, cited in section 1: a larger periodic grid
+    makes the embedded spectrum less negative.  For the slowly decaying
+    generalised Cauchy family (not PSD on any of these grids) the clamped
+    covariance error falls about fourfold per doubling of the grid."""
+    errs = []
+    for p in (2, 4, 8):
+        e = orc.embed([16, 16], 1, 0.8, 2.0, 0.4, clamp=True, factor=p)
+        assert e["report"]["clamped"] == 1
+        errs.append(e["report"]["cov_error"])
+        # the reported error is that of the realised covariance IDFT(lambda+)
+        realised = np.real(np.fft.ifftn(e["lambda_plus"]))
+        M = e["c"].shape
+        survey = np.ix_(*[np.r_[0:16, M[a] - 15:M[a]] for a in range(2)])
+        assert np.max(np.abs(realised - e["c"])[survey]) == pytest.approx(e["report"]["cov_error"], rel=1e-9)
+    assert errs[1] < errs[0] / 2 and errs[2] < errs[1] / 2

@@ -28,13 +28,12 @@ def _target_cov(n, c):
 
 
 def _linear_map(orc, n, s):
-    M = tuple(2 * v for v in n)
-    total = int(np.prod(M))
+    total = int(np.asarray(s).size)
     cols = []
     for k in range(total):
         e = np.zeros(total, dtype=np.complex128)
         e[k] = 1.0
-        cols.append(orc.sample_given_noise(n, s.ravel(), e).ravel())
+        cols.append(orc.sample_given_noise(n, s, e).ravel())
     return np.stack(cols, axis=1)
 
 
@@ -50,6 +49,25 @@ def test_sampler_is_exact_on_the_survey(orc, n, kind, scale):
     assert np.max(np.abs(AAH.imag)) < 1e-12 * C.max()
     # A A^T = 0 is automatic for complex noise; W W^T has zero expectation
     # The two fields are uncorrelated: E[Re W Im W^T] = -Im(A A^H) = 0 (above).
+
+
+@pytest.mark.parametrize("n,M,kind,scale", [((4, 3), (16, 12), 0, 0.7), ((3, 2, 2), (24, 16, 16), 2, 0.9),
+                                            ((6,), (48,), 0, 1.2), ((3, 5), (8, 16), 2, 0.8), ((5,), (16,), 0, 0.9)])
+def test_padded_sampler_is_exact_on_the_survey(orc, n, M, kind, scale):
+    """On a periodic grid of M_i >= 2 n_i points the survey box is still a
+    sub-box of side at most half the period, so its covariance Re(A A^H) is
+    xi(x - y) exactly: compared with xi evaluated in closed form at the cell
+    separations (not read off the oracle's own row).  Covers p times the side
+    and survey sizes embedded in the next power of two."""
+    e = orc.embed(list(n), kind, 1.1, scale, 0.0, M=M)
+    assert e["report"]["status"] == 0 and e["report"]["clamped"] == 0
+    A = _linear_map(orc, n, e["sqrt_lambda"])
+    AAH = A @ A.conj().T
+    idx = np.indices(n).reshape(len(n), -1).T
+    r = np.sqrt(((idx[:, None, :] - idx[None, :, :]) ** 2).sum(-1))
+    C = 1.1 * (np.exp(-r**2 / (2 * scale**2)) if kind == 0 else np.exp(-r / scale))
+    assert np.max(np.abs(AAH.real - C)) < 1e-12 * C.max()
+    assert np.max(np.abs(AAH.imag)) < 1e-12 * C.max()
 
 
 def test_clamped_sampler_realises_inverse_transform_of_lambda_plus(orc):
