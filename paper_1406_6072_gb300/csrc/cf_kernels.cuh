@@ -46,6 +46,13 @@ struct FieldEpi {
     uint32_t r0;        // global index of the chunk's first realization
     long long cells;
     const RealDesc* desc;  // batched launch: per-realization parameters (else null)
+    PoissonDefer defer;    // inconclusive binary32 decisions (null items: decide in place)
+
+    __device__ __forceinline__ int32_t count(int32_t* dst, float G, double half_sigma2_d, float half_sigma2_ff,
+                                             double nbar_d, float nbar_ff, float fi, unsigned long long ub) const {
+        const int j = poisson_count_try(G, half_sigma2_ff, nbar_ff, fi, ub);
+        return j >= 0 ? j : poisson_defer(defer, dst, G, half_sigma2_d, nbar_d, fi, ub);
+    }
 
     __device__ __forceinline__ void operator()(int rl, long long cell, C2<T> w) const {
         if (desc) {
@@ -61,9 +68,9 @@ struct FieldEpi {
             const float g0 = (float)w.x, g1 = (float)w.y;
             const uint4 x = poisson_words((unsigned long long)cell, r0 + (uint32_t)rl, pkey0, pkey1);
             const float fi = f ? f[cell] : 1.0f;
-            counts[base] = poisson_count_fast(g0, half_sigma2, half_sigma2_f, nbar, nbar_f, fi, bits53(x.x, x.y));
+            counts[base] = count(counts + base, g0, half_sigma2, half_sigma2_f, nbar, nbar_f, fi, bits53(x.x, x.y));
             counts[base + cells] =
-                poisson_count_fast(g1, half_sigma2, half_sigma2_f, nbar, nbar_f, fi, bits53(x.z, x.w));
+                count(counts + base + cells, g1, half_sigma2, half_sigma2_f, nbar, nbar_f, fi, bits53(x.z, x.w));
             if (delta) {
                 delta[base] = expf(g0 - half_sigma2_f) - 1.0f;
                 delta[base + cells] = expf(g1 - half_sigma2_f) - 1.0f;
@@ -77,10 +84,10 @@ struct FieldEpi {
         d.fields[cell + cells] = g1;
         if (d.counts) {
             const uint4 x = poisson_words((unsigned long long)cell, d.r, d.pkey0, d.pkey1);
-            d.counts[cell] = poisson_count_fast(g0, d.half_sigma2, d.half_sigma2_f, d.nbar, d.nbar_f, 1.0f,
-                                                bits53(x.x, x.y));
-            d.counts[cell + cells] = poisson_count_fast(g1, d.half_sigma2, d.half_sigma2_f, d.nbar, d.nbar_f, 1.0f,
-                                                        bits53(x.z, x.w));
+            d.counts[cell] = count(d.counts + cell, g0, d.half_sigma2, d.half_sigma2_f, d.nbar, d.nbar_f, 1.0f,
+                                   bits53(x.x, x.y));
+            d.counts[cell + cells] = count(d.counts + cell + cells, g1, d.half_sigma2, d.half_sigma2_f, d.nbar,
+                                           d.nbar_f, 1.0f, bits53(x.z, x.w));
         }
     }
 };

@@ -32,13 +32,14 @@ struct SRowsCfg : TileCfg<T, L, CF_SROWS_E, CF_SROWS_THREADS, CF_SROWS_MINB> {
 // first-stage points (Philox stream 0), scales it by sqrt(lambda+)/sqrt(M^d),
 // runs the inverse line transform, and keeps the first `keep` outputs (the
 // survey's n <= L/2 points).  Output: complex intermediate
-// [chunk][nrows][keep], or for a one-dimensional grid the fields (and counts)
-// directly.
+// [chunk][nrows][keep] (EPI false), or for a one-dimensional grid the fields
+// (and counts) directly (EPI true; a separate instantiation, so that the
+// multi-dimensional row pass carries no epilogue code and registers).
 // --------------------------------------------------------------------------
-template <typename T, int L>
+template <typename T, int L, bool EPI>
 __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     k_sample_rows(const T* __restrict__ s, T amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
-                  long long nrows, int keep, C2<T>* __restrict__ out, int mode, FieldEpi<T> epi,
+                  long long nrows, int keep, C2<T>* __restrict__ out, FieldEpi<T> epi,
                   const C2<T>* __restrict__ tw, const RealDesc* __restrict__ desc) {
     using Cfg = SRowsCfg<T, L>;
     using G = typename Cfg::G;
@@ -87,10 +88,10 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     }
     auto sink = [&](int, int p, C2<T> val) {
         if (!valid || p >= keep) return;
-        if (mode == 0)
-            out[((size_t)rl * nrows + row) * keep + p] = val;
-        else
+        if constexpr (EPI)
             epi(rl, (long long)row * keep + p, val);
+        else
+            out[((size_t)rl * nrows + row) * keep + p] = val;
     };
     line_fft<T, L, +1, L / 2>(sm, RowLayout<E, G::PADDED>(), line, j, v, tw, sink);
 }
@@ -102,12 +103,12 @@ static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_sca
     return dispatch_line(L, [&](auto Lc) -> cf_status {
         constexpr int LL = decltype(Lc)::value;
         using Cfg = SRowsCfg<T, LL>;
-        auto kern = k_sample_rows<T, LL>;
+        auto kern = mode ? k_sample_rows<T, LL, true> : k_sample_rows<T, LL, false>;
         CF_TRY(prepare_smem(kern, Cfg::SMEM));
         dim3 grid((unsigned)((nrows + Cfg::ROWS - 1) / Cfg::ROWS), (unsigned)chunk);
         ScopedKernelTimer kt(st, sizeof(T) == 4 ? "sample_rows_f32" : "sample_rows_f64", LL);
         kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
-                                                     nrows, keep, out, mode, epi, twiddles<T>(), desc);
+                                                     nrows, keep, out, epi, twiddles<T>(), desc);
         CF_CHECK_LAUNCH();
         return CF_OK;
     });
@@ -157,6 +158,24 @@ static int tuned_chunk(const GridInfo& g, size_t elem) {
     return it == g_tuned_chunk.end() ? 0 : it->second;
 }
 
+// Binary32 workspaces end with the list of Poisson decisions left to the
+// binary64 walk (a counter, then entries; about 4e-4 of the counts at
+// nbar = 2, room for 1/256 of them): the fix-up kernel decides them after the
+// column pass, with full warps.  Without room for the list the epilogue
+// decides in place.
+constexpr size_t kDeferHead = 256;
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static size_t defer_entries(const GridInfo& g) { return (size_t)(2 * g.ncell) / 256 + 16; }
+static size_t defer_bytes(const GridInfo& g, size_t elem) {
+    return elem == sizeof(C2<float>) ? sizeof(PoissonTodo) * defer_entries(g) : 0;
+}
+
+// Workspace bytes of a chunk of c realizations: intermediates, then the list.
+static size_t chunk_bytes(const GridInfo& g, size_t elem, size_t c) {
+    const size_t list = defer_bytes(g, elem);
+    return align256(c * per_realization_bytes(g, elem)) + (list ? kDeferHead + c * list : 0);
+}
+
 static int pick_chunk(const GridInfo& g, size_t elem, int R, size_t ws_bytes) {
     const size_t per = per_realization_bytes(g, elem);
     if (per == 0) return R < 65535 ? R : 65535;  // grid.y bound
@@ -165,9 +184,46 @@ static int pick_chunk(const GridInfo& g, size_t elem, int R, size_t ws_bytes) {
     if (c < 1) c = 1;
     if (c > (size_t)R) c = (size_t)R;
     if (c > 65535) c = 65535;
-    const size_t by_ws = ws_bytes / per;
+    const size_t list = defer_bytes(g, elem);
+    size_t by_ws = ws_bytes > 2 * kDeferHead ? (ws_bytes - 2 * kDeferHead) / (per + list) : 0;
+    if (by_ws == 0) by_ws = ws_bytes / per;  // the intermediates alone
     if (c > by_ws) c = by_ws;
     return (int)c;
+}
+
+// The list inside a workspace holding `chunk` realizations (null items when
+// it does not fit).
+static PoissonDefer defer_list(const GridInfo& g, size_t elem, int chunk, void* ws, size_t ws_bytes) {
+    PoissonDefer d{};
+    if (!ws || !defer_bytes(g, elem) || chunk_bytes(g, elem, (size_t)chunk) > ws_bytes) return d;
+    unsigned char* t = (unsigned char*)ws + align256((size_t)chunk * per_realization_bytes(g, elem));
+    const size_t cap = (size_t)chunk * defer_entries(g);
+    d.count = (unsigned int*)t;
+    d.items = (PoissonTodo*)(t + kDeferHead);
+    d.capacity = cap > 0xffffffffull ? 0xffffffffu : (unsigned int)cap;
+    return d;
+}
+
+// Decides the listed counts in binary64 (one thread per entry).
+__global__ void __launch_bounds__(128) k_poisson_fixup(PoissonDefer d) {
+    const unsigned int n = *d.count < d.capacity ? *d.count : d.capacity;
+    for (unsigned int i = blockIdx.x * 128u + threadIdx.x; i < n; i += gridDim.x * 128u) {
+        const PoissonTodo t = d.items[i];
+        *t.dst = poisson_count_f64(t.G, t.half_sigma2, t.nbar, t.f, t.ubits);
+    }
+}
+
+static cf_status defer_begin(const PoissonDefer& d, cudaStream_t st) {
+    if (d.items) CF_CUDA(cudaMemsetAsync(d.count, 0, sizeof(unsigned int), st));
+    return CF_OK;
+}
+
+static cf_status defer_end(const PoissonDefer& d, cudaStream_t st) {
+    if (!d.items) return CF_OK;
+    ScopedKernelTimer kt(st, "poisson_fixup");
+    k_poisson_fixup<<<256, 128, 0, st>>>(d);
+    CF_CHECK_LAUNCH();
+    return CF_OK;
 }
 
 template <typename T>
@@ -186,9 +242,11 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
     C2<T>* buf1 = (C2<T>*)ws;
     C2<T>* buf2 = nullptr;
     if (d == 3) buf2 = buf1 + (size_t)chunk * g.m[0] * g.m[1] * g.n[2];
+    const PoissonDefer defer = lp ? defer_list(g, elem, chunk, ws, ws_bytes) : PoissonDefer{};
     for (int c0 = 0; c0 < R; c0 += chunk) {
         const int nr = (R - c0) < chunk ? (R - c0) : chunk;
         FieldEpi<T> epi{};
+        epi.defer = defer;
         epi.fields = fields ? (T*)fields + (size_t)c0 * 2 * cells : nullptr;
         epi.cells = cells;
         epi.r0 = (uint32_t)(r0 + (uint64_t)c0);
@@ -206,6 +264,7 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
         const uint32_t rr0 = (uint32_t)(r0 + (uint64_t)c0);
         const long long Ml = g.m[d - 1];
         const long long nrows = g.mtotal / Ml;
+        CF_TRY(defer_begin(defer, st));
         if (d == 1) {
             CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, nullptr, 1, epi, st));
         } else if (d == 2) {
@@ -219,6 +278,7 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
             // pass 3: axis 0 of [chunk][M0][N1*N2] -> fields
             CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0])));
         }
+        CF_TRY(defer_end(defer, st));
     }
     record_use(const_cast<cf_embedding*>(e), st);
     return CF_OK;
@@ -278,11 +338,14 @@ cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, v
     C2<float>* buf2 = d == 3 ? buf1 + (size_t)chunk * g.m[0] * g.m[1] * g.n[2] : nullptr;
     const long long Ml = g.m[d - 1];
     const long long nrows = g.mtotal / Ml;
+    const PoissonDefer defer = defer_list(g, elem, chunk, ws, ws_bytes);
     for (int c0 = 0; c0 < nreal; c0 += chunk) {
         const int nr = (nreal - c0) < chunk ? (nreal - c0) : chunk;
         FieldEpi<float> epi{};
         epi.cells = cells;
         epi.desc = desc + c0;
+        epi.defer = defer;
+        CF_TRY(defer_begin(defer, st));
         if (d == 1) {
             CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, nullptr, 1, epi, st, desc + c0));
         } else if (d == 2) {
@@ -293,13 +356,14 @@ cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, v
             CF_TRY((launch_cols<float, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1])));
             CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0])));
         }
+        CF_TRY(defer_end(defer, st));
     }
     return CF_OK;
 }
 
 size_t sample_chunk_bytes(const GridInfo& g, int nreal) {
-    const size_t per = per_realization_bytes(g, sizeof(C2<float>));
-    return per * (size_t)pick_chunk(g, sizeof(C2<float>), nreal < 1 ? 1 : nreal, (size_t)-1);
+    const size_t elem = sizeof(C2<float>);
+    return chunk_bytes(g, elem, (size_t)pick_chunk(g, elem, nreal < 1 ? 1 : nreal, (size_t)-1));
 }
 
 // Entry for cf_sample_noalloc (cf_noalloc.cu): the binary32 sampler into a
@@ -328,9 +392,8 @@ extern "C" cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, 
     }
     if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
     const size_t elem = dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>);
-    const size_t per = per_realization_bytes(e->grid, elem);
     int chunk = pick_chunk(e->grid, elem, R < 1 ? 1 : R, (size_t)-1);
-    *bytes = per * (size_t)(chunk < 1 ? 1 : chunk);
+    *bytes = chunk_bytes(e->grid, elem, (size_t)(chunk < 1 ? 1 : chunk));
     return CF_OK;
 }
 

@@ -289,6 +289,41 @@ def test_fused_sample_lp_parity(orc):
     emb.close()
 
 
+@pytest.mark.parametrize("n,nbar,sigma2", [((128, 128), 40.0, 1.5), ((64, 64, 32), 9.68, 0.8), ((1024,), 2.0, 0.8)])
+def test_deferred_binary64_decisions(orc, n, nbar, sigma2):
+    """Counts the binary32 walk leaves undecided go to a list in the workspace
+    and are decided by a second kernel; with a workspace too small for the
+    list they are decided in place.  Both give the same counts, which match
+    the oracle (up to flagged boundary cells)."""
+    R, seed, pseed = 3, 51, 52
+    g = cf.make_grid(n)
+    emb = cf.cf_embed(g, cf.make_xi(cf.CF_XI_GAUSSIAN, sigma2, 3.0))
+    fields = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+    counts = {}
+    M = [2 * v for v in n]
+    one = 8 * int(np.prod(M[:-1])) * n[-1] if len(n) == 2 else None
+    sizes = {"list": cf.cf_sample_workspace_size(emb, R, cf.CF_F32)}
+    if len(n) == 2:
+        sizes["in_place"] = one  # one realization's intermediates and no room for the list
+    else:
+        sizes["in_place"] = 0 if len(n) == 1 else None
+    for name, wsb in sizes.items():
+        if wsb is None:
+            continue
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=DEV)
+        c = torch.full((R, 2) + n, -7, dtype=torch.int32, device=DEV)
+        cf.cf_sample_lp(emb, seed, 0, R, cf.CF_F32, fields, cf.make_lp(sigma2, nbar, c, pseed), ws, wsb)
+        torch.cuda.synchronize()
+        counts[name] = c
+    assert all(int(c.min()) >= 0 for c in counts.values())
+    if len(counts) == 2:
+        assert torch.equal(counts["list"], counts["in_place"])
+    fl, nd = _lp_check(orc, fields.double().cpu().numpy().reshape(2 * R, -1),
+                       counts["list"].cpu().numpy().reshape(2 * R, -1), None, sigma2, nbar, None, pseed, 0)
+    print("flagged %d, differing %d" % (fl, nd))
+    emb.close()
+
+
 PK_CASES = [((64, 64), 16, cf.CF_BINS_LINEAR), ((32, 32), 5, cf.CF_BINS_LOG), ((16, 16, 16), 8, cf.CF_BINS_LINEAR),
             ((128, 128), 64, cf.CF_BINS_LINEAR), ((8, 8), 3, cf.CF_BINS_LINEAR)]
 
