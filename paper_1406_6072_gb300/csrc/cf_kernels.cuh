@@ -137,7 +137,10 @@ struct TileCfg {
     // lines per CTA
     static constexpr int LINES = G::TL >= THREADS_ ? 1 : ((THREADS_ / G::TL) > 32 ? 32 : (THREADS_ / G::TL));
     static constexpr int THREADS = LINES * G::TL;
-    static constexpr int MINB = THREADS * MINB_ <= 2048 ? MINB_ : (2048 / THREADS > 0 ? 2048 / THREADS : 1);
+    // resident CTAs promised to the register allocator: at most 1024 threads
+    // per SM in total, i.e. at least 64 registers per thread (a line longer
+    // than one CTA's default thread count otherwise got 32 and spilled)
+    static constexpr int MINB = THREADS * MINB_ <= 1024 ? MINB_ : (1024 / THREADS > 0 ? 1024 / THREADS : 1);
     static constexpr size_t SMEM = sizeof(C2<T>) * (size_t)LINES * (size_t)G::PADDED;
 };
 
