@@ -160,16 +160,22 @@ def kernel_costs(wl, R, chunks):
     return costs
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current version of that kernel."""
+def recorded_dominant():
+    """The committed ncu record of the dominant kernel (largest share of the
+    launch list), or {}."""
     try:
         with open(os.path.join(ROOT, "profiles", "dominant_kernel_traffic.json")) as f:
-            d = json.load(f)
-        if d.get("kernel") == kernel and d.get("current", False):
-            return d["dram_bytes_per_launch"]
+            return json.load(f)
     except Exception:
-        pass
+        return {}
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on this workload and the current version of that kernel."""
+    d = recorded_dominant()
+    if d.get("kernel") == kernel and d.get("workload") == workload and d.get("current", False):
+        return d["dram_bytes_per_launch"]
     return None
 
 
@@ -183,7 +189,12 @@ def roofline(wl, R, timing, steps, hbm_peak, peak_kind, sm_mhz):
     launches_rows = per_kernel.get("sample_rows_f32", [steps, 0])[0]
     chunks = max(1, launches_rows // max(steps, 1))
     costs = kernel_costs(wl, R, chunks)
-    dom = max(per_kernel.items(), key=lambda kv: kv[1][1])[0]
+    # the kernel with the largest share of the ncu launch list (serialised
+    # times; event times of kernels on concurrent streams overlap), else the
+    # largest event time
+    dom = recorded_dominant().get("kernel")
+    if dom not in costs or per_kernel.get(dom, [0, 0.0])[1] <= 0:
+        dom = max(per_kernel.items(), key=lambda kv: kv[1][1])[0]
     if dom not in costs:
         timed = [k for k in costs if per_kernel.get(k, [0, 0.0])[1] > 0]
         if not timed:
@@ -198,7 +209,7 @@ def roofline(wl, R, timing, steps, hbm_peak, peak_kind, sm_mhz):
     achieved = ops / avg_s / 1e12
     hbm = byts / avg_s / 1e9
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
-            "unit": "TOP/s", "frac": round(achieved / alu_peak, 4), "traffic": recorded_traffic(dom),
+            "unit": "TOP/s", "frac": round(achieved / alu_peak, 4), "traffic": recorded_traffic(dom, wl.name),
             "peak_source": "152 SMs x 128 FP32 lanes x %s SM clock %.0f MHz (one op per lane per cycle)"
                            % ("sampled" if sm_mhz else "maximum", clock),
             "ops_per_launch": int(ops), "bytes_per_launch": int(byts), "avg_launch_ms": round(avg_s * 1e3, 5),

@@ -377,26 +377,25 @@ __global__ void k_pk_mean(const double* __restrict__ pk, long long nfields, int 
     if (threadIdx.x == 0) mean[b] = nfields > 0 ? sh[0] / (double)nfields : 0.0;
 }
 
-// unbiased covariance: one block per (a, b) with a <= b, threads over fields
-__global__ void k_pk_cov(const double* __restrict__ pk, const double* __restrict__ mean, long long nfields, int nbins,
-                         double* __restrict__ cov) {
-    __shared__ double sh[256];
-    const int a = blockIdx.y, b = blockIdx.x;
-    if (b < a) return;
-    const double ma = mean[a], mb = mean[b];
-    double s = 0.0;
-    for (long long f = threadIdx.x; f < nfields; f += blockDim.x)
-        s += (pk[f * nbins + a] - ma) * (pk[f * nbins + b] - mb);
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double c = nfields > 1 ? sh[0] / (double)(nfields - 1) : 0.0;
-        cov[(size_t)a * nbins + b] = c;
-        cov[(size_t)b * nbins + a] = c;
+// unbiased covariance: one warp per bin pair (a, b >= a), blockIdx.y = a and
+// warp blockIdx.x * 8 + w gives b - a; lanes over fields with a warp-shuffle
+// sum (short dependent chains: binary64 latency is long on this part)
+__global__ void __launch_bounds__(256) k_pk_cov(const double* __restrict__ pk, const double* __restrict__ mean,
+                                                long long nfields, int nbins, double* __restrict__ cov) {
+    const int a = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double ma = mean[a];
+    const int b = a + (int)blockIdx.x * 8 + warp;
+    if (b < nbins) {
+        const double mb = mean[b];
+        double s = 0.0;
+        for (long long f = lane; f < nfields; f += 32) s += (pk[f * nbins + a] - ma) * (pk[f * nbins + b] - mb);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const double c = nfields > 1 ? s / (double)(nfields - 1) : 0.0;
+            cov[(size_t)a * nbins + b] = c;
+            cov[(size_t)b * nbins + a] = c;
+        }
     }
 }
 
@@ -679,7 +678,7 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
         if (mean || cov) {
             double* mu = mean ? mean : cross;  // scratch when only the covariance is wanted
             k_pk_mean<<<P.nbins, 256, 0, s>>>(pk_out, nfields, P.nbins, mu);
-            if (cov) k_pk_cov<<<dim3(P.nbins, P.nbins), 256, 0, s>>>(pk_out, mu, nfields, P.nbins, cov);
+            if (cov) k_pk_cov<<<dim3((P.nbins + 7) / 8, P.nbins), 256, 0, s>>>(pk_out, mu, nfields, P.nbins, cov);
         }
     }
     CF_CHECK_LAUNCH();
@@ -694,7 +693,7 @@ cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* m
     if (!mu && pool_malloc((void**)&mu, sizeof(double) * (size_t)ncols, s) != cudaSuccess)
         return fail(CF_ERR_NOMEM, "scratch for the mean failed");
     k_pk_mean<<<ncols, 256, 0, s>>>(x, nrows, ncols, mu);
-    if (cov) k_pk_cov<<<dim3(ncols, ncols), 256, 0, s>>>(x, mu, nrows, ncols, cov);
+    if (cov) k_pk_cov<<<dim3((ncols + 7) / 8, ncols), 256, 0, s>>>(x, mu, nrows, ncols, cov);
     if (!mean) cudaFreeAsync(mu, s);
     CF_CHECK_LAUNCH();
     return CF_OK;

@@ -184,9 +184,13 @@ static int pick_chunk(const GridInfo& g, size_t elem, int R, size_t ws_bytes) {
     if (c < 1) c = 1;
     if (c > (size_t)R) c = (size_t)R;
     if (c > 65535) c = 65535;
+    // the most realizations whose intermediates and list fit, else the most
+    // whose intermediates alone fit
     const size_t list = defer_bytes(g, elem);
-    size_t by_ws = ws_bytes > 2 * kDeferHead ? (ws_bytes - 2 * kDeferHead) / (per + list) : 0;
-    if (by_ws == 0) by_ws = ws_bytes / per;  // the intermediates alone
+    size_t by_ws = ws_bytes / (per + list);
+    if (by_ws > c) by_ws = c;
+    while (by_ws > 0 && chunk_bytes(g, elem, by_ws) > ws_bytes) --by_ws;
+    if (by_ws == 0) by_ws = ws_bytes / per;
     if (c > by_ws) c = by_ws;
     return (int)c;
 }

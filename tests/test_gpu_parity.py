@@ -408,3 +408,25 @@ def test_periodic_box_embedding(orc, box_factor, log1p):
         torch.cuda.synchronize()
         assert torch.equal(corner, fields[:, :, : n[0], : n[1]])
     emb.close()
+
+
+def test_workspace_of_the_reported_size_takes_one_chunk():
+    """A workspace of cf_sample_workspace_size(R) bytes holds all R
+    realizations of a small grid at once (with the list of deferred Poisson
+    decisions): one launch of each pass, no ragged tail chunk."""
+    n, R = (128, 128), 64
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 0.8, 3.0))
+    wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
+    fields = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+    counts = torch.empty((R, 2) + n, dtype=torch.int32, device=DEV)
+    torch.cuda.synchronize()
+    cf.cf_kernel_timing(1)
+    cf.cf_sample_lp(emb, 3, 0, R, cf.CF_F32, fields, cf.make_lp(0.8, 2.0, counts, 4), ws, wsb)
+    torch.cuda.synchronize()
+    t = cf.cf_kernel_timing_read()
+    cf.cf_kernel_timing(0)
+    launches = {k.split("<")[0]: v[0] for k, v in t.items()}
+    assert launches.get("sample_rows_f32") == 1 and launches.get("icols_fields_lp_f32") == 1, launches
+    assert launches.get("poisson_fixup") == 1, launches
+    emb.close()
