@@ -52,6 +52,8 @@ def parse_args():
                    help="mock_n128 workload: realizations per method (default 2000)")
     p.add_argument("--graph", action="store_true",
                    help="time replays of a captured plan (embedding computed once, per-realization path replayed)")
+    p.add_argument("--fused", action="store_true",
+                   help="square 2D grids: sampler and the fields' spectra through cf_sample_spectra")
     p.add_argument("--precision", default="all", choices=["all", "f64", "f32", "bf16_tc", "f16_tc"],
                    help="precision-sweep workload: run one precision only")
     return p.parse_args()
@@ -797,7 +799,7 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
     if table is None:
         return None
     h_table = torch.from_numpy(np.ascontiguousarray(table)).pin_memory()
-    other = FieldPipeline(wl, pipe.dev, stream=torch.cuda.Stream(pipe.dev))
+    other = FieldPipeline(wl, pipe.dev, stream=torch.cuda.Stream(pipe.dev), fused=pipe.fused)
     lanes = []
     for p in (pipe, other):
         d_table = torch.empty_like(h_table, device=p.dev)
@@ -877,7 +879,7 @@ def main():
     # embeddings on their own stream: step k+1's binary64 embedding overlaps
     # step k's sampler and spectra (every step still embeds, samples and
     # computes its spectra; the timed region covers all of it)
-    pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev))
+    pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev), fused=args.fused)
     R = pipe.R
 
     def barrier():
@@ -940,7 +942,8 @@ def main():
                        "cells_per_step": cells_all, "realizations_per_s": R * world / (ms_max * 1e-3),
                        "l2": "each step writes %d MiB of fields and counts (> 129 MB L2)"
                              % (2 * pipe.cells_per_step * 4 >> 20),
-                       "parallelism": "replicas x%d" % world, "tuned_chunk": tuned},
+                       "parallelism": "replicas x%d" % world, "tuned_chunk": tuned,
+                       "fused_spectra": bool(pipe.fused)},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report, "cufft_reference": cufft,

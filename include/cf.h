@@ -53,6 +53,7 @@ extern "C" {
 #endif
 
 typedef struct CUstream_st* cf_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+typedef struct CUevent_st* cf_event_t;   /* == cudaEvent_t */
 
 typedef enum {
     CF_OK = 0,
@@ -374,6 +375,30 @@ CF_API cf_status cf_power_spectrum_counts(const int32_t* counts, const float* f_
                                    int64_t nfields, const cf_bins* bins, double* pk_out,
                                    int64_t* nmodes_out, double* mean_or_null, double* cov_or_null,
                                    void* ws, size_t ws_bytes, cf_stream_t s);
+
+/* cf_sample (binary32) or cf_sample_lp (lp non-NULL) followed by
+ * cf_power_spectrum of the 2R fields, with the sampler's last pass fused with
+ * the first axis of the spectra (sections 2 and 3.2): the column pass keeps
+ * each cropped column in shared memory and transforms it forward, so the
+ * fields are not read back for their spectra.  Square 2D grids only (n0 = n1
+ * = n, 128 <= n <= 2048, embed_factor 2), R <= 32767.  Same outputs as the
+ * separate calls: fields and counts identical, spectra equal up to rounding
+ * (another order of the transform's axes).  ws / ws_bytes: the sampler
+ * workspace (cf_sample_workspace_size); pk_ws: pk_ws_bytes >=
+ * cf_sample_spectra_workspace_size(e, R, bins) bytes of device memory for the
+ * half spectra and accumulators.  The count maps' spectra, if wanted, come
+ * from cf_power_spectrum_counts on lp->counts_out; sampled_or_null, if given,
+ * is recorded on s once the fields and counts are complete and before the
+ * spectra, so that work on another stream may start from them.  Errors:
+ * CF_ERR_UNSUPPORTED for other grids, CF_ERR_NOMEM for a short workspace, else
+ * as the separate calls. */
+CF_API cf_status cf_sample_spectra_workspace_size(const cf_embedding* e, int32_t R, const cf_bins* bins,
+                                                  size_t* pk_ws_bytes);
+CF_API cf_status cf_sample_spectra(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, float* fields_out,
+                                   const cf_lp_params* lp_or_null, const cf_bins* bins, double* pk_out,
+                                   int64_t* nmodes_out, double* mean_or_null, double* cov_or_null, void* ws,
+                                   size_t ws_bytes, void* pk_ws, size_t pk_ws_bytes, cf_event_t sampled_or_null,
+                                   cf_stream_t s);
 
 /* ---------------------------------------------------------------- plans
  * The binary32 per-realization path of one embedding recorded once as a CUDA

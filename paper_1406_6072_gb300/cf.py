@@ -145,6 +145,9 @@ _sigs = {
                           C.c_size_t, _S],
     "cf_power_spectrum_counts": [_P, _P, C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), _P, _P, _P, _P, _P,
                                  C.c_size_t, _S],
+    "cf_sample_spectra_workspace_size": [_P, C.c_int32, C.POINTER(cf_bins), C.POINTER(C.c_size_t)],
+    "cf_sample_spectra": [_P, C.c_uint64, C.c_uint64, C.c_int32, _P, _P, C.POINTER(cf_bins), _P, _P, _P, _P, _P,
+                          C.c_size_t, _P, C.c_size_t, _P, _S],
     "cf_serve_create": [C.POINTER(cf_serve_cfg), C.POINTER(_P)],
     "cf_serve_submit": [_P, C.POINTER(cf_request), C.POINTER(C.c_uint64)],
     "cf_serve_poll": [_P, C.c_uint64, C.POINTER(cf_result)],
@@ -420,6 +423,29 @@ def cf_power_spectrum_workspace_size(grid, nfields, bins, dtype):
     _check(_lib.cf_power_spectrum_workspace_size(C.byref(grid), nfields, C.byref(bins), dtype, C.byref(n)),
            "cf_power_spectrum_workspace_size")
     return n.value
+
+
+def cf_sample_spectra_workspace_size(emb, R, bins):
+    n = C.c_size_t()
+    _check(_lib.cf_sample_spectra_workspace_size(emb.handle, R, C.byref(bins), C.byref(n)),
+           "cf_sample_spectra_workspace_size")
+    return n.value
+
+
+def cf_sample_spectra(emb, seed, r0, R, fields_out, lp, bins, pk_out, nmodes_out, mean=None, cov=None, ws=None,
+                      ws_bytes=0, pk_ws=None, pk_ws_bytes=0, sampled_event=None, stream=None):
+    """cf_sample / cf_sample_lp (lp may be None) fused with cf_power_spectrum
+    of the fields; sampled_event (torch.cuda.Event) is recorded once the
+    fields and counts are complete."""
+    ev = None
+    if sampled_event is not None:
+        h = sampled_event.cuda_event if hasattr(sampled_event, "cuda_event") else int(sampled_event)
+        if not h:
+            raise ValueError("sampled_event has no CUDA event yet (record it once first)")
+        ev = C.c_void_p(h)
+    _check(_lib.cf_sample_spectra(emb.handle, seed, r0, R, _ptr(fields_out), C.byref(lp) if lp is not None else None,
+                                  C.byref(bins), _ptr(pk_out), _ptr(nmodes_out), _ptr(mean), _ptr(cov), _ptr(ws),
+                                  ws_bytes, _ptr(pk_ws), pk_ws_bytes, ev, _stream(stream)), "cf_sample_spectra")
 
 
 def cf_power_spectrum(fields, dtype, grid, nfields, bins, pk_out, nmodes_out, mean=None, cov=None, ws=None,

@@ -685,6 +685,52 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
     return CF_OK;
 }
 
+// Spectra of F real fields of a 2D square grid whose transform along one
+// axis is done already (the sampler's fused column pass): half[F][n][n/2+1],
+// the transformed axis last.  The binning pass transforms the other axis and
+// bins with the mirror weights of the half axis (k^2 is symmetric in the two
+// axes), then the final pass, mean and covariance.  acc_ws holds
+// pk_halves_acc_bytes() bytes.
+size_t pk_halves_acc_bytes(const cf_grid* grid, long long F, const cf_bins* bins) {
+    PkPlan P;
+    if (make_plan(grid, F, bins, sizeof(C2<float>), &P) != CF_OK) return 0;
+    return align256(P.off_half);
+}
+
+cf_status pk_from_halves_f32(const cf_grid* grid, long long F, const cf_bins* bins, const C2<float>* half,
+                             double* pk_out, int64_t* nmodes_out, double* mean, double* cov, char* acc_ws,
+                             cudaStream_t s) {
+    PkPlan P;
+    CF_TRY(make_plan(grid, F, bins, sizeof(C2<float>), &P));
+    if (P.g.ndim != 2) return fail(CF_ERR_UNSUPPORTED, "fused spectra are 2D");
+    const int16_t* bin_of = nullptr;
+    const unsigned long long* nmodes = nullptr;
+    double* acc = (double*)(acc_ws + P.off_acc);
+    double* mpow = (double*)(acc_ws + P.off_mpow);
+    {
+        ScopedKernelTimer kt(s, "pk_setup");
+        CF_TRY(get_bins(P, acc_ws, s, &bin_of, &nmodes));
+        CF_CUDA(cudaMemsetAsync(acc_ws + P.off_acc, 0, P.off_half - P.off_acc, s));
+    }
+    CF_TRY(dispatch_line(P.g.n[0], [&](auto Lc) -> cf_status {
+        return launch_pk_cols<float, decltype(Lc)::value>(half, P.H, 1, P, bin_of, acc, nullptr, nullptr, 0, F, s);
+    }));
+    const double volfac = P.g.cell[0] / (double)P.g.n[0] * P.g.cell[1] / (double)P.g.n[1];
+    {
+        ScopedKernelTimer kt(s, "pk_finalize");
+        k_pk_finalize<<<grid_blocks(F * P.nbins, 256, 1024), 256, 0, s>>>(acc, nullptr, mpow, nullptr, nullptr,
+                                                                          (double)P.g.ncell, nmodes, F, P.nbins,
+                                                                          volfac, pk_out, nmodes_out);
+        if (mean || cov) {
+            double* mu = mean ? mean : (double*)(acc_ws + P.off_cross);
+            k_pk_mean<<<P.nbins, 256, 0, s>>>(pk_out, F, P.nbins, mu);
+            if (cov) k_pk_cov<<<dim3((P.nbins + 7) / 8, P.nbins), 256, 0, s>>>(pk_out, mu, F, P.nbins, cov);
+        }
+    }
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
 // Mean over rows and unbiased covariance of x [nrows][ncols] (binary64); used
 // for the power spectra and for the counts-in-cells histograms.
 cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* mean, double* cov, cudaStream_t s) {

@@ -114,6 +114,91 @@ static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_sca
     });
 }
 
+// --------------------------------------------------------------------------
+// Last sampler pass of a 2D square grid (L = M0 = 2n) fused with the first
+// axis of the fields' power spectrum (section 3.2, eq. (Def spec)): the CTA's
+// C columns are transformed back, cropped and passed to the field epilogue
+// as in k_cols, and the cropped columns W (Re = field 2r, Im = field 2r+1)
+// are kept in shared memory and transformed forward along axis 0 (length
+// n).  The two real fields' spectra separate per column:
+// A(k) = (Z(k) + conj Z(-k))/2, B(k) = (Z(k) - conj Z(-k))/2i, k in [0, n/2],
+// written as half[field][column][k] -- the layout of the power spectrum's
+// half spectra with the two axes swapped, which for a square grid its
+// binning pass takes as it is.
+// --------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(ColsCfg<float, L, true>::THREADS, ColsCfg<float, L, true>::MINB)
+    k_cols_spec(const C2<float>* __restrict__ in, FieldEpi<float> epi, C2<float>* __restrict__ half,
+                long long half_f0, const C2<float>* __restrict__ tw) {
+    using Cfg = ColsCfg<float, L, true>;
+    using G = typename Cfg::G;
+    constexpr int C = Cfg::C;
+    constexpr int N = L / 2;                    // survey side
+    constexpr int HN = N / 2 + 1;               // half spectrum length
+    using GF = LineGeom<float, N, 8>;           // forward lines: C lines of N points
+    static_assert(C * GF::TL == Cfg::THREADS, "forward transform must use every thread");
+    static_assert(C * GF::PADDED <= C * G::PADDED, "forward lines must fit the exchange buffer");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C2<float>* sm = reinterpret_cast<C2<float>*>(smraw);
+    const int ln = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    const long long col0 = (long long)blockIdx.x * C;
+    const long long o = blockIdx.y;
+    const C2<float>* src = in + (size_t)o * L * (size_t)N + (size_t)(col0 + ln);
+    C2<float> v[G::E];
+#pragma unroll
+    for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)N];
+    RowLayout<GF::E, GF::PADDED> lf;
+    auto sink = [&](int lnn, int p, C2<float> val) {
+        epi((int)o, (long long)p * N + col0 + lnn, val);
+        sm[lf(lnn, p)] = val;  // after the last stage's barrier: the buffer is free
+    };
+    line_fft<float, L, +1, L / 2, true>(sm, ColLayout<G::E, C>(), ln, j, v, tw, sink);
+    __syncthreads();
+    // forward transform of the C cropped columns
+    const int lineF = threadIdx.x / GF::TL, jF = threadIdx.x % GF::TL;
+    C2<float> w[GF::E];
+#pragma unroll
+    for (int q = 0; q < GF::E; ++q) w[q] = sm[lf(lineF, jF + q * (N / GF::E))];
+    auto sinkF = [&](int lnn, int p, C2<float> val) { sm[lf(lnn, p)] = val; };
+    line_fft<float, N, -1, N, true>(sm, lf, lineF, jF, w, tw, sinkF);
+    __syncthreads();
+    const long long fa = half_f0 + 2 * o, fb = fa + 1;
+    for (int t = threadIdx.x; t < C * HN; t += Cfg::THREADS) {
+        const int l = t / HN, k = t % HN;
+        const C2<float> z = sm[lf(l, k)];
+        const C2<float> zm = sm[lf(l, (N - k) & (N - 1))];
+        const size_t c = (size_t)(col0 + l);
+        half[((size_t)fa * N + c) * HN + k] = mk(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+        half[((size_t)fb * N + c) * HN + k] = mk(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+}
+
+template <int L>
+static cf_status launch_cols_spec(const C2<float>* in, int nr, const FieldEpi<float>& epi, C2<float>* half,
+                                  long long half_f0, cudaStream_t st) {
+    using Cfg = ColsCfg<float, L, true>;
+    auto kern = k_cols_spec<L>;
+    CF_TRY(prepare_smem(kern, Cfg::SMEM));
+    dim3 grid((unsigned)((L / 2) / Cfg::C), (unsigned)nr);
+    ScopedKernelTimer kt(st, epi.counts ? "icols_fields_lp_spec_f32" : "icols_fields_spec_f32", L);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(in, epi, half, half_f0, twiddles<float>());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+static cf_status launch_cols_spec_any(long long L, const C2<float>* in, int nr, const FieldEpi<float>& epi,
+                                      C2<float>* half, long long half_f0, cudaStream_t st) {
+    switch (L) {
+    case 256: return launch_cols_spec<256>(in, nr, epi, half, half_f0, st);
+    case 512: return launch_cols_spec<512>(in, nr, epi, half, half_f0, st);
+    case 1024: return launch_cols_spec<1024>(in, nr, epi, half, half_f0, st);
+    case 2048: return launch_cols_spec<2048>(in, nr, epi, half, half_f0, st);
+    case 4096: return launch_cols_spec<4096>(in, nr, epi, half, half_f0, st);
+    default: return fail(CF_ERR_UNSUPPORTED, "fused spectra need embedded sides 256..4096 (got %lld)", L);
+    }
+}
+
 // Intermediate bytes of one realization.
 static size_t per_realization_bytes(const GridInfo& g, size_t elem) {
     if (g.ndim == 1) return 0;
@@ -132,6 +217,12 @@ static size_t chunk_target_bytes() {
     }();
     return v;
 }
+
+// Spectra from the fused column pass's half spectra (cf_pk.cu).
+size_t pk_halves_acc_bytes(const cf_grid* grid, long long F, const cf_bins* bins);
+cf_status pk_from_halves_f32(const cf_grid* grid, long long F, const cf_bins* bins, const C2<float>* half,
+                             double* pk_out, int64_t* nmodes_out, double* mean, double* cov, char* acc_ws,
+                             cudaStream_t s);
 
 // Tensor-core modes (cf_tc.cu).
 cf_status tc_check_grid(const GridInfo& g);
@@ -230,10 +321,12 @@ static cf_status defer_end(const PoissonDefer& d, cudaStream_t st) {
     return CF_OK;
 }
 
+// spec_half (binary32, 2D square grids): also the first axis of the fields'
+// power spectrum, half[2R][n][n/2+1] (k_cols_spec).
 template <typename T>
 static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, int R, void* fields,
                              const cf_lp_params* lp, void* ws, size_t ws_bytes, double amp_scale,
-                             cudaStream_t st) {
+                             cudaStream_t st, C2<float>* spec_half = nullptr) {
     const GridInfo& g = e->grid;
     const size_t elem = sizeof(C2<T>);
     const int chunk = pick_chunk(g, elem, R, ws_bytes);
@@ -274,6 +367,13 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
         } else if (d == 2) {
             CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
             // pass 2: columns of [chunk][M0][N1], keep N0, fields epilogue
+            if constexpr (sizeof(T) == 4) {
+                if (spec_half) {
+                    CF_TRY(launch_cols_spec_any(g.m[0], buf1, nr, epi, spec_half, 2 * (long long)c0, st));
+                    CF_TRY(defer_end(defer, st));
+                    continue;
+                }
+            }
             CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0])));
         } else {
             CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
@@ -521,4 +621,60 @@ extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_
     }
     CF_CHECK_LAUNCH();
     return CF_OK;
+}
+
+// ------------------------------------------------------------- fused spectra
+static cf_status spectra_layout(const cf_embedding* e, int32_t R, const cf_bins* bins, cf_grid* grid, size_t* acc,
+                                size_t* half) {
+    const GridInfo& g = e->grid;
+    if (g.ndim != 2 || g.n[0] != g.n[1] || g.m[0] != 2 * g.n[0] || g.m[1] != 2 * g.n[1] || g.m[0] < 256 ||
+        g.m[0] > 4096)
+        return fail(CF_ERR_UNSUPPORTED, "fused spectra need a square 2D survey of side 128..2048 embedded in 2n");
+    if (R < 1 || 2ll * R > 65535) return fail(CF_ERR_ARG, "R must be 1..32767");
+    *grid = cf_grid{};
+    grid->ndim = 2;
+    grid->embed_factor = 2;
+    for (int a = 0; a < 2; ++a) {
+        grid->n[a] = g.n[a];
+        grid->cell[a] = g.cell[a];
+    }
+    *acc = pk_halves_acc_bytes(grid, 2ll * R, bins);
+    if (*acc == 0) return fail(CF_ERR_ARG, "invalid bins for the power spectrum");
+    *half = sizeof(C2<float>) * 2 * (size_t)R * (size_t)g.n[0] * (size_t)(g.n[1] / 2 + 1);
+    return CF_OK;
+}
+
+extern "C" cf_status cf_sample_spectra_workspace_size(const cf_embedding* e, int32_t R, const cf_bins* bins,
+                                                      size_t* pk_ws_bytes) {
+    clear_error();
+    if (!e || !bins || !pk_ws_bytes) return fail(CF_ERR_ARG, "NULL argument");
+    cf_grid grid;
+    size_t acc = 0, half = 0;
+    CF_TRY(spectra_layout(e, R, bins, &grid, &acc, &half));
+    *pk_ws_bytes = acc + half;
+    return CF_OK;
+}
+
+extern "C" cf_status cf_sample_spectra(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R, float* fields_out,
+                                       const cf_lp_params* lp, const cf_bins* bins, double* pk_out,
+                                       int64_t* nmodes_out, double* mean_or_null, double* cov_or_null, void* ws,
+                                       size_t ws_bytes, void* pk_ws, size_t pk_ws_bytes, cf_event_t sampled,
+                                       cf_stream_t s) {
+    clear_error();
+    CF_TRY(check_sample_args(e, r0, R, CF_F32));
+    if (!fields_out || !bins || !pk_out || !nmodes_out) return fail(CF_ERR_ARG, "fields, bins, pk and nmodes are required");
+    if (lp && !lp->counts_out) return fail(CF_ERR_ARG, "lp->counts_out is required");
+    if (lp && !(lp->nbar >= 0.0)) return fail(CF_ERR_ARG, "nbar must be >= 0");
+    cf_grid grid;
+    size_t acc = 0, half = 0;
+    CF_TRY(spectra_layout(e, R, bins, &grid, &acc, &half));
+    if (!pk_ws || pk_ws_bytes < acc + half)
+        return fail(CF_ERR_NOMEM, "spectra workspace of %zu bytes, %zu needed", pk_ws_bytes, acc + half);
+    const cudaStream_t st = (cudaStream_t)s;
+    CF_TRY(enter(st));
+    C2<float>* halves = (C2<float>*)((char*)pk_ws + acc);
+    CF_TRY(sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, st, halves));
+    if (sampled) CF_CUDA(cudaEventRecord((cudaEvent_t)sampled, st));
+    return pk_from_halves_f32(&grid, 2ll * R, bins, halves, pk_out, nmodes_out, mean_or_null, cov_or_null,
+                              (char*)pk_ws, st);
 }

@@ -20,7 +20,8 @@ class FieldPipeline:
     embedding is released in stream order after its last use, so replacing it
     while its sampler is still queued is safe."""
 
-    def __init__(self, wl: Workload, device="cuda:0", stream=None, R=None, with_pk=True, embed_stream=None):
+    def __init__(self, wl: Workload, device="cuda:0", stream=None, R=None, with_pk=True, embed_stream=None,
+                 fused=False):
         self.wl = wl
         self.dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
@@ -59,6 +60,15 @@ class FieldPipeline:
                 self.stream_g = torch.cuda.Stream(self.dev)
                 self.ev_sampled = torch.cuda.Event()
                 self.ev_counts_done = torch.cuda.Event()
+                self.ev_sampled.record(self.stream)  # creates the CUDA event (the fused call records it)
+        # fused=True on square 2D grids: the sampler's last pass also runs the
+        # first axis of the fields' spectra (cf_sample_spectra; measured no
+        # faster on the 512^2 workload, where the two spectra run concurrently)
+        self.fused = (fused and self.with_pk and self.dtype == cf.CF_F32 and wl.ndim == 2 and wl.n[0] == wl.n[1]
+                      and wl.factor == 2 and 128 <= wl.n[0] <= 2048)
+        if self.fused:
+            self.fused_ws_bytes = None
+            self.fused_ws = None
 
     def embed(self, xi=None):
         if self.emb is not None:
@@ -85,6 +95,16 @@ class FieldPipeline:
 
     def sample(self, r0=0):
         wl = self.wl
+        if self.fused:
+            need = cf.cf_sample_spectra_workspace_size(self.emb, self.R, self.bins)
+            if self.fused_ws is None or need > self.fused_ws_bytes:
+                self.fused_ws_bytes = need
+                self.fused_ws = torch.empty(need, dtype=torch.uint8, device=self.dev)
+            lp = cf.make_lp(wl.sigma2, wl.nbar, self.counts, wl.seed + 1000) if self.with_lp else None
+            cf.cf_sample_spectra(self.emb, wl.seed, r0, self.R, self.fields, lp, self.bins, self.pk, self.nmodes,
+                                 self.mean, self.cov, self.ws, self.ws_bytes, self.fused_ws, self.fused_ws_bytes,
+                                 self.ev_sampled if self.with_lp else None, self.stream)
+            return
         if self.with_lp:
             lp = cf.make_lp(wl.sigma2, wl.nbar, self.counts, wl.seed + 1000)
             cf.cf_sample_lp(self.emb, wl.seed, r0, self.R, self.dtype, self.fields, lp, self.ws, self.ws_bytes,
@@ -97,13 +117,15 @@ class FieldPipeline:
             return
         F = 2 * self.R
         if self.with_lp:
-            self.ev_sampled.record(self.stream)
+            if not self.fused:
+                self.ev_sampled.record(self.stream)
             self.stream_g.wait_event(self.ev_sampled)
             cf.cf_power_spectrum_counts(self.counts, None, self.grid, F, self.bins, self.pkg, self.nmodes_g,
                                         self.meang, self.covg, self.pk_ws_g, self.pk_ws_bytes, self.stream_g)
             self.ev_counts_done.record(self.stream_g)
-        cf.cf_power_spectrum(self.fields, self.dtype, self.grid, F, self.bins, self.pk, self.nmodes, self.mean,
-                             self.cov, self.pk_ws, self.pk_ws_bytes, self.stream)
+        if not self.fused:  # the fused call computed the fields' spectra
+            cf.cf_power_spectrum(self.fields, self.dtype, self.grid, F, self.bins, self.pk, self.nmodes, self.mean,
+                                 self.cov, self.pk_ws, self.pk_ws_bytes, self.stream)
         if self.with_lp:
             # the step ends on the main stream once both spectra are done (the
             # next sampling overwrites the count maps)
