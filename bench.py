@@ -52,6 +52,8 @@ def parse_args():
                    help="mock_n128 workload: realizations per method (default 2000)")
     p.add_argument("--graph", action="store_true",
                    help="time replays of a captured plan (embedding computed once, per-realization path replayed)")
+    p.add_argument("--embed-df", action="store_true",
+                   help="eigenvalues through double-float transforms (CF_EMBED_DF) instead of binary64")
     p.add_argument("--fused", action="store_true",
                    help="square 2D grids: sampler and the fields' spectra through cf_sample_spectra")
     p.add_argument("--precision", default="all", choices=["all", "f64", "f32", "bf16_tc", "f16_tc"],
@@ -799,7 +801,8 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
     if table is None:
         return None
     h_table = torch.from_numpy(np.ascontiguousarray(table)).pin_memory()
-    other = FieldPipeline(wl, pipe.dev, stream=torch.cuda.Stream(pipe.dev), fused=pipe.fused)
+    other = FieldPipeline(wl, pipe.dev, stream=torch.cuda.Stream(pipe.dev), fused=pipe.fused,
+                          embed_df=bool(pipe.flags & cf.CF_EMBED_DF))
     lanes = []
     for p in (pipe, other):
         d_table = torch.empty_like(h_table, device=p.dev)
@@ -879,7 +882,8 @@ def main():
     # embeddings on their own stream: step k+1's binary64 embedding overlaps
     # step k's sampler and spectra (every step still embeds, samples and
     # computes its spectra; the timed region covers all of it)
-    pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev), fused=args.fused)
+    pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev), fused=args.fused,
+                         embed_df=args.embed_df)
     R = pipe.R
 
     def barrier():
@@ -943,7 +947,8 @@ def main():
                        "l2": "each step writes %d MiB of fields and counts (> 129 MB L2)"
                              % (2 * pipe.cells_per_step * 4 >> 20),
                        "parallelism": "replicas x%d" % world, "tuned_chunk": tuned,
-                       "fused_spectra": bool(pipe.fused)},
+                       "fused_spectra": bool(pipe.fused), "eigenvalue_transforms": "double-float" if args.embed_df
+                       else "binary64"},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report, "cufft_reference": cufft,

@@ -120,6 +120,14 @@ typedef struct {
 /* cf_embed flags */
 #define CF_EMBED_CLAMP 1u        /* set eigenvalues < -tau to zero instead of failing */
 #define CF_EMBED_SKIP_ERROR 2u   /* with CF_EMBED_CLAMP: skip the covariance-error pass */
+#define CF_EMBED_DF 8u           /* parametric xi: the transforms of the eigenvalues and of
+                                    the covariance-error pass run in double-float arithmetic
+                                    (pairs of binary32, about 48 bits): eigenvalues within
+                                    about 1e-14 lambda_max of binary64 ones (inside the 1e-12
+                                    tolerance), several times faster on this GPU, whose
+                                    binary64 rate is low.  For binary32 and lower-precision
+                                    fields; binary64 fields want the default binary64
+                                    transforms (their tolerance is 1e-10 on the fields) */
 #define CF_EMBED_LOG1P 4u        /* xi is the correlation function of the lognormal
                                     density delta; the Gaussian covariance embedded is
                                     ln(1 + xi) (section 3.1, eq. (Lncov)).  xi must stay

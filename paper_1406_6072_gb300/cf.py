@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "CF_OK", 1: "CF_ERR_ARG", 2: "CF_ERR_NOT_PSD", 3: "CF_ERR_NOM
                 8: "CF_ERR_NOT_FOUND"}
 CF_F64, CF_F32, CF_BF16_TC, CF_F16_TC = 0, 1, 2, 3
 CF_XI_GAUSSIAN, CF_XI_GEN_CAUCHY, CF_XI_EXPONENTIAL, CF_XI_TABLE = 0, 1, 2, 3
-CF_EMBED_CLAMP, CF_EMBED_SKIP_ERROR, CF_EMBED_LOG1P = 1, 2, 4
+CF_EMBED_CLAMP, CF_EMBED_SKIP_ERROR, CF_EMBED_LOG1P, CF_EMBED_DF = 1, 2, 4, 8
 CF_BINS_LINEAR, CF_BINS_LOG, CF_BINS_EDGES = 0, 1, 2
 
 

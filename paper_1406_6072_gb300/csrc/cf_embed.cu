@@ -2,8 +2,10 @@
 // binary64 eigenvalues and the positivity check (section 2, eqs. (grid),
 // (Specd), (condition)).
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
-#include "cf_kernels.cuh"
+#include "cf_df.cuh"
 
 namespace cf {
 
@@ -271,15 +273,27 @@ __global__ void k_lambda_plus_complex(const double* __restrict__ lam, double tau
 // complex line and read back as Re and Im, and along the last axis only the
 // non-redundant half k <= M/2 is kept; the full result is mirrored at the end.
 // ---------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(RowsCfg<double, L>::THREADS, RowsCfg<double, L>::MINB)
-    k_even_rows(const double* __restrict__ in, long long nrows, double* __restrict__ out,
-                const C2<double>* __restrict__ tw) {
-    using Cfg = RowsCfg<double, L>;
+// S: the arithmetic of the transforms, binary64 or double-float (DF); the
+// input x and the output are binary64, the scratch `half` holds S values.
+template <typename S>
+__device__ __forceinline__ S to_s(double d) {
+    if constexpr (sizeof(S) == 8 && __is_same(S, double)) return d;
+    else return df_from(d);
+}
+template <typename S>
+__device__ __forceinline__ double from_s(S v) {
+    if constexpr (__is_same(S, double)) return v;
+    else return df_to(v);
+}
+
+template <typename S, int L>
+__global__ void __launch_bounds__(RowsCfg<S, L>::THREADS, RowsCfg<S, L>::MINB)
+    k_even_rows(const double* __restrict__ in, long long nrows, S* __restrict__ out, const C2<S>* __restrict__ tw) {
+    using Cfg = RowsCfg<S, L>;
     using G = typename Cfg::G;
     constexpr int H = L / 2 + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2<double>* sm = reinterpret_cast<C2<double>*>(smraw);
+    C2<S>* sm = reinterpret_cast<C2<S>*>(smraw);
     const int line = threadIdx.x / G::TL;
     const int j = threadIdx.x % G::TL;
     const long long pair = (long long)blockIdx.x * Cfg::ROWS + line;
@@ -288,29 +302,29 @@ __global__ void __launch_bounds__(RowsCfg<double, L>::THREADS, RowsCfg<double, L
     const bool hasb = rb < nrows;
     const double* a = in + (size_t)(valid ? ra : 0) * L;
     const double* b = in + (size_t)(hasb ? rb : 0) * L;
-    C2<double> v[G::E];
+    C2<S> v[G::E];
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
         const int x = j + q * (L / G::E);
-        v[q] = mk(a[x], hasb ? b[x] : 0.0);
+        v[q] = mk(to_s<S>(a[x]), to_s<S>(hasb ? b[x] : 0.0));
     }
-    auto sink = [&](int, int k, C2<double> val) {
+    auto sink = [&](int, int k, C2<S> val) {
         if (!valid || k >= H) return;
         out[(size_t)ra * H + k] = val.x;
         if (hasb) out[(size_t)rb * H + k] = val.y;
     };
-    line_fft<double, L, -1, L>(sm, RowLayout<G::E, G::PADDED>(), line, j, v, tw, sink);
+    line_fft<S, L, -1, L>(sm, RowLayout<G::E, G::PADDED>(), line, j, v, tw, sink);
 }
 
 // Columns of in[outer][L][inner] in pairs (i, i+1): out has the same layout
 // (in place allowed).
-template <int L>
-__global__ void __launch_bounds__(ColsCfg<double, L>::THREADS, ColsCfg<double, L>::MINB)
-    k_even_cols(const double* in, long long inner, double* out, const C2<double>* __restrict__ tw) {
-    using Cfg = ColsCfg<double, L>;
+template <typename S, int L>
+__global__ void __launch_bounds__(ColsCfg<S, L>::THREADS, ColsCfg<S, L>::MINB)
+    k_even_cols(const S* in, long long inner, S* out, const C2<S>* __restrict__ tw) {
+    using Cfg = ColsCfg<S, L>;
     using G = typename Cfg::G;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C2<double>* sm = reinterpret_cast<C2<double>*>(smraw);
+    C2<S>* sm = reinterpret_cast<C2<S>*>(smraw);
     const int ln = threadIdx.x % Cfg::C;
     const int j = threadIdx.x / Cfg::C;
     const long long ia = 2 * ((long long)blockIdx.x * Cfg::C + ln), ib = ia + 1;
@@ -318,23 +332,26 @@ __global__ void __launch_bounds__(ColsCfg<double, L>::THREADS, ColsCfg<double, L
     const bool valid = ia < inner;
     const bool hasb = ib < inner;
     const size_t base = (size_t)o * L * (size_t)inner;
-    C2<double> v[G::E];
+    const S zero = to_s<S>(0.0);
+    C2<S> v[G::E];
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
         const size_t row = base + (size_t)(j + q * (L / G::E)) * (size_t)inner;
-        v[q] = mk(valid ? in[row + ia] : 0.0, hasb ? in[row + ib] : 0.0);
+        v[q] = mk(valid ? in[row + ia] : zero, hasb ? in[row + ib] : zero);
     }
-    auto sink = [&](int, int p, C2<double> val) {
+    auto sink = [&](int, int p, C2<S> val) {
         if (!valid) return;
         const size_t row = base + (size_t)p * (size_t)inner;
         out[row + ia] = val.x;
         if (hasb) out[row + ib] = val.y;
     };
-    line_fft<double, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+    line_fft<S, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
 }
 
-// full[rows][M] from half[rows][M/2+1] of an even last axis, times scale
-__global__ void k_even_mirror(const double* __restrict__ half, long long rows, long long M, double scale,
+// full[rows][M] from half[rows][M/2+1] of an even last axis, times scale (a
+// power of two)
+template <typename S>
+__global__ void k_even_mirror(const S* __restrict__ half, long long rows, long long M, double scale,
                               double* __restrict__ full) {
     const long long H = M / 2 + 1;
     const long long total = rows * M;
@@ -342,7 +359,7 @@ __global__ void k_even_mirror(const double* __restrict__ half, long long rows, l
          t += (long long)gridDim.x * blockDim.x) {
         const long long r = t / M, k = t - r * M;
         const long long kk = k < H ? k : M - k;
-        full[t] = half[r * H + kk] * scale;
+        full[t] = from_s<S>(half[r * H + kk]) * scale;
     }
 }
 
@@ -357,53 +374,64 @@ __global__ void k_lambda_plus_real(const double* __restrict__ lam, const struct 
     }
 }
 
-template <int L>
-static cf_status launch_even_rows(const double* in, long long nrows, double* out, cudaStream_t s) {
-    using Cfg = RowsCfg<double, L>;
-    auto kern = k_even_rows<L>;
+template <typename S, int L>
+static cf_status launch_even_rows(const double* in, long long nrows, S* out, cudaStream_t s) {
+    using Cfg = RowsCfg<S, L>;
+    auto kern = k_even_rows<S, L>;
     CF_TRY(prepare_smem(kern, Cfg::SMEM));
     const long long pairs = (nrows + 1) / 2;
-    ScopedKernelTimer kt(s, "even_rows_f64", L);
+    ScopedKernelTimer kt(s, sizeof(S) == 8 && __is_same(S, double) ? "even_rows_f64" : "even_rows_df", L);
     kern<<<(unsigned)((pairs + Cfg::ROWS - 1) / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, s>>>(in, nrows, out,
-                                                                                     twiddles<double>());
+                                                                                     twiddles<S>());
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
 
-template <int L>
-static cf_status launch_even_cols(double* data, long long outer, long long inner, cudaStream_t s) {
-    using Cfg = ColsCfg<double, L>;
-    auto kern = k_even_cols<L>;
+template <typename S, int L>
+static cf_status launch_even_cols(S* data, long long outer, long long inner, cudaStream_t s) {
+    using Cfg = ColsCfg<S, L>;
+    auto kern = k_even_cols<S, L>;
     CF_TRY(prepare_smem(kern, Cfg::SMEM));
     if (outer > 65535) return fail(CF_ERR_UNSUPPORTED, "even transform with %lld outer slices", outer);
     const long long pairs = (inner + 1) / 2;
     dim3 grid((unsigned)((pairs + Cfg::C - 1) / Cfg::C), (unsigned)outer);
-    ScopedKernelTimer kt(s, "even_cols_f64", L);
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(data, inner, data, twiddles<double>());
+    ScopedKernelTimer kt(s, __is_same(S, double) ? "even_cols_f64" : "even_cols_df", L);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(data, inner, data, twiddles<S>());
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
 
 // full = scale * DFT(x) for x real and even along every axis; half is scratch
-// of (mtotal / M_last) * (M_last/2 + 1) doubles.
-static cf_status even_dft(const double* x, const GridInfo& g, double scale, double* half, double* full,
-                          cudaStream_t s) {
+// of (mtotal / M_last) * (M_last/2 + 1) values of 8 bytes.  The transforms run
+// in binary64, or with CF_EMBED_DF in double-float arithmetic (cf_df.cuh).
+template <typename S>
+static cf_status even_dft_t(const double* x, const GridInfo& g, double scale, S* half, double* full,
+                            cudaStream_t s) {
     const int d = g.ndim;
     const long long Ml = g.m[d - 1];
     const long long H = Ml / 2 + 1;
     const long long rows = g.mtotal / Ml;
-    CF_TRY(dispatch_line(Ml, [&](auto Lc) -> cf_status { return launch_even_rows<decltype(Lc)::value>(x, rows, half, s); }));
+    CF_TRY(dispatch_line(Ml, [&](auto Lc) -> cf_status {
+        return launch_even_rows<S, decltype(Lc)::value>(x, rows, half, s);
+    }));
     for (int a = d - 2; a >= 0; --a) {
         long long inner = H, outer = 1;
         for (int b2 = a + 1; b2 < d - 1; ++b2) inner *= g.m[b2];
         for (int b2 = 0; b2 < a; ++b2) outer *= g.m[b2];
         CF_TRY(dispatch_line(g.m[a], [&](auto Lc) -> cf_status {
-            return launch_even_cols<decltype(Lc)::value>(half, outer, inner, s);
+            return launch_even_cols<S, decltype(Lc)::value>(half, outer, inner, s);
         }));
     }
-    k_even_mirror<<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
+    k_even_mirror<S><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
     CF_CHECK_LAUNCH();
     return CF_OK;
+}
+
+static cf_status even_dft(const double* x, const GridInfo& g, double scale, double* half, double* full,
+                          uint32_t flags, cudaStream_t s) {
+    if (!(flags & CF_EMBED_DF)) return even_dft_t<double>(x, g, scale, half, full, s);
+    static_assert(sizeof(DF) == sizeof(double), "the scratch holds 8-byte values");
+    return even_dft_t<DF>(x, g, scale, reinterpret_cast<DF*>(half), full, s);
 }
 
 // Device buffers of one embedding computation.
@@ -470,7 +498,7 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
         CF_CHECK_LAUNCH();
         if (even) {
             // lambda+ is real and even: its inverse transform equals its forward one
-            CF_TRY(even_dft(buf, gi, 1.0 / (double)total, buf + total, buf, s));
+            CF_TRY(even_dft(buf, gi, 1.0 / (double)total, buf + total, buf, flags, s));
             ScopedKernelTimer kt(s, "embed_cov_error");
             k_cov_error_partial_real<<<blocks, kRedThreads, 0, s>>>(buf, sc.c, gi, sc.part);
         } else {
@@ -576,7 +604,7 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
     if (xi->kind != CF_XI_TABLE) {
         // the row depends on |lag| only: even along every axis
         double* full = (double*)sc.z;
-        CF_TRY(even_dft(sc.c, gi, 1.0, full + gi.mtotal, full, sc.s));
+        CF_TRY(even_dft(sc.c, gi, 1.0, full + gi.mtotal, full, flags, sc.s));
         return finish_embedding(gi, sc, flags, full, true, out, rep);
     }
     CF_TRY((fft_nd_inplace<double, -1>(sc.z, gi, sc.s)));
@@ -669,7 +697,7 @@ extern "C" cf_status cf_embed_periodic(const cf_grid* g, const cf_xi* xi, int32_
         }
         CF_CHECK_LAUNCH();
         double* full = (double*)bs.z;
-        CF_TRY(even_dft(bs.c, gb, 1.0, full + gb.mtotal, full, s));
+        CF_TRY(even_dft(bs.c, gb, 1.0, full + gb.mtotal, full, flags, s));
         double scale = 1.0;
         for (int a = 0; a < gs.ndim; ++a) scale /= (double)resolution;
         if (box_factor == 1) scale *= (double)(1 << gs.ndim);

@@ -7,7 +7,7 @@
 #include <mutex>
 #include <string>
 
-#include "cf_fft.cuh"
+#include "cf_df.cuh"
 #include "cf_internal.h"
 
 namespace cf {
@@ -29,14 +29,16 @@ void clear_error() { g_last_error.clear(); }
 // Twiddle tables, one copy per device that loads the library.
 __device__ C2<float> g_tw32[TWN];
 __device__ C2<double> g_tw64[TWN];
+__device__ C2<DF> g_twdf[TWN];
 
-__global__ void k_init_twiddles(C2<float>* tw32, C2<double>* tw64) {
+__global__ void k_init_twiddles(C2<float>* tw32, C2<double>* tw64, C2<DF>* twdf) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= TWN) return;
     double s, c;
     sincospi(2.0 * (double)j / (double)TWN, &s, &c);
     tw64[j] = mk(c, s);
     tw32[j] = mk((float)c, (float)s);
+    twdf[j] = mk(df_from(c), df_from(s));
 }
 
 static constexpr int kMaxDevices = 64;
@@ -44,6 +46,7 @@ static std::mutex g_init_mu;
 static bool g_inited[kMaxDevices];
 static C2<float>* g_tw32_ptr[kMaxDevices];
 static C2<double>* g_tw64_ptr[kMaxDevices];
+static C2<DF>* g_twdf_ptr[kMaxDevices];
 // Library memory pool per device: stream-ordered allocations of embeddings,
 // scratch and served results.  Freed blocks stay in the pool (release
 // threshold: unlimited), so that repeated embeddings do not map and unmap
@@ -64,13 +67,16 @@ cf_status ensure_device_init() {
     if (g_inited[dev]) return CF_OK;
     void* p32 = nullptr;
     void* p64 = nullptr;
+    void* pdf = nullptr;
     CF_CUDA(cudaGetSymbolAddress(&p32, g_tw32));
     CF_CUDA(cudaGetSymbolAddress(&p64, g_tw64));
-    k_init_twiddles<<<(TWN + 255) / 256, 256>>>((C2<float>*)p32, (C2<double>*)p64);
+    CF_CUDA(cudaGetSymbolAddress(&pdf, g_twdf));
+    k_init_twiddles<<<(TWN + 255) / 256, 256>>>((C2<float>*)p32, (C2<double>*)p64, (C2<DF>*)pdf);
     CF_CHECK_LAUNCH();
     CF_CUDA(cudaDeviceSynchronize());
     g_tw32_ptr[dev] = (C2<float>*)p32;
     g_tw64_ptr[dev] = (C2<double>*)p64;
+    g_twdf_ptr[dev] = (C2<DF>*)pdf;
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -167,6 +173,7 @@ cf_status enter(cudaStream_t s) {
 
 const C2<float>* twiddles_f32() { return g_tw32_ptr[current_device()]; }
 const C2<double>* twiddles_f64() { return g_tw64_ptr[current_device()]; }
+const C2<DF>* twiddles_df() { return g_twdf_ptr[current_device()]; }
 
 cf_status check_grid(const cf_grid* g, GridInfo* gi) {
     if (!g) return fail(CF_ERR_ARG, "grid is NULL");

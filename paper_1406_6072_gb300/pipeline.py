@@ -21,7 +21,7 @@ class FieldPipeline:
     while its sampler is still queued is safe."""
 
     def __init__(self, wl: Workload, device="cuda:0", stream=None, R=None, with_pk=True, embed_stream=None,
-                 fused=False):
+                 fused=False, embed_df=False):
         self.wl = wl
         self.dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
@@ -31,7 +31,7 @@ class FieldPipeline:
         self.tdtype = torch.float32 if wl.dtype == "f32" else torch.float64
         self.grid = cf.make_grid(wl.n, wl.cell[: wl.ndim], wl.factor)
         self.xi = cf.make_xi(wl.xi_kind, wl.amp, wl.scale, wl.beta)
-        self.flags = cf.CF_EMBED_CLAMP if wl.clamp else 0
+        self.flags = (cf.CF_EMBED_CLAMP if wl.clamp else 0) | (cf.CF_EMBED_DF if embed_df else 0)
         self.with_lp = wl.nbar is not None and self.dtype == cf.CF_F32
         self.with_pk = with_pk and wl.nbins is not None
         F = 2 * self.R

@@ -430,3 +430,31 @@ def test_workspace_of_the_reported_size_takes_one_chunk():
     assert launches.get("sample_rows_f32") == 1 and launches.get("icols_fields_lp_f32") == 1, launches
     assert launches.get("poisson_fixup") == 1, launches
     emb.close()
+
+
+@pytest.mark.parametrize("n,kind,amp,scale,beta,clamp", [((512, 512), 1, 0.8, 8.0, 0.4, True),
+                                                         ((64, 64), 0, 1.0, 4.0, 0.0, False),
+                                                         ((128, 128, 128), 2, 1.0, 6.0, 0.0, False),
+                                                         ((16, 32), 2, 1.3, 1.5, 0.0, False)])
+def test_double_float_embedding(orc, n, kind, amp, scale, beta, clamp):
+    """CF_EMBED_DF: eigenvalues through double-float transforms within the
+    1e-12 lambda_max gate of the oracle's binary64 ones, the same threshold
+    decisions, and binary32 fields within the binary32 gate end to end."""
+    o = orc.embed(list(n), kind, amp, scale, beta, clamp=clamp)
+    flags = cf.CF_EMBED_DF | (cf.CF_EMBED_CLAMP if clamp else 0)
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(kind, amp, scale, beta), flags)
+    lam = torch.empty(o["lambda"].shape, dtype=torch.float64, device=DEV)
+    cf.cf_embedding_lambda(emb, lam)
+    torch.cuda.synchronize()
+    lmax = o["lambda"].max()
+    err = float(np.max(np.abs(lam.cpu().numpy() - o["lambda"])) / lmax)
+    print("double-float eigenvalues: max error %.2e lambda_max" % err)
+    assert err <= 1e-12
+    assert emb.report["n_negative"] == o["report"]["n_negative"]
+    if o["report"]["clamped"]:
+        assert emb.report["cov_error"] == pytest.approx(o["report"]["cov_error"], rel=1e-6, abs=1e-13)
+    R = 2
+    got = _fields(emb, 91, 4, R, cf.CF_F32, n).double().cpu().numpy()
+    ref = orc.sample(n, o["sqrt_lambda"], 91, 4, R, 1)
+    assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
+    emb.close()
