@@ -52,6 +52,9 @@ def parse_args():
                    help="mock_n128 workload: realizations per method (default 2000)")
     p.add_argument("--graph", action="store_true",
                    help="time replays of a captured plan (embedding computed once, per-realization path replayed)")
+    p.add_argument("--lanes", type=int, default=1,
+                   help="pipelines that alternate steps (own buffers and streams), so that one step's "
+                        "sampler overlaps the previous step's spectra")
     p.add_argument("--embed-df", action="store_true",
                    help="eigenvalues through double-float transforms (CF_EMBED_DF) instead of binary64")
     p.add_argument("--fused", action="store_true",
@@ -885,6 +888,16 @@ def main():
     pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev), fused=args.fused,
                          embed_df=args.embed_df)
     R = pipe.R
+    # lanes: step k runs on pipeline k % lanes (its own fields, counts,
+    # workspaces and streams), so that step k+1's sampler overlaps step k's
+    # spectra; every step still embeds, samples and computes both spectra
+    lanes = [pipe] + [FieldPipeline(wl, dev, stream=torch.cuda.Stream(dev), embed_stream=torch.cuda.Stream(dev),
+                                    fused=args.fused, embed_df=args.embed_df) for _ in range(max(1, args.lanes) - 1)]
+
+    def run_step(k):
+        ln = lanes[k % len(lanes)]
+        with torch.cuda.stream(ln.stream):
+            ln.step(r0=replicas.realization_start(rank, world, k, R))
 
     def barrier():
         if dist is not None:
@@ -898,7 +911,7 @@ def main():
             tuned = {"chunk": chunk, "ms_per_realization": tms}
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
-            pipe.step(r0=replicas.realization_start(rank, world, k, R))
+            run_step(k)
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
@@ -908,14 +921,22 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        for ln in lanes[1:]:
+            ln.stream.wait_event(e0)
         for k in range(args.steps):
-            pipe.step(r0=replicas.realization_start(rank, world, args.warmup + k, R))
+            run_step(args.warmup + k)
+        for ln in lanes[1:]:  # the timed region ends when every lane is done
+            done = torch.cuda.Event()
+            done.record(ln.stream)
+            stream.wait_event(done)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         timing = cf.cf_kernel_timing_read()
         cf.cf_kernel_timing(0)
         clk = clocks.stop()
+    for ln in lanes[1:]:
+        ln.close()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = replicas.max_over_ranks(ms, dist, dev)
     cells_all = pipe.cells_per_step * world
@@ -948,7 +969,7 @@ def main():
                              % (2 * pipe.cells_per_step * 4 >> 20),
                        "parallelism": "replicas x%d" % world, "tuned_chunk": tuned,
                        "fused_spectra": bool(pipe.fused), "eigenvalue_transforms": "double-float" if args.embed_df
-                       else "binary64"},
+                       else "binary64", "lanes": len(lanes)},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report, "cufft_reference": cufft,

@@ -49,7 +49,7 @@ __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, doubl
                     const long long m2 = a2 ? g.m[2] - l2 : l2;
                     const long long idx = (m0 * g.m[1] + m1) * g.m[2] + m2;
                     c[idx] = v;
-                    z[idx] = mk(v, 0.0);
+                    if (z) z[idx] = mk(v, 0.0);
                 }
             }
         }
@@ -112,16 +112,29 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// Order-preserving integer key of a binary64 value (not NaN): the signed
+// comparison of keys is the comparison of the values, so minima, maxima and
+// threshold tests run on the integer pipes (binary64 throughput is low on
+// this GPU).  The map is an involution.
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double key_value(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffll));
+}
+
 __global__ void __launch_bounds__(kRedThreads)
     k_minmax_partial(const double* __restrict__ lam, long long total, double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
-    double mn = INFINITY, mx = -INFINITY;
+    long long kmn = 0x7fffffffffffffffll, kmx = -0x7fffffffffffffffll - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const double l = lam[i];
-        mn = fmin(mn, l);
-        mx = fmax(mx, l);
+        const long long k = order_key(lam[i]);
+        kmn = k < kmn ? k : kmn;
+        kmx = k > kmx ? k : kmx;
     }
+    double mn = key_value(kmn), mx = key_value(kmx);
     mn = block_min(mn, sh);
     mx = block_max(mx, sh);
     if (threadIdx.x == 0) {
@@ -162,23 +175,23 @@ __global__ void __launch_bounds__(kRedThreads)
                 unsigned long long* __restrict__ counts) {
     __shared__ double sh[kRedThreads];
     const double tau = st->tau;
+    const long long ktau = order_key(tau), kntau = order_key(-tau);
     double neg = 0.0;
     unsigned long long nneg = 0, nzero = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const double l = lam[i];
-        double lp;
-        if (l > tau) {
-            lp = l;
-        } else if (l >= -tau) {
-            lp = 0.0;
+        const long long k = order_key(l);
+        float sv = 0.0f;
+        if (k > ktau) {  // l > tau
+            sv = sqrtf((float)(l * inv_total));
+        } else if (k >= kntau) {  // -tau <= l <= tau
             ++nzero;
         } else {
-            lp = 0.0;
             ++nneg;
             neg += -l;
         }
-        s32[i] = sqrtf((float)(lp * inv_total));
+        s32[i] = sv;
     }
     neg = block_sum(neg, sh);
     // counts are exact in binary64 (< 2^53): reduce per block, one atomic each
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(ColsCfg<S, L>::THREADS, ColsCfg<S, L>::MINB)
 
 // full[rows][M] from half[rows][M/2+1] of an even last axis, times scale (a
 // power of two)
-template <typename S>
+template <typename S, bool SCALE>
 __global__ void k_even_mirror(const S* __restrict__ half, long long rows, long long M, double scale,
                               double* __restrict__ full) {
     const long long H = M / 2 + 1;
@@ -359,7 +372,8 @@ __global__ void k_even_mirror(const S* __restrict__ half, long long rows, long l
          t += (long long)gridDim.x * blockDim.x) {
         const long long r = t / M, k = t - r * M;
         const long long kk = k < H ? k : M - k;
-        full[t] = from_s<S>(half[r * H + kk]) * scale;
+        const double v = from_s<S>(half[r * H + kk]);
+        full[t] = SCALE ? v * scale : v;
     }
 }
 
@@ -422,7 +436,10 @@ static cf_status even_dft_t(const double* x, const GridInfo& g, double scale, S*
             return launch_even_cols<S, decltype(Lc)::value>(half, outer, inner, s);
         }));
     }
-    k_even_mirror<S><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
+    if (scale == 1.0)
+        k_even_mirror<S, false><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
+    else
+        k_even_mirror<S, true><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
@@ -597,8 +614,10 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
     } else {
         if (log1p_xi && !(xi->amp > -1.0)) return fail(CF_ERR_ARG, "CF_EMBED_LOG1P needs amp > -1");
         ScopedKernelTimer kt(sc.s, "embed_fill");
+        // the row is even: its transform goes through even_dft, which needs
+        // no complex copy of it
         k_fill_row<<<blocks, kRedThreads, 0, sc.s>>>(gi, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi, sc.c,
-                                                     sc.z);
+                                                     nullptr);
     }
     CF_CHECK_LAUNCH();
     if (xi->kind != CF_XI_TABLE) {
@@ -693,7 +712,7 @@ extern "C" cf_status cf_embed_periodic(const cf_grid* g, const cf_xi* xi, int32_
         {
             ScopedKernelTimer kt(s, "embed_fill");
             k_fill_row<<<blocks, kRedThreads, 0, s>>>(gb, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi, bs.c,
-                                                      bs.z);
+                                                      nullptr);
         }
         CF_CHECK_LAUNCH();
         double* full = (double*)bs.z;
