@@ -14,8 +14,31 @@ namespace cf {
 // -n..n-1).  xi depends on |lag_i| only, so one thread evaluates xi once per
 // point of [0, M_0/2] x ... and writes it to the 2^d mirror positions m_i = l_i
 // and M_i - l_i (one position when l_i is 0 or M_i/2).
+__device__ __forceinline__ double xi_value(int kind, double amp, double scale, double beta, int log1p_xi,
+                                           double r2) {
+    double v;
+    if (kind == CF_XI_GAUSSIAN)
+        v = amp * exp(-r2 / (2.0 * scale * scale));
+    else if (kind == CF_XI_GEN_CAUCHY)
+        v = amp * pow(1.0 + r2 / (scale * scale), -beta);
+    else
+        v = amp * exp(-sqrt(r2) / scale);
+    if (log1p_xi) v = log1p(v);  // eq. (Lncov): Gaussian covariance from the density correlation
+    return v;
+}
+
+// With equal cell sides h, r^2 = h^2 (l_0^2 + l_1^2 + l_2^2): xi of every
+// integer k = sum l_a^2 once (the same binary64 value as the direct
+// evaluation when h = 1), which in 3D is far fewer evaluations than lags.
+__global__ void k_xi_by_k(int kind, double amp, double scale, double beta, int log1p_xi, double h2, long long kmax,
+                          double* __restrict__ tab) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k <= kmax;
+         k += (long long)gridDim.x * blockDim.x)
+        tab[k] = xi_value(kind, amp, scale, beta, log1p_xi, (double)k * h2);
+}
+
 __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, double beta, int log1p_xi,
-                           double* __restrict__ c, C2<double>* __restrict__ z) {
+                           const double* __restrict__ tab, double* __restrict__ c, C2<double>* __restrict__ z) {
     const long long h0 = g.m[0] / 2, h1 = g.m[1] / 2, h2 = g.m[2] / 2;
     const long long q0 = h0 + 1, q1 = g.ndim > 1 ? h1 + 1 : 1, q2 = g.ndim > 2 ? h2 + 1 : 1;
     const long long total = q0 * q1 * q2;
@@ -23,19 +46,17 @@ __global__ void k_fill_row(GridInfo g, int kind, double amp, double scale, doubl
          t += (long long)gridDim.x * blockDim.x) {
         const long long l2 = t % q2, l1 = (t / q2) % q1, l0 = t / (q1 * q2);
         const long long l[3] = {l0, l1, l2};
-        double r2 = 0.0;
-        for (int a = 0; a < g.ndim; ++a) {
-            const double x = (double)l[a] * g.cell[a];
-            r2 += x * x;
-        }
         double v;
-        if (kind == CF_XI_GAUSSIAN)
-            v = amp * exp(-r2 / (2.0 * scale * scale));
-        else if (kind == CF_XI_GEN_CAUCHY)
-            v = amp * pow(1.0 + r2 / (scale * scale), -beta);
-        else
-            v = amp * exp(-sqrt(r2) / scale);
-        if (log1p_xi) v = log1p(v);  // eq. (Lncov): Gaussian covariance from the density correlation
+        if (tab) {
+            v = tab[l0 * l0 + l1 * l1 + l2 * l2];
+        } else {
+            double r2 = 0.0;
+            for (int a = 0; a < g.ndim; ++a) {
+                const double x = (double)l[a] * g.cell[a];
+                r2 += x * x;
+            }
+            v = xi_value(kind, amp, scale, beta, log1p_xi, r2);
+        }
         // mirror positions
         const int na = g.ndim;
         const int nm0 = (l0 == 0 || l0 == h0) ? 1 : 2;
@@ -451,6 +472,31 @@ static cf_status even_dft(const double* x, const GridInfo& g, double scale, doub
     return even_dft_t<DF>(x, g, scale, reinterpret_cast<DF*>(half), full, s);
 }
 
+// c (the even row of a parametric xi) on the device: through a table of xi
+// by k = sum l_a^2 when the cell sides are equal and the table is smaller
+// than a quarter of the lags.
+static cf_status fill_even_row(const GridInfo& g, const cf_xi* xi, int log1p_xi, double* c, cudaStream_t s) {
+    long long kmax = 0, lags = 1;
+    bool equal = true;
+    for (int a = 0; a < g.ndim; ++a) {
+        kmax += (g.m[a] / 2) * (g.m[a] / 2);
+        lags *= g.m[a] / 2 + 1;
+        equal = equal && g.cell[a] == g.cell[0];
+    }
+    double* tab = nullptr;
+    if (equal && 4 * (kmax + 1) < lags) {
+        if (pool_malloc((void**)&tab, sizeof(double) * (size_t)(kmax + 1), s) != cudaSuccess)
+            return fail(CF_ERR_NOMEM, "xi table allocation failed");
+        k_xi_by_k<<<grid_blocks(kmax + 1, 256, 1024), 256, 0, s>>>(xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi,
+                                                                  g.cell[0] * g.cell[0], kmax, tab);
+    }
+    k_fill_row<<<grid_blocks(lags, 256, 4096), 256, 0, s>>>(g, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi,
+                                                            tab, c, nullptr);
+    if (tab) cudaFreeAsync(tab, s);
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
 // Device buffers of one embedding computation.
 struct EmbedScratch {
     C2<double>* z = nullptr;
@@ -616,8 +662,7 @@ extern "C" cf_status cf_embed(const cf_grid* g, const cf_xi* xi, uint32_t flags,
         ScopedKernelTimer kt(sc.s, "embed_fill");
         // the row is even: its transform goes through even_dft, which needs
         // no complex copy of it
-        k_fill_row<<<blocks, kRedThreads, 0, sc.s>>>(gi, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi, sc.c,
-                                                     nullptr);
+        CF_TRY(fill_even_row(gi, xi, log1p_xi, sc.c, sc.s));
     }
     CF_CHECK_LAUNCH();
     if (xi->kind != CF_XI_TABLE) {
@@ -711,8 +756,7 @@ extern "C" cf_status cf_embed_periodic(const cf_grid* g, const cf_xi* xi, int32_
         const int blocks = grid_blocks(gb.mtotal, kRedThreads, kRedBlocks);
         {
             ScopedKernelTimer kt(s, "embed_fill");
-            k_fill_row<<<blocks, kRedThreads, 0, s>>>(gb, xi->kind, xi->amp, xi->scale, xi->beta, log1p_xi, bs.c,
-                                                      nullptr);
+            CF_TRY(fill_even_row(gb, xi, log1p_xi, bs.c, s));
         }
         CF_CHECK_LAUNCH();
         double* full = (double*)bs.z;
