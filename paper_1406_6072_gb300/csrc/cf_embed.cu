@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(RowsCfg<S, L>::THREADS, RowsCfg<S, L>::MINB)
         out[(size_t)ra * H + k] = val.x;
         if (hasb) out[(size_t)rb * H + k] = val.y;
     };
-    line_fft<S, L, -1, L>(sm, RowLayout<G::E, G::PADDED>(), line, j, v, tw, sink);
+    line_fft<S, L, -1, L>(sm, RowLayout<G::PADE, G::PADDED>(), line, j, v, tw, sink);
 }
 
 // Columns of in[outer][L][inner] in pairs (i, i+1): out has the same layout

@@ -42,7 +42,12 @@ template <typename T, int L, int EMAX = FftE<T>::value>
 struct LineGeom {
     static constexpr int E = L < EMAX ? L : EMAX;  // points per thread
     static constexpr int TL = L / E;               // threads per line
-    static constexpr int PADDED = L + L / E;       // padded line length
+    static constexpr int PADDED = L + L / E;       // padded line length (line stride)
+    // padding granularity of the row layout: one slot per E points, except
+    // one per 16 for 8-byte elements with E = 8 (there a slot per 8 points
+    // shifts 16 consecutive lanes over 17 slots and every contiguous access
+    // of a warp takes 3 shared-memory wavefronts instead of 2)
+    static constexpr int PADE = (sizeof(T) == 4 && E == 8) ? 16 : E;
 };
 
 // padded shared-memory slot of point p

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(RowsCfg<T, L>::THREADS, RowsCfg<T, L>::MINB)
     auto sink = [&](int, int p, C2<T> val) {
         if (valid) base[p] = val;
     };
-    line_fft<T, L, SIGN, L>(sm, RowLayout<G::E, G::PADDED>(), line, j, v, tw, sink);
+    line_fft<T, L, SIGN, L>(sm, RowLayout<G::PADE, G::PADDED>(), line, j, v, tw, sink);
 }
 
 // --------------------------------------------------------------------------

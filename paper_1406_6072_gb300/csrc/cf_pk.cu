@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
             }
         }
     }
-    RowLayout<E, G::PADDED> lay;
+    RowLayout<G::PADE, G::PADDED> lay;
     // the spectrum of the line goes back into the exchange buffer
     auto sink = [&](int ln, int p, C2<T> val) { sm[lay(ln, p)] = val; };
     line_fft<T, L, -1, L, true>(sm, lay, line, j, v, tw, sink);

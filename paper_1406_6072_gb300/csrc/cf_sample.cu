@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
         else
             out[((size_t)rl * nrows + row) * keep + p] = val;
     };
-    line_fft<T, L, +1, L / 2>(sm, RowLayout<E, G::PADDED>(), line, j, v, tw, sink);
+    line_fft<T, L, +1, L / 2>(sm, RowLayout<G::PADE, G::PADDED>(), line, j, v, tw, sink);
 }
 
 template <typename T>
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(ColsCfg<float, L, true>::THREADS, ColsCfg<floa
     C2<float> v[G::E];
 #pragma unroll
     for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)N];
-    RowLayout<GF::E, GF::PADDED> lf;
+    RowLayout<GF::PADE, GF::PADDED> lf;
     auto sink = [&](int lnn, int p, C2<float> val) {
         epi((int)o, (long long)p * N + col0 + lnn, val);
         sm[lf(lnn, p)] = val;  // after the last stage's barrier: the buffer is free
