@@ -33,7 +33,9 @@ def test_tuned_chunk_is_used_and_changes_no_result(n, dt):
     scratch = torch.empty((R, 2) + n, dtype=before.dtype, device=DEV)
     chunk, ms = cf.cf_tune_sample(emb, dt, R, ws, ws_cap, scratch)
     assert chunk in (1, 2, 4, 8) and ms > 0
-    assert cf.cf_sample_workspace_size(emb, R, dt) == per * chunk
+    # the workspace for R realizations is now the one of a tuned chunk
+    assert cf.cf_sample_workspace_size(emb, R, dt) == cf.cf_sample_workspace_size(emb, chunk, dt)
+    assert cf.cf_sample_workspace_size(emb, R, dt) <= per * chunk
     after = _run(emb, n, R, dt, cf.cf_sample_workspace_size(emb, R, dt))
     assert torch.equal(before, after)
     emb.close()
