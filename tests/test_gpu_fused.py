@@ -91,3 +91,27 @@ def test_fused_spectra_refusals():
         cf.cf_sample_spectra(emb, 1, 0, 1, f, None, bins, pk, nm, None, None, ws, wsb, small, 64)
     assert ei.value.status == cf.CF_ERR_NOMEM
     emb.close()
+
+
+def test_fused_spectra_with_chunked_workspace():
+    """A sampler workspace of two realizations (several chunks, ragged last)
+    gives the same fields as one chunk, and the same spectra up to the order
+    of their atomic bin sums."""
+    n, R, nbins = (256, 256), 5, 24
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 5.0))
+    bins = cf.make_bins(nbins)
+    pkb = cf.cf_sample_spectra_workspace_size(emb, R, bins)
+    out = []
+    for wsr in (R, 2):
+        wsb = cf.cf_sample_workspace_size(emb, wsr, cf.CF_F32)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
+        fields = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+        pk = torch.empty((2 * R, nbins), dtype=torch.float64, device=DEV)
+        nm = torch.empty(nbins, dtype=torch.int64, device=DEV)
+        pkws = torch.empty(pkb, dtype=torch.uint8, device=DEV)
+        cf.cf_sample_spectra(emb, 3, 11, R, fields, None, bins, pk, nm, None, None, ws, wsb, pkws, pkb)
+        torch.cuda.synchronize()
+        out.append((fields, pk))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.allclose(out[0][1], out[1][1], rtol=2e-5, atol=0)
+    emb.close()

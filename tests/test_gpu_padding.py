@@ -130,3 +130,34 @@ def test_padded_grid_refusals():
     with pytest.raises(cf.CfError) as ei:
         cf.cf_power_spectrum_workspace_size(cf.make_grid((100, 100)), 2, bins, cf.CF_F32)
     assert ei.value.status == cf.CF_ERR_UNSUPPORTED
+
+
+def test_padded_masked_counts_and_double_float(orc):
+    """A padded, non-power-of-two grid with a survey mask in the fused
+    lognormal + Poisson step, and the double-float eigenvalue transforms on a
+    padded grid."""
+    from paper_1406_6072_gb300 import workloads as W
+    n, p, R = (48, 80), 4, 2
+    g = cf.make_grid(n, factor=p)
+    M = _m(n, p)
+    o = orc.embed(list(n), cf.CF_XI_GEN_CAUCHY, 0.8, 4.0, 0.4, clamp=True, M=M)
+    emb = cf.cf_embed(g, cf.make_xi(cf.CF_XI_GEN_CAUCHY, 0.8, 4.0, 0.4), cf.CF_EMBED_CLAMP | cf.CF_EMBED_DF)
+    lam = torch.empty(M, dtype=torch.float64, device=DEV)
+    cf.cf_embedding_lambda(emb, lam)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(lam.cpu().numpy() - o["lambda"])) <= 1e-12 * o["lambda"].max()
+    f = W.survey_mask(n, seed=17)
+    ft = torch.from_numpy(f).to(DEV)
+    wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
+    fields = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+    counts = torch.empty((R, 2) + n, dtype=torch.int32, device=DEV)
+    cf.cf_sample_lp(emb, 5, 0, R, cf.CF_F32, fields, cf.make_lp(0.8, 3.0, counts, 6, f=ft), ws, wsb)
+    torch.cuda.synchronize()
+    ref = orc.sample(n, o["sqrt_lambda"], 5, 0, R, 1)
+    assert rel_l2(fields.double().cpu().numpy(), ref) <= 1e-5
+    Gd = fields.double().cpu().numpy().reshape(2 * R, -1)
+    _, oc, margin = orc.lognormal_poisson(Gd, 0.8, 3.0, f=f.ravel().astype(np.float64), seed=6, field0=0)
+    c = counts.cpu().numpy().reshape(oc.shape)
+    assert not ((c != oc) & (margin >= 1e-6)).any()
+    emb.close()
