@@ -133,7 +133,7 @@ SMS, LANES = 152, 128          # GB300: SMs, FP32 lanes per SM
 
 def kernel_costs(wl, R, chunks):
     """Algorithmic bytes and operations per step of each kernel of the binary32
-    path, 2D or 3D (definitions in the design doc section 7; FMA = 1 op).
+    path, 2D or 3D (FMA = 1 op).
 
     sample_rows: noise + last-axis transform of every embedded row; writes the
     pruned intermediate (R * prod(M[:-1]) * n[-1] complex64) and reads
