@@ -60,7 +60,7 @@ typedef enum {
     CF_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad enum)  */
     CF_ERR_NOT_PSD = 2,      /* an embedding eigenvalue < -tau and no clamping       */
     CF_ERR_NOMEM = 3,        /* device or host allocation failed / workspace small   */
-    CF_ERR_UNSUPPORTED = 4,  /* size or mode not supported by this build             */
+    CF_ERR_UNSUPPORTED = 4,  /* size or mode not supported by the library or call   */
     CF_ERR_CUDA = 5,         /* a CUDA runtime call failed (message has the detail)  */
     CF_ERR_TIMEOUT = 6,      /* cf_serve_wait ran out of time                        */
     CF_ERR_BUSY = 7,         /* server queue full / shutting down                    */

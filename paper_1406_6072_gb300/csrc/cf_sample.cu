@@ -420,7 +420,7 @@ static cf_status check_sample_args(const cf_embedding* e, uint64_t r0, int32_t R
         if (!tc_ok) return fail(CF_ERR_UNSUPPORTED, "dtype %d is available in cf_sample only", dt);
         CF_TRY(tc_check_grid(e->grid));
     } else if (dt != CF_F32 && dt != CF_F64) {
-        return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+        return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported by this call", dt);
     }
     if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
     return CF_OK;
@@ -517,7 +517,7 @@ extern "C" cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, 
         *bytes = tc_header_bytes() + tc_bytes_per_realization(e->grid) * (size_t)(chunk < 1 ? 1 : chunk);
         return CF_OK;
     }
-    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported by this call", dt);
     const size_t elem = dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>);
     int chunk = pick_chunk(e->grid, elem, R < 1 ? 1 : R, (size_t)-1);
     *bytes = chunk_bytes(e->grid, elem, (size_t)(chunk < 1 ? 1 : chunk));
@@ -626,7 +626,7 @@ extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_
     if (R < 0 || ncells < 0) return fail(CF_ERR_ARG, "negative size");
     if (R > 65535) return fail(CF_ERR_UNSUPPORTED, "at most 65535 realizations per call");
     if (r0 + (uint64_t)R > (1ull << 32)) return fail(CF_ERR_ARG, "realization index exceeds 32 bits");
-    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported by this call", dt);
     if (dt == CF_F32 && (m_last < 2 || (m_last & 1) || ncells % m_last))
         return fail(CF_ERR_ARG, "m_last must be even and divide ncells");
     if (R == 0 || ncells == 0) return CF_OK;
@@ -640,7 +640,7 @@ extern "C" cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_
         k_noise_f64<<<grid, 256, 0, (cudaStream_t)s>>>((uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)r0, ncells,
                                                       (C2<double>*)out);
     } else {
-        return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported in this build", dt);
+        return fail(CF_ERR_UNSUPPORTED, "dtype %d not supported by this call", dt);
     }
     CF_CHECK_LAUNCH();
     return CF_OK;
