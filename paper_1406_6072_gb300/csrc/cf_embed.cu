@@ -246,13 +246,15 @@ __global__ void __launch_bounds__(kRedThreads)
                         double inv_total, double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
     double mx = 0.0;
+    int shift[3];  // embedded sides are powers of two: indices by shifts and masks
+    for (int a = 0; a < 3; ++a) shift[a] = __ffsll(g.m[a]) - 1;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.mtotal;
          idx += (long long)gridDim.x * blockDim.x) {
         long long rem = idx;
         bool survey = true;
         for (int a = g.ndim - 1; a >= 0; --a) {
-            const long long m = rem % g.m[a];
-            rem /= g.m[a];
+            const long long m = rem & (g.m[a] - 1);
+            rem >>= shift[a];
             if (m >= g.n[a] && m <= g.m[a] - g.n[a]) survey = false;
         }
         if (survey) mx = fmax(mx, fabs(z[idx].x * inv_total - c[idx]));
@@ -266,13 +268,15 @@ __global__ void __launch_bounds__(kRedThreads)
                              double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
     double mx = 0.0;
+    int shift[3];  // embedded sides are powers of two: indices by shifts and masks
+    for (int a = 0; a < 3; ++a) shift[a] = __ffsll(g.m[a]) - 1;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.mtotal;
          idx += (long long)gridDim.x * blockDim.x) {
         long long rem = idx;
         bool survey = true;
         for (int a = g.ndim - 1; a >= 0; --a) {
-            const long long m = rem % g.m[a];
-            rem /= g.m[a];
+            const long long m = rem & (g.m[a] - 1);
+            rem >>= shift[a];
             if (m >= g.n[a] && m <= g.m[a] - g.n[a]) survey = false;
         }
         if (survey) mx = fmax(mx, fabs(z[idx] - c[idx]));
@@ -389,9 +393,10 @@ __global__ void k_even_mirror(const S* __restrict__ half, long long rows, long l
                               double* __restrict__ full) {
     const long long H = M / 2 + 1;
     const long long total = rows * M;
+    const int shM = __ffsll(M) - 1;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / M, k = t - r * M;
+        const long long r = t >> shM, k = t & (M - 1);  // M is a power of two
         const long long kk = k < H ? k : M - k;
         const double v = from_s<S>(half[r * H + kk]);
         full[t] = SCALE ? v * scale : v;
