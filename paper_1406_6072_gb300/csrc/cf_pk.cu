@@ -47,6 +47,31 @@ __global__ void k_pk_bintable(Edges ed, int nbins, long long k2max, int16_t* __r
     }
 }
 
+// Integer form of the same bins: thr[b] = the least k2 >= 1 with sqrt(k2) >= e_b
+// (binary64, correctly rounded, as above; k2max + 1 if none).  sqrt is monotone,
+// so bin(k2) = max{b : thr[b] <= k2} for thr[0] <= k2 < thr[nbins], else -1:
+// exactly the table's bin, found in shared memory instead of a table read.
+// The thresholds are stored after the table (bin_thresholds()).
+__global__ void k_pk_thresholds(Edges ed, int nbins, long long k2max, int* __restrict__ thr) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbins) return;
+    long long lo = 1, hi = k2max + 1;  // first k2 in [lo, hi] with sqrt(k2) >= e_b (hi: none)
+    while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (sqrt((double)mid) >= ed.e[b]) hi = mid; else lo = mid + 1;
+    }
+    thr[b] = (int)lo;
+}
+
+__host__ __device__ inline const int* bin_thresholds(const int16_t* bin_of, long long k2max) {
+    return reinterpret_cast<const int*>(reinterpret_cast<const char*>(bin_of) +
+                                        ((sizeof(int16_t) * (size_t)(k2max + 1) + 15) & ~(size_t)15));
+}
+// bytes of the table plus its thresholds
+inline size_t bin_table_bytes(long long k2max) {
+    return ((sizeof(int16_t) * (size_t)(k2max + 1) + 15) & ~(size_t)15) + sizeof(int) * (kMaxBins + 1);
+}
+
 __device__ __forceinline__ long long signed_mode(long long i, long long n) { return i <= n / 2 ? i : i - n; }
 
 #ifndef CF_PKR_E
@@ -272,10 +297,13 @@ __global__ void __launch_bounds__(PkColsCfg<T, L>::THREADS, PkColsCfg<T, L>::MIN
     C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
     T* sbin = reinterpret_cast<T*>(sm + (size_t)Cfg::C * G::PADDED);
     T* scross = sbin + nbins;
+    int* sthr = reinterpret_cast<int*>(scross + nbins);
+    const int* thr = bin_thresholds(bin_of, k2max);
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
         sbin[b] = (T)0;
         scross[b] = (T)0;
     }
+    for (int b = threadIdx.x; b <= nbins; b += blockDim.x) sthr[b] = thr[b];
     const int ln = threadIdx.x % Cfg::C;
     const int j = threadIdx.x / Cfg::C;
     const long long i = (long long)blockIdx.x * Cfg::C + ln;
@@ -301,8 +329,23 @@ __global__ void __launch_bounds__(PkColsCfg<T, L>::THREADS, PkColsCfg<T, L>::MIN
             const int p = j * E + t;
             const C2<T> x = sm[lay(ln, p)];
             const long long s0 = signed_mode(p, L);
-            const long long k2 = s0 * s0 + c2;
-            const int b = k2 <= k2max ? (int)bin_of[k2] : -1;
+            const int k2 = (int)(s0 * s0 + c2);
+            int b = -1;
+            if (k2 >= sthr[0] && k2 < sthr[nbins]) {  // (thr[0] >= 1: the DC mode has no bin)
+                if (cur >= 0) {
+                    // neighbouring modes share a bin or sit in the next one
+                    b = cur;
+                    while (k2 >= sthr[b + 1]) ++b;
+                    while (k2 < sthr[b]) --b;
+                } else {
+                    int lo = 0, hi = nbins;  // sthr[lo] <= k2 < sthr[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sthr[mid] <= k2) lo = mid; else hi = mid;
+                    }
+                    b = lo;
+                }
+            }
             if (b != cur) {
                 if (cur >= 0) {
                     atomicAdd(&sbin[cur], run);
@@ -481,7 +524,7 @@ static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins
         o = align256(o + bytes);
         return at;
     };
-    P->off_bin = take(sizeof(int16_t) * (size_t)(P->k2max + 1));
+    P->off_bin = take(bin_table_bytes(P->k2max));
     P->off_nmodes = take(sizeof(unsigned long long) * P->nbins);
     P->off_acc = take(sizeof(double) * (size_t)nfields * P->nbins);
     P->off_cross = take(sizeof(double) * (size_t)nfields * P->nbins);
@@ -518,6 +561,8 @@ static cf_status build_bins(const PkPlan& P, int16_t* bin_of, unsigned long long
     const long long n_mid = d == 3 ? g.n[1] : 1;
     const long long inner = n_mid * P.H;
     k_pk_bintable<<<grid_blocks(P.k2max + 1, 256, 1024), 256, 0, s>>>(P.edges, P.nbins, P.k2max, bin_of);
+    k_pk_thresholds<<<(P.nbins + 1 + 127) / 128, 128, 0, s>>>(P.edges, P.nbins, P.k2max,
+                                                           const_cast<int*>(bin_thresholds(bin_of, P.k2max)));
     CF_CUDA(cudaMemsetAsync(nmodes, 0, sizeof(unsigned long long) * P.nbins, s));
     const size_t smem = (size_t)((P.nbins + 1) & ~1) * sizeof(unsigned int) + (size_t)P.nbins * sizeof(double);
     k_pk_nmodes<float><<<grid_blocks(g.n[0] * inner, 256, 256), 256, smem, s>>>(
@@ -555,7 +600,7 @@ static cf_status get_bins(const PkPlan& P, char* ws, cudaStream_t s, const int16
         return CF_OK;
     }
     BinCacheEntry c{dev, P.g.ndim, P.g.n[0], P.nbins, edges, nullptr, nullptr, nullptr};
-    CF_CUDA(cudaMalloc((void**)&c.bin_of, sizeof(int16_t) * (size_t)(P.k2max + 1)));
+    CF_CUDA(cudaMalloc((void**)&c.bin_of, bin_table_bytes(P.k2max)));
     CF_CUDA(cudaMalloc((void**)&c.nmodes, sizeof(unsigned long long) * P.nbins));
     CF_CUDA(cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming));
     CF_TRY(build_bins(P, c.bin_of, c.nmodes, s));
@@ -596,7 +641,7 @@ static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mi
                                 long long nchunk, cudaStream_t s) {
     using Cfg = PkColsCfg<T, L>;
     auto kern = k_pk_cols<T, L>;
-    const size_t smem = Cfg::SMEM + 2 * sizeof(T) * (size_t)P.nbins;
+    const size_t smem = Cfg::SMEM + 2 * sizeof(T) * (size_t)P.nbins + sizeof(int) * (size_t)(P.nbins + 1);
     CF_TRY(prepare_smem(kern, smem));
     dim3 grid((unsigned)((inner + Cfg::C - 1) / Cfg::C), (unsigned)nchunk);
     ScopedKernelTimer kt(s, sizeof(T) == 4 ? "pk_cols_f32" : "pk_cols_f64", L);
