@@ -306,10 +306,13 @@ __global__ void k_lambda_plus_complex(const double* __restrict__ lam, double tau
 
 // ---------------------------------------------------------------------------
 // DFT of a real array that is even along every axis (x(M - m) = x(m) per
-// axis), as the embedded row of an isotropic xi is.  Its DFT is real and even,
-// so two real lines are transformed as the real and imaginary parts of one
-// complex line and read back as Re and Im, and along the last axis only the
-// non-redundant half k <= M/2 is kept; the full result is mirrored at the end.
+// axis), as the embedded row of an isotropic xi is.  Its DFT is real and even
+// along every axis too, so only the non-redundant corner [0, M_a/2]^d is
+// transformed and stored (H_a = M_a/2 + 1 per axis); the full result is
+// mirrored at the end.  The row pass transforms the rows of the corner's
+// leading indices; a column pass rebuilds each line of length M_a from its
+// H_a stored values (x(M_a - m) = x(m)) and keeps outputs k <= M_a/2.  Two real
+// lines are transformed as the real and imaginary parts of one complex line.
 // ---------------------------------------------------------------------------
 // S: the arithmetic of the transforms, binary64 or double-float (DF); the
 // input x and the output are binary64, the scratch `half` holds S values.
@@ -324,9 +327,13 @@ __device__ __forceinline__ double from_s(S v) {
     else return df_to(v);
 }
 
+// Row r of the corner (nrows = prod of H_a over the leading axes) is full row
+// (r / Hm) Mm + r % Hm of in[..][L]: Hm, Mm = H and M of the middle axis in 3D,
+// 1 and 1 otherwise.
 template <typename S, int L>
 __global__ void __launch_bounds__(RowsCfg<S, L>::THREADS, RowsCfg<S, L>::MINB)
-    k_even_rows(const double* __restrict__ in, long long nrows, S* __restrict__ out, const C2<S>* __restrict__ tw) {
+    k_even_rows(const double* __restrict__ in, long long nrows, long long Hm, long long Mm, S* __restrict__ out,
+                const C2<S>* __restrict__ tw) {
     using Cfg = RowsCfg<S, L>;
     using G = typename Cfg::G;
     constexpr int H = L / 2 + 1;
@@ -338,8 +345,10 @@ __global__ void __launch_bounds__(RowsCfg<S, L>::THREADS, RowsCfg<S, L>::MINB)
     const long long ra = 2 * pair, rb = ra + 1;
     const bool valid = ra < nrows;
     const bool hasb = rb < nrows;
-    const double* a = in + (size_t)(valid ? ra : 0) * L;
-    const double* b = in + (size_t)(hasb ? rb : 0) * L;
+    const long long fa = valid ? (ra / Hm) * Mm + ra % Hm : 0;
+    const long long fb = hasb ? (rb / Hm) * Mm + rb % Hm : 0;
+    const double* a = in + (size_t)fa * L;
+    const double* b = in + (size_t)fb * L;
     C2<S> v[G::E];
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
@@ -354,13 +363,14 @@ __global__ void __launch_bounds__(RowsCfg<S, L>::THREADS, RowsCfg<S, L>::MINB)
     line_fft<S, L, -1, L>(sm, RowLayout<G::PADE, G::PADDED>(), line, j, v, tw, sink);
 }
 
-// Columns of in[outer][L][inner] in pairs (i, i+1): out has the same layout
-// (in place allowed).
+// Columns of in[outer][L/2+1][inner] in pairs (i, i+1), each the stored half
+// of an even line of length L: out has the same layout (in place allowed).
 template <typename S, int L>
 __global__ void __launch_bounds__(ColsCfg<S, L>::THREADS, ColsCfg<S, L>::MINB)
     k_even_cols(const S* in, long long inner, S* out, const C2<S>* __restrict__ tw) {
     using Cfg = ColsCfg<S, L>;
     using G = typename Cfg::G;
+    constexpr int H = L / 2 + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     C2<S>* sm = reinterpret_cast<C2<S>*>(smraw);
     const int ln = threadIdx.x % Cfg::C;
@@ -369,16 +379,17 @@ __global__ void __launch_bounds__(ColsCfg<S, L>::THREADS, ColsCfg<S, L>::MINB)
     const long long o = blockIdx.y;
     const bool valid = ia < inner;
     const bool hasb = ib < inner;
-    const size_t base = (size_t)o * L * (size_t)inner;
+    const size_t base = (size_t)o * H * (size_t)inner;
     const S zero = to_s<S>(0.0);
     C2<S> v[G::E];
 #pragma unroll
     for (int q = 0; q < G::E; ++q) {
-        const size_t row = base + (size_t)(j + q * (L / G::E)) * (size_t)inner;
+        const int p = j + q * (L / G::E);
+        const size_t row = base + (size_t)(p < H ? p : L - p) * (size_t)inner;
         v[q] = mk(valid ? in[row + ia] : zero, hasb ? in[row + ib] : zero);
     }
     auto sink = [&](int, int p, C2<S> val) {
-        if (!valid) return;
+        if (!valid || p >= H) return;
         const size_t row = base + (size_t)p * (size_t)inner;
         out[row + ia] = val.x;
         if (hasb) out[row + ib] = val.y;
@@ -386,19 +397,26 @@ __global__ void __launch_bounds__(ColsCfg<S, L>::THREADS, ColsCfg<S, L>::MINB)
     line_fft<S, L, -1, L>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
 }
 
-// full[rows][M] from half[rows][M/2+1] of an even last axis, times scale (a
-// power of two)
+// full[M_0]..[M_{d-1}] from the corner half[H_0]..[H_{d-1}] of an array even
+// along every axis, times scale (a power of two).  Axes past d have M = H = 1.
 template <typename S, bool SCALE>
-__global__ void k_even_mirror(const S* __restrict__ half, long long rows, long long M, double scale,
-                              double* __restrict__ full) {
-    const long long H = M / 2 + 1;
-    const long long total = rows * M;
-    const int shM = __ffsll(M) - 1;
+__global__ void k_even_mirror(const S* __restrict__ half, GridInfo g, double scale, double* __restrict__ full) {
+    int sh[3];
+    long long M[3], H[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        M[a] = a < g.ndim ? g.m[a] : 1;
+        H[a] = M[a] / 2 + 1 < M[a] ? M[a] / 2 + 1 : M[a];
+        sh[a] = __ffsll(M[a]) - 1;  // embedded sides are powers of two
+    }
+    const long long total = g.mtotal;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t >> shM, k = t & (M - 1);  // M is a power of two
-        const long long kk = k < H ? k : M - k;
-        const double v = from_s<S>(half[r * H + kk]);
+        const long long k2 = t & (M[2] - 1), k1 = (t >> sh[2]) & (M[1] - 1), k0 = t >> (sh[2] + sh[1]);
+        const long long c0 = k0 < H[0] ? k0 : M[0] - k0;
+        const long long c1 = k1 < H[1] ? k1 : M[1] - k1;
+        const long long c2 = k2 < H[2] ? k2 : M[2] - k2;
+        const double v = from_s<S>(half[(c0 * H[1] + c1) * H[2] + c2]);
         full[t] = SCALE ? v * scale : v;
     }
 }
@@ -415,13 +433,14 @@ __global__ void k_lambda_plus_real(const double* __restrict__ lam, const struct 
 }
 
 template <typename S, int L>
-static cf_status launch_even_rows(const double* in, long long nrows, S* out, cudaStream_t s) {
+static cf_status launch_even_rows(const double* in, long long nrows, long long Hm, long long Mm, S* out,
+                                  cudaStream_t s) {
     using Cfg = RowsCfg<S, L>;
     auto kern = k_even_rows<S, L>;
     CF_TRY(prepare_smem(kern, Cfg::SMEM));
     const long long pairs = (nrows + 1) / 2;
     ScopedKernelTimer kt(s, sizeof(S) == 8 && __is_same(S, double) ? "even_rows_f64" : "even_rows_df", L);
-    kern<<<(unsigned)((pairs + Cfg::ROWS - 1) / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, s>>>(in, nrows, out,
+    kern<<<(unsigned)((pairs + Cfg::ROWS - 1) / Cfg::ROWS), Cfg::THREADS, Cfg::SMEM, s>>>(in, nrows, Hm, Mm, out,
                                                                                      twiddles<S>());
     CF_CHECK_LAUNCH();
     return CF_OK;
@@ -442,30 +461,32 @@ static cf_status launch_even_cols(S* data, long long outer, long long inner, cud
 }
 
 // full = scale * DFT(x) for x real and even along every axis; half is scratch
-// of (mtotal / M_last) * (M_last/2 + 1) values of 8 bytes.  The transforms run
-// in binary64, or with CF_EMBED_DF in double-float arithmetic (cf_df.cuh).
+// of prod_a (M_a/2 + 1) values of 8 bytes.  The transforms run in binary64, or
+// with CF_EMBED_DF in double-float arithmetic (cf_df.cuh).
 template <typename S>
 static cf_status even_dft_t(const double* x, const GridInfo& g, double scale, S* half, double* full,
                             cudaStream_t s) {
     const int d = g.ndim;
-    const long long Ml = g.m[d - 1];
-    const long long H = Ml / 2 + 1;
-    const long long rows = g.mtotal / Ml;
-    CF_TRY(dispatch_line(Ml, [&](auto Lc) -> cf_status {
-        return launch_even_rows<S, decltype(Lc)::value>(x, rows, half, s);
+    long long H[3];
+    for (int a = 0; a < d; ++a) H[a] = g.m[a] / 2 + 1;
+    long long rows = 1;
+    for (int a = 0; a < d - 1; ++a) rows *= H[a];
+    const long long Hm = d == 3 ? H[1] : 1, Mm = d == 3 ? g.m[1] : 1;
+    CF_TRY(dispatch_line(g.m[d - 1], [&](auto Lc) -> cf_status {
+        return launch_even_rows<S, decltype(Lc)::value>(x, rows, Hm, Mm, half, s);
     }));
     for (int a = d - 2; a >= 0; --a) {
-        long long inner = H, outer = 1;
-        for (int b2 = a + 1; b2 < d - 1; ++b2) inner *= g.m[b2];
-        for (int b2 = 0; b2 < a; ++b2) outer *= g.m[b2];
+        long long inner = 1, outer = 1;
+        for (int b2 = a + 1; b2 < d; ++b2) inner *= H[b2];
+        for (int b2 = 0; b2 < a; ++b2) outer *= H[b2];
         CF_TRY(dispatch_line(g.m[a], [&](auto Lc) -> cf_status {
             return launch_even_cols<S, decltype(Lc)::value>(half, outer, inner, s);
         }));
     }
     if (scale == 1.0)
-        k_even_mirror<S, false><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
+        k_even_mirror<S, false><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, g, scale, full);
     else
-        k_even_mirror<S, true><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, rows, Ml, scale, full);
+        k_even_mirror<S, true><<<grid_blocks(g.mtotal, 256, 4096), 256, 0, s>>>(half, g, scale, full);
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
