@@ -318,32 +318,42 @@ __global__ void __launch_bounds__(PkColsCfg<T, L>::THREADS, PkColsCfg<T, L>::MIN
     line_fft<T, L, -1, L, true>(sm, lay, ln, j, v, tw, sink);
     __syncthreads();
     if (valid) {
-        const long long il = i % H;
-        const long long smid = signed_mode(i / H, n_mid);
-        const long long c2 = smid * smid + il * il;
-        const T w = (il == 0 || 2 * il == n_last) ? (T)1 : (T)2;
+        // 32-bit mode arithmetic: k2 <= k2max < 2^31
+        const int il = (int)(i % H);
+        const int smid = (int)signed_mode(i / H, n_mid);
+        const int c2 = smid * smid + il * il;
+        const T w = (il == 0 || 2 * (long long)il == n_last) ? (T)1 : (T)2;
+        const int t_first = sthr[0], t_end = sthr[nbins];  // (t_first >= 1: the DC mode has no bin)
         int cur = -1;
+        int lo_t = 0, hi_t = 0;  // [thr[cur], thr[cur + 1]) while cur >= 0, else empty
         T run = (T)0, runx = (T)0;
 #pragma unroll 4
         for (int t = 0; t < E; ++t) {
             const int p = j * E + t;
             const C2<T> x = sm[lay(ln, p)];
-            const long long s0 = signed_mode(p, L);
-            const int k2 = (int)(s0 * s0 + c2);
-            int b = -1;
-            if (k2 >= sthr[0] && k2 < sthr[nbins]) {  // (thr[0] >= 1: the DC mode has no bin)
-                if (cur >= 0) {
-                    // neighbouring modes share a bin or sit in the next one
-                    b = cur;
-                    while (k2 >= sthr[b + 1]) ++b;
-                    while (k2 < sthr[b]) --b;
+            const int s0 = p <= L / 2 ? p : p - L;
+            const int k2 = s0 * s0 + c2;
+            int b = cur;
+            if (k2 < lo_t || k2 >= hi_t) {
+                if (k2 < t_first || k2 >= t_end) {
+                    b = -1;
+                    lo_t = hi_t = 0;
                 } else {
-                    int lo = 0, hi = nbins;  // sthr[lo] <= k2 < sthr[hi]
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sthr[mid] <= k2) lo = mid; else hi = mid;
+                    if (cur >= 0) {
+                        // neighbouring modes sit in the same or a nearby bin
+                        b = cur;
+                        while (k2 >= sthr[b + 1]) ++b;
+                        while (k2 < sthr[b]) --b;
+                    } else {
+                        int lo = 0, hi = nbins;  // sthr[lo] <= k2 < sthr[hi]
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sthr[mid] <= k2) lo = mid; else hi = mid;
+                        }
+                        b = lo;
                     }
-                    b = lo;
+                    lo_t = sthr[b];
+                    hi_t = sthr[b + 1];
                 }
             }
             if (b != cur) {
