@@ -50,3 +50,11 @@ def test_product_arm_needs_a_gpu():
     p = _run(["--steps", "3", "--warmup", "3"], timeout=300)
     assert p.returncode != 0
     assert not [d for d in _lines(p.stdout) if "value" in d]
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300, env=env)
+    assert p.returncode == 0
+    assert not _lines(p.stdout)
