@@ -233,18 +233,24 @@ CF_API cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, in
  * that every device loading the library holds until the process exits.
  *  - Sizes whose single realization needs more than 16 MiB of intermediate
  *    (e.g. 2D surveys above 1024x1024, 3D above 64^3) are rejected with
- *    CF_ERR_UNSUPPORTED and a message giving the bytes needed.
+ *    CF_ERR_UNSUPPORTED and a message giving the bytes needed.  An embedding
+ *    built on another device than s's is rejected with CF_ERR_ARG.
  *  - Nothing is allocated on the device: no cudaMalloc, cudaFree or allocator
  *    call.  The first call on a device does a one-time set-up (the array's
- *    device address, an ordering event, the twiddle tables): make it before
- *    any stream capture.  The first use of an embedding on a stream other
- *    than the one it was built on creates one CUDA event (host-side object)
- *    so that cf_embedding_free can wait for the work.
+ *    device address, an ordering event, the twiddle tables) that synchronises
+ *    the device: make it before any stream capture.  The first use of an
+ *    embedding on a stream other than the one it was built on creates one
+ *    CUDA event (host-side object) so that cf_embedding_free can wait for the
+ *    work.
+ *  - While another thread captures in global mode, s must be a stream created
+ *    with cudaStreamNonBlocking: work on the legacy default stream (s = NULL,
+ *    or a default stream of a framework that maps to it) synchronises with
+ *    every other stream and invalidates that capture.
  *  - All calls share the array, which keeps the last call's contents; every
  *    element a call reads it has written first, so nothing needs clearing.
- *    The library orders successive calls on the GPU (host lock + device
- *    event); calls whose work nevertheless overlapped on the GPU would race
- *    on the array. */
+ *    The library orders successive direct calls on a device (host lock +
+ *    device event); calls whose work nevertheless overlaps on the GPU race on
+ *    the array. */
 CF_API cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R,
                                    void* fields_out, cf_stream_t s);
 

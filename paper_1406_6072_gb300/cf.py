@@ -330,7 +330,11 @@ def cf_sample(emb, seed, r0, R, dtype, fields_out, ws, ws_bytes, stream=None):
 
 def cf_sample_noalloc(emb, seed, r0, R, fields_out, stream=None):
     """Binary32 sampler with its intermediate in the library's static array
-    (no device allocation); see include/cf.h."""
+    (no device allocation).  Calls share that array; the first call on a
+    device synchronises it for a one-time set-up, so make it before any
+    capture.  When another thread captures a CUDA graph in global mode, pass a
+    stream created non-blocking (torch.cuda.Stream() is): the legacy default
+    stream synchronises with the capturing stream and breaks the capture."""
     _check(_lib.cf_sample_noalloc(emb.handle, seed, r0, R, _ptr(fields_out), _stream(stream)), "cf_sample_noalloc")
 
 

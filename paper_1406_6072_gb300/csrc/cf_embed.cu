@@ -294,15 +294,6 @@ __global__ void __launch_bounds__(kRedThreads)
     if (threadIdx.x == 0) st->cov_error = mx;
 }
 
-// lambda+ as a complex array (for the realised-covariance pass)
-__global__ void k_lambda_plus_complex(const double* __restrict__ lam, double tau,
-                                      C2<double>* __restrict__ z, long long total) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const double l = lam[i];
-        z[i] = mk(l > tau ? l : 0.0, 0.0);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // DFT of a real array that is even along every axis (x(M - m) = x(m) per
@@ -429,6 +420,18 @@ __global__ void k_lambda_plus_real(const double* __restrict__ lam, const struct 
          i += (long long)gridDim.x * blockDim.x) {
         const double l = lam[i];
         out[i] = l > tau ? l : 0.0;
+    }
+}
+
+// lambda+ (threshold tau read on the device) as a complex array, written
+// straight into the transform buffer (no in-place real-to-complex widening)
+__global__ void k_lambda_plus_complex(const double* __restrict__ lam, const struct EmbedStats* __restrict__ st,
+                                      C2<double>* __restrict__ z, long long total) {
+    const double tau = st->tau;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double l = lam[i];
+        z[i] = mk(l > tau ? l : 0.0, 0.0);
     }
 }
 
@@ -579,21 +582,21 @@ static cf_status finish_embedding(const GridInfo& gi, EmbedScratch& sc, uint32_t
     CF_CHECK_LAUNCH();
     if (want_error) {
         // realised covariance = IDFT(lambda+)/M^d, compared with c on survey lags
-        double* buf = (double*)sc.z;  // M^d doubles, then scratch for the half spectra
-        {
-            ScopedKernelTimer kt(s, "embed_cov_error");
-            k_lambda_plus_real<<<blocks, kRedThreads, 0, s>>>(e->lambda, sc.st, buf, total);
-        }
-        CF_CHECK_LAUNCH();
         if (even) {
             // lambda+ is real and even: its inverse transform equals its forward one
+            double* buf = (double*)sc.z;  // M^d doubles, then scratch for the half spectra
+            {
+                ScopedKernelTimer kt(s, "embed_cov_error");
+                k_lambda_plus_real<<<blocks, kRedThreads, 0, s>>>(e->lambda, sc.st, buf, total);
+            }
+            CF_CHECK_LAUNCH();
             CF_TRY(even_dft(buf, gi, 1.0 / (double)total, buf + total, buf, flags, s));
             ScopedKernelTimer kt(s, "embed_cov_error");
             k_cov_error_partial_real<<<blocks, kRedThreads, 0, s>>>(buf, sc.c, gi, sc.part);
         } else {
             {
                 ScopedKernelTimer kt(s, "embed_cov_error");
-                k_real_to_complex<<<blocks, kRedThreads, 0, s>>>(buf, nullptr, sc.z, total);
+                k_lambda_plus_complex<<<blocks, kRedThreads, 0, s>>>(e->lambda, sc.st, sc.z, total);
             }
             CF_CHECK_LAUNCH();
             CF_TRY((fft_nd_inplace<double, +1>(sc.z, gi, s)));

@@ -64,6 +64,9 @@ cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* m
 // Entry-point prologue: makes the device of stream s current (the legacy
 // default stream keeps the current device) and runs the one-time set-up.
 cf_status enter(cudaStream_t s);
+// enter(s), then refuses an embedding that lives on another device than the
+// stream's (its arrays would be another GPU's memory to the kernels).
+cf_status enter_with(const cf_embedding* e, cudaStream_t s);
 const C2<float>* twiddles_f32();   // current device, TWN entries exp(+2 pi i j/TWN)
 const C2<double>* twiddles_f64();
 

@@ -72,7 +72,7 @@ extern "C" cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uin
                     per, kNoAllocScratchBytes);
     if (R == 0) return CF_OK;
     const cudaStream_t st = (cudaStream_t)s;
-    CF_TRY(enter(st));
+    CF_TRY(enter_with(e, st));
     int dev = 0;
     CF_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(CF_ERR_UNSUPPORTED, "device index %d", dev);

@@ -102,7 +102,7 @@ extern "C" cf_status cf_plan_create(const cf_embedding* e, uint64_t seed, uint64
         return fail(CF_ERR_UNSUPPORTED, "plans take counts_out only (no mask, no delta output)");
     if (bins && (!pk_out || !nmodes_out)) return fail(CF_ERR_ARG, "bins need pk_out and nmodes_out");
     if (pk_counts_out && !(bins && lp)) return fail(CF_ERR_ARG, "pk_counts_out needs bins and lp");
-    CF_TRY(enter((cudaStream_t)s));
+    CF_TRY(enter_with(e, (cudaStream_t)s));
     const cudaStream_t st = (cudaStream_t)s;
     cf_plan* p = new cf_plan();
     auto bail = [&](cf_status code) {

@@ -171,6 +171,16 @@ cf_status enter(cudaStream_t s) {
     return ensure_device_init();
 }
 
+cf_status enter_with(const cf_embedding* e, cudaStream_t s) {
+    CF_TRY(enter(s));
+    int cur = -1;
+    CF_CUDA(cudaGetDevice(&cur));
+    if (e->device != cur)
+        return fail(CF_ERR_ARG, "the embedding was built on device %d but the stream belongs to device %d", e->device,
+                    cur);
+    return CF_OK;
+}
+
 const C2<float>* twiddles_f32() { return g_tw32_ptr[current_device()]; }
 const C2<double>* twiddles_f64() { return g_tw64_ptr[current_device()]; }
 const C2<DF>* twiddles_df() { return g_twdf_ptr[current_device()]; }

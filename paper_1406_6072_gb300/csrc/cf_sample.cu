@@ -530,7 +530,7 @@ extern "C" cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0
     CF_TRY(check_sample_args(e, r0, R, dt, true));
     if (!fields_out) return fail(CF_ERR_ARG, "fields_out is NULL");
     if (R == 0) return CF_OK;
-    CF_TRY(enter((cudaStream_t)s));
+    CF_TRY(enter_with(e, (cudaStream_t)s));
     if (is_tc(dt)) {
         const size_t head = tc_header_bytes();
         const int chunk = ws && ws_bytes > head ? pick_chunk(e->grid, 4, R, ws_bytes - head) : 0;
@@ -555,7 +555,7 @@ extern "C" cf_status cf_sample_lp(const cf_embedding* e, uint64_t seed, uint64_t
     if (!lp || !lp->counts_out) return fail(CF_ERR_ARG, "lp and lp->counts_out are required");
     if (!(lp->nbar >= 0.0)) return fail(CF_ERR_ARG, "nbar must be >= 0");
     if (R == 0) return CF_OK;
-    CF_TRY(enter((cudaStream_t)s));
+    CF_TRY(enter_with(e, (cudaStream_t)s));
     return sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, (cudaStream_t)s);
 }
 
@@ -564,7 +564,7 @@ extern "C" cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t 
     clear_error();
     CF_TRY(check_sample_args(e, 0, R, dt));
     if (R < 1 || !fields_scratch) return fail(CF_ERR_ARG, "R >= 1 and fields_scratch are required");
-    CF_TRY(enter((cudaStream_t)s));
+    CF_TRY(enter_with(e, (cudaStream_t)s));
     const cudaStream_t st = (cudaStream_t)s;
     const size_t elem = dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>);
     const size_t per = per_realization_bytes(e->grid, elem);
@@ -694,7 +694,7 @@ extern "C" cf_status cf_sample_spectra(const cf_embedding* e, uint64_t seed, uin
     if (!pk_ws || pk_ws_bytes < acc + half)
         return fail(CF_ERR_NOMEM, "spectra workspace of %zu bytes, %zu needed", pk_ws_bytes, acc + half);
     const cudaStream_t st = (cudaStream_t)s;
-    CF_TRY(enter(st));
+    CF_TRY(enter_with(e, st));
     C2<float>* halves = (C2<float>*)((char*)pk_ws + acc);
     CF_TRY(sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, st, halves));
     if (sampled) CF_CUDA(cudaEventRecord((cudaEvent_t)sampled, st));

@@ -16,6 +16,8 @@ from paper_1406_6072_gb300 import cf  # noqa: E402
 from paper_1406_6072_gb300 import workloads as W  # noqa: E402
 from paper_1406_6072_gb300.pipeline import FieldPipeline  # noqa: E402
 
+DEV = torch.device("cuda:0")
+
 
 def _check_realization(orc, wl, o_emb, fields, counts, pk, pkg, r, r0):
     n = wl.n
@@ -65,3 +67,49 @@ def test_workload_at_full_size(orc, name, sampled):
     nm = pipe.nmodes.cpu().numpy()
     assert nm.sum() > 0 and np.all(nm >= 0)
     pipe.close()
+
+
+@pytest.fixture(scope="module")
+def cauchy_n512(orc):
+    """The 512^2 generalised-Cauchy workload's embedding (not PSD, clamped)
+    from the oracle: row, eigenvalues and report."""
+    wl = W.CONFIGS["cauchy2d_n512_f32"]
+    return wl, orc.embed(list(wl.n), wl.xi_kind, wl.amp, wl.scale, wl.beta, clamp=True)
+
+
+def _check_clamp_report(rep, orep):
+    # section 2, eq. (condition): the clamped spectrum's realised covariance
+    # error is the method's statement of how far the sample is from exact
+    assert rep["clamped"] == 1 and orep["clamped"] == 1
+    assert rep["n_negative"] == orep["n_negative"]
+    assert abs(rep["n_zeroed"] - orep["n_zeroed"]) <= max(2, orep["n_zeroed"] // 100)
+    assert rep["neg_mass"] == pytest.approx(orep["neg_mass"], rel=1e-9)
+    assert rep["cov_error"] == pytest.approx(orep["cov_error"], rel=1e-6)
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_tabulated_row_clamp_report_at_full_size(cauchy_n512, on_device):
+    """The general (complex-transform) embedding path with a tabulated first
+    row at 1024^2: the grid-stride passes wrap many times here, so any
+    overlap between the clamped spectrum and its transform buffer shows."""
+    wl, o = cauchy_n512
+    tab = torch.from_numpy(np.ascontiguousarray(o["c"]))
+    if on_device:
+        tab = tab.to(DEV)
+    emb = cf.cf_embed(cf.make_grid(wl.n), cf.make_xi(cf.CF_XI_TABLE, table=tab), cf.CF_EMBED_CLAMP)
+    lam = torch.empty(o["lambda"].shape, dtype=torch.float64, device=DEV)
+    cf.cf_embedding_lambda(emb, lam)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(lam.cpu().numpy() - o["lambda"])) <= 1e-12 * o["lambda"].max()
+    _check_clamp_report(emb.report, o["report"])
+    emb.close()
+
+
+def test_explicit_lambda_clamp_report_at_full_size(cauchy_n512):
+    """cf_embed_from_lambda at 1024^2 with the oracle's (non-PSD) eigenvalues."""
+    wl, o = cauchy_n512
+    lam = torch.from_numpy(np.ascontiguousarray(o["lambda"])).to(DEV)
+    emb = cf.cf_embed_from_lambda(cf.make_grid(wl.n), lam, cf.CF_EMBED_CLAMP)
+    torch.cuda.synchronize()
+    _check_clamp_report(emb.report, o["report"])
+    emb.close()
