@@ -209,8 +209,9 @@ CF_API cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_t nc
                         cf_dtype dt, void* out, cf_stream_t s);
 
 /* Workspace (bytes, device) that cf_sample / cf_sample_lp need for R
- * realizations; realizations are processed in chunks sized so that the
- * intermediate of a chunk stays in L2, so the size saturates for large R. */
+ * realizations; realizations are processed in chunks whose intermediate
+ * fits 1 GiB (or the chunk cf_tune_sample recorded for this grid), so the size
+ * saturates for large R. */
 CF_API cf_status cf_sample_workspace_size(const cf_embedding* e, int32_t R, cf_dtype dt, size_t* bytes);
 
 /* Steps b1-b4 (section 2, eq. (Papos2) and the closing paragraph): for each

@@ -1,6 +1,6 @@
 """Full-size parity: the workloads at their real sizes, run exactly as
 bench.py runs them (FieldPipeline: embed, fused sample + lognormal/Poisson in
-L2-sized chunks, both power spectra), checked on realizations sampled across
+chunks of up to 1 GiB of intermediate, both power spectra), checked on realizations sampled across
 the batch against the oracle, which computes them one by one.  Tolerances as
 in test_gpu_parity.py."""
 import numpy as np

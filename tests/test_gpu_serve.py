@@ -132,3 +132,48 @@ def test_failures_are_statuses():
     st = cf.cf_serve_stats(sv)
     assert st["failed"] == 2 and st["completed"] == 1
     cf.cf_serve_destroy(sv)
+
+
+def test_batched_mixed_stream_matches_the_oracle(orc):
+    """Requests of one shape queued behind a large one are served by one
+    descriptor-driven launch (different amplitude, seed, realization offset
+    and Poisson parameters per request); every served field is compared with
+    the oracle's sampler at the request's amplitude (binary32 gate, relative
+    L2 1e-5) and every count with the oracle's inverse CDF on the served
+    field (bit-exact outside the 1e-6 boundary band)."""
+    specs = [((64, 64), cf.CF_XI_GAUSSIAN, 0.35, 3.0, 0.0, 501, 0, 3, 0.35, 2.0),
+             ((64, 64), cf.CF_XI_GAUSSIAN, 1.20, 3.0, 0.0, 502, 17, 2, 1.20, 5.0),
+             ((64, 64), cf.CF_XI_GAUSSIAN, 0.80, 3.0, 0.0, 0xABCDEF0123, 2**32 - 9, 4, 0.80, 0.5),
+             ((16, 16, 16), cf.CF_XI_EXPONENTIAL, 0.9, 2.0, 0.0, 504, 3, 2, 0.9, 3.0),
+             ((16, 16, 16), cf.CF_XI_EXPONENTIAL, 0.4, 2.0, 0.0, 505, 9, 3, 0.4, 1.0),
+             ((64, 64), cf.CF_XI_GEN_CAUCHY, 0.6, 4.0, 0.4, 506, 1, 2, 0.6, 2.0)]
+    sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=1, max_batch_realizations=64))
+    big = cf.make_request((1024, 1024), cf.CF_XI_GAUSSIAN, 1.0, 4.0, R=64)
+    t_big = cf.cf_serve_submit(sv, big)
+    tickets, outs, keep = [], [], []
+    for n, kind, amp, scale, beta, seed, r0, R, s2, nbar in specs:
+        hf, hc = _host((R, 2) + n), _host((R, 2) + n, torch.int32)
+        req = cf.make_request(n, kind, amp, scale, beta, seed=seed, r0=r0, R=R, want_counts=True, sigma2=s2,
+                              nbar=nbar, lp_seed=seed + 7, host_fields=hf, host_counts=hc)
+        keep.append(req)
+        tickets.append(cf.cf_serve_submit(sv, req))
+        outs.append((hf, hc))
+    res = [cf.cf_serve_wait(sv, t, 60_000_000) for t in tickets]
+    assert cf.cf_serve_wait(sv, t_big, 60_000_000)["status"] == cf.CF_OK
+    st = cf.cf_serve_stats(sv)
+    assert st["batches"] < st["batched_requests"], "the queued requests were not batched"
+    for (n, kind, amp, scale, beta, seed, r0, R, s2, nbar), r, (hf, hc) in zip(specs, res, outs):
+        assert r["status"] == cf.CF_OK
+        o = orc.embed(list(n), kind, amp, scale, beta, clamp=True)
+        ref = orc.sample(n, o["sqrt_lambda"], seed, r0, R, 1)
+        got = hf.double().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-5, (n, amp, seed, err)
+        _, oc, margin = orc.lognormal_poisson(got.reshape(2 * R, -1), s2, nbar, seed=seed + 7, field0=2 * r0)
+        c = hc.numpy().reshape(2 * R, -1)
+        bad = (c != oc) & (margin >= 1e-6)
+        assert not bad.any(), (n, seed, int(bad.sum()))
+        assert (margin < 1e-6).mean() < 1e-3
+    for t in tickets + [t_big]:
+        cf.cf_serve_release(sv, t)
+    cf.cf_serve_destroy(sv)
