@@ -86,7 +86,7 @@ def _lib_handle():
         lib.or_lognormal_poisson.argtypes = [_P, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                              _P, C.c_uint64, C.c_uint64, _P, _P, _P]
         lib.or_bin_edges.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _P, _P]
-        lib.or_power_spectrum.argtypes = [_P, C.c_int32, _P, C.c_double, C.c_int64, C.c_int32,
+        lib.or_power_spectrum.argtypes = [_P, C.c_int32, _P, _P, C.c_int64, C.c_int32,
                                           _P, _P, _P]
         lib.or_counts_to_delta.argtypes = [_P, _P, C.c_int64, C.c_int64, _P]
         lib.or_mean_cov.argtypes = [_P, C.c_int64, C.c_int32, _P, _P]
@@ -273,15 +273,20 @@ def bin_edges(kind, nbins, kmin, kmax, edges=None):
 
 
 def power_spectrum(fields, n, edges, cell=1.0):
-    """fields [F][*n] -> (pk [F][nbins], nmodes [nbins])."""
+    """Binned power spectrum, section 3.2 eq. (Def spec): fields [F][*n] ->
+    (pk [F][nbins], nmodes [nbins]).  cell: one size for every axis or one
+    per axis.  |k| is in units of the fundamental frequency of the longest
+    side (the integer index length on a cube)."""
     dims, d = _dims(n)
+    cellv = np.ones(3, dtype=np.float64)
+    cellv[:d] = np.broadcast_to(np.asarray(cell, dtype=np.float64), (d,))
     fl = np.ascontiguousarray(fields, dtype=np.float64)
     F = fl.shape[0]
     edges = np.ascontiguousarray(edges, dtype=np.float64)
     nb = edges.size - 1
     pk = np.zeros((F, nb), dtype=np.float64)
     nm = np.zeros(nb, dtype=np.int64)
-    _lib_handle().or_power_spectrum(_ptr(fl), d, _ptr(dims), cell, F, nb, _ptr(edges), _ptr(pk),
+    _lib_handle().or_power_spectrum(_ptr(fl), d, _ptr(dims), _ptr(cellv), F, nb, _ptr(edges), _ptr(pk),
                                     _ptr(nm))
     return pk, nm
 

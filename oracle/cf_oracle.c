@@ -700,14 +700,24 @@ void or_bin_edges(int32_t kind, int32_t nbins, double kmin, double kmax,
     }
 }
 
-void or_power_spectrum(const double* fields, int32_t ndim, const int64_t* n, double cell,
+void or_power_spectrum(const double* fields, int32_t ndim, const int64_t* n, const double* cell,
                        int64_t nfields, int32_t nbins, const double* edges, double* pk,
                        int64_t* nmodes)
 {
+    /* Section 3.2, eq. (Def spec): mode m of the survey box has wavevector
+     * k_d = 2 pi s_d / L_d with s_d the signed index and L_d = n_d cell_d the
+     * side.  |k| is measured in units of the fundamental 2 pi / L_ref of the
+     * longest side L_ref: q = sqrt(sum_d (s_d r_d)^2), r_d = L_ref / L_d, each
+     * operation rounded in binary64 in this order (for a cube r_d = 1 and q is
+     * the integer index length sqrt(sum s_d^2)). */
     int64_t total = 1;
     for (int d = 0; d < ndim; ++d) total *= n[d];
-    double vol_cell = 1.0;
-    for (int d = 0; d < ndim; ++d) vol_cell *= cell;
+    double vol_cell = 1.0, lref = 0.0, r[3] = {1.0, 1.0, 1.0};
+    for (int d = 0; d < ndim; ++d) {
+        vol_cell *= cell[d];
+        if ((double)n[d] * cell[d] > lref) lref = (double)n[d] * cell[d];
+    }
+    for (int d = 0; d < ndim; ++d) r[d] = lref / ((double)n[d] * cell[d]);
     double* z = (double*)malloc(sizeof(double) * 2 * (size_t)total);
     double* sums = (double*)malloc(sizeof(double) * (size_t)nbins);
     for (int32_t b = 0; b < nbins; ++b) nmodes[b] = 0;
@@ -719,15 +729,19 @@ void or_power_spectrum(const double* fields, int32_t ndim, const int64_t* n, dou
         or_fft_nd(z, ndim, n, -1);
         for (int32_t b = 0; b < nbins; ++b) sums[b] = 0.0;
         for (int64_t idx = 0; idx < total; ++idx) {
-            int64_t rem = idx, k2 = 0;
+            int64_t rem = idx, sv[3] = {0, 0, 0};
             for (int d = ndim - 1; d >= 0; --d) {
                 int64_t i = rem % n[d];
                 rem /= n[d];
-                int64_t sn = (i <= n[d] / 2) ? i : i - n[d];
-                k2 += sn * sn;
+                sv[d] = (2 * i <= n[d]) ? i : i - n[d];
             }
-            if (k2 == 0) continue;
-            double kn = sqrt((double)k2);
+            double q2 = 0.0;
+            for (int d = 0; d < ndim; ++d) {
+                const double t = (double)sv[d] * r[d];
+                q2 = q2 + t * t;
+            }
+            if (q2 == 0.0) continue;
+            double kn = sqrt(q2);
             if (!(kn >= edges[0] && kn < edges[nbins])) continue;
             int32_t b = 0;
             while (!(kn < edges[b + 1])) ++b;

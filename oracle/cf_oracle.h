@@ -87,7 +87,7 @@ void or_lognormal_poisson(const double* G, int64_t cells, int64_t nfields, doubl
 enum { OR_BINS_LINEAR = 0, OR_BINS_LOG = 1, OR_BINS_EDGES = 2 };
 void or_bin_edges(int32_t kind, int32_t nbins, double kmin, double kmax,
                   const double* edges_in, double* edges_out);
-void or_power_spectrum(const double* fields, int32_t ndim, const int64_t* n, double cell,
+void or_power_spectrum(const double* fields, int32_t ndim, const int64_t* n, const double* cell,
                        int64_t nfields, int32_t nbins, const double* edges,
                        double* pk, int64_t* nmodes);
 void or_counts_to_delta(const int32_t* counts, const double* f_or_null, int64_t cells,

@@ -19,42 +19,79 @@ import pytest
 from paper_1406_6072_gb300 import workloads as W
 
 
+def _mode_lengths(n, cell):
+    """|k| of every mode of an n-grid with cell sizes `cell`, in units of the
+    fundamental 2 pi / L_ref of the longest side L_ref = max n_d cell_d,
+    computed directly from k_d = s_d / (n_d cell_d) (cycles per unit)."""
+    d = len(n)
+    cell = np.broadcast_to(np.asarray(cell, dtype=np.float64), (d,))
+    L = np.array(n, dtype=np.float64) * cell
+    idx = np.indices(n).reshape(d, -1).T
+    s = np.where(2 * idx <= np.array(n), idx, idx - np.array(n))
+    return L.max() * np.sqrt(np.sum((s / L) ** 2, axis=1))
+
+
 def _brute_pk(field, edges, cell):
     n = field.shape
     d = len(n)
+    cellv = np.broadcast_to(np.asarray(cell, dtype=np.float64), (d,))
     idx = np.indices(n).reshape(d, -1).T
     flat = field.ravel()
     nb = edges.size - 1
     sums = np.zeros(nb)
     counts = np.zeros(nb, dtype=np.int64)
-    for k in idx:
+    q = _mode_lengths(n, cellv)
+    for t, k in enumerate(idx):
         ph = np.zeros(len(idx))
         for a in range(d):
             ph += (k[a] * idx[:, a] % n[a]) / n[a]
         X = np.sum(flat * np.exp(-2j * np.pi * ph))
-        sn = [k[a] if k[a] <= n[a] // 2 else k[a] - n[a] for a in range(d)]
-        k2 = sum(v * v for v in sn)
-        if k2 == 0:
+        if not np.any(k):
             continue
-        kn = math.sqrt(k2)
+        kn = q[t]
         for b in range(nb):
             if edges[b] <= kn < edges[b + 1]:
                 sums[b] += abs(X) ** 2
                 counts[b] += 1
-    pk = np.where(counts > 0, cell**d * sums / (np.prod(n) * np.maximum(counts, 1)), 0.0)
+    pk = np.where(counts > 0, np.prod(cellv) * sums / (np.prod(n) * np.maximum(counts, 1)), 0.0)
     return pk, counts
 
 
-@pytest.mark.parametrize("n,cell", [((6, 8), 1.0), ((4, 4, 4), 0.5), ((12,), 2.0), ((8, 8), 1.0)])
+@pytest.mark.parametrize("n,cell", [((6, 8), 1.0), ((4, 4, 4), 0.5), ((12,), 2.0), ((8, 8), 1.0),
+                                    ((5, 4, 3), (0.5, 0.7, 1.1)), ((6, 10), (2.0, 1.0)), ((9, 7), 1.0)])
 def test_power_spectrum_brute_force(orc, n, cell):
     rng = np.random.default_rng(sum(n))
     fields = rng.standard_normal((3,) + n)
-    edges = orc.bin_edges(orc.BINS_LINEAR, 3, 0.0, min(n) / 2)
+    q = _mode_lengths(n, cell)
+    cube = len(set(n)) == 1 and np.ndim(cell) == 0
+    # cubes: integer edges (exact integer mode lengths); otherwise edges that
+    # no mode length comes near, so that rounding cannot decide a bin
+    kmax = q.max() * 0.9 if not cube else min(n) / 2
+    edges = orc.bin_edges(orc.BINS_LINEAR, 3, 0.0, kmax if cube else kmax + 0.0123)
+    if not cube:
+        assert np.min(np.abs(q[q > 0][:, None] - edges[None, :])) > 1e-9
     pk, nm = orc.power_spectrum(fields, n, edges, cell=cell)
     for f in range(3):
         ref, cnt = _brute_pk(fields[f], edges, cell)
         assert np.array_equal(nm, cnt)
         assert np.allclose(pk[f], ref, rtol=1e-11, atol=1e-13)
+
+
+def test_power_spectrum_plane_waves_in_a_rectangular_box(orc):
+    """A plane wave of physical wavelength lam puts all its power at
+    |k| = L_ref / lam (fundamental units of the longest side), whatever the
+    axis and cell size: box 10 x 6 cells of 1 x 2 units (L = 10, 12)."""
+    n, cell = (10, 6), (1.0, 2.0)
+    i0, i1 = np.indices(n)
+    waves = {2.4: np.cos(2 * np.pi * 2 * i0 / 10),      # wavelength 5 units along axis 0
+             1.0: np.cos(2 * np.pi * 1 * i1 / 6),       # wavelength 12 units along axis 1
+             3.0: np.cos(2 * np.pi * 3 * i1 / 6)}       # wavelength 4 units along axis 1 (Nyquist)
+    edges = np.array([0.5, 1.5, 2.7, 3.5])
+    for q, f in waves.items():
+        pk, nm = orc.power_spectrum(f[None], n, edges, cell=cell)
+        hit = np.searchsorted(edges, q, side="right") - 1
+        assert pk[0, hit] > 0
+        assert np.all(pk[0, np.arange(3) != hit] < 1e-20 * pk[0, hit])
 
 
 def test_parseval(orc):
