@@ -352,11 +352,15 @@ CF_API cf_status cf_lognormal_poisson(const void* G, cf_dtype dt, int64_t cells_
 
 typedef enum { CF_BINS_LINEAR = 0, CF_BINS_LOG = 1, CF_BINS_EDGES = 2 } cf_bins_kind;
 
-/* Bins of |n| = sqrt(sum_i n_i^2), n_i in (-n/2, n/2] the mode index in
- * fundamental units.  Bin b is [e_b, e_{b+1}).  LINEAR: e_b = kmin + b (kmax -
- * kmin)/nbins; LOG: e_b = kmin exp(b ln(kmax/kmin)/nbins) (the paper's 20
- * ln-spaced bins); EDGES: host array edges[nbins+1], increasing.  kmax <= 0
- * means n/2.  The DC mode is never binned. */
+/* Bins of the mode length |k| in units of the fundamental frequency 2 pi/L_ref
+ * of the longest side L_ref = max_i n_i cell_i: q = sqrt(sum_i (s_i r_i)^2),
+ * s_i in (-n_i/2, n_i/2] the signed mode index and r_i = L_ref/(n_i cell_i),
+ * each operation rounded in binary64 in this order (on a cube r_i = 1 and q is
+ * the index length sqrt(sum_i s_i^2)).  Bin b is [e_b, e_{b+1}).  LINEAR:
+ * e_b = kmin + b (kmax - kmin)/nbins; LOG: e_b = kmin exp(b ln(kmax/kmin)/nbins)
+ * (the paper's 20 ln-spaced bins); EDGES: host array edges[nbins+1],
+ * increasing.  kmax <= 0 means the smallest axis Nyquist frequency in these
+ * units, min_i n_i r_i / 2 (n/2 on a cube).  The DC mode is never binned. */
 typedef struct {
     int32_t nbins;
     int32_t kind;
@@ -373,7 +377,10 @@ CF_API cf_status cf_power_spectrum_workspace_size(const cf_grid* g, int64_t nfie
  * [nfields][n...] (float for CF_F32, double for CF_F64):
  *   pk_out[f][b] = cell^d / (prod n_i * N_b) * sum_{|n| in bin b} |DFT(phi)_n|^2
  * over all modes of the full grid (both +n and -n); nmodes_out[b] = N_b
- * (int64).  ndim must be 2 or 3 with the same power-of-two n on all axes.  If mean_or_null / cov_or_null are
+ * (int64).  Any box of 1 to 3 dimensions: sides up to 4096
+ * (powers of two) or 2048 (other lengths, through Bluestein transforms),
+ * rectangular and with unequal cells (cubes with power-of-two sides take a
+ * faster path with the same results).  If mean_or_null / cov_or_null are
  * given, the mean over fields [nbins] and the unbiased (1/(F-1)) covariance
  * [nbins][nbins] are written too (section 3.2, "prediction and covariance from
  * a very large number of simulations").  Outputs are device doubles/int64. */
@@ -396,7 +403,7 @@ CF_API cf_status cf_power_spectrum_counts(const int32_t* counts, const float* f_
  * the first axis of the spectra (sections 2 and 3.2): the column pass keeps
  * each cropped column in shared memory and transforms it forward, so the
  * fields are not read back for their spectra.  Square 2D grids only (n0 = n1
- * = n, 128 <= n <= 2048, embed_factor 2), R <= 32767.  Same outputs as the
+ * = n, 128 <= n <= 2048, equal cell sides, embed_factor 2), R <= 32767.  Same outputs as the
  * separate calls: fields and counts identical, spectra equal up to rounding
  * (another order of the transform's axes).  ws / ws_bytes: the sampler
  * workspace (cf_sample_workspace_size); pk_ws: pk_ws_bytes >=

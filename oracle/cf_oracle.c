@@ -26,6 +26,7 @@
 #include "cf_oracle.h"
 
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -656,6 +657,12 @@ int32_t or_poisson_icdf(double U, double mu, double* margin)
         if (margin) *margin = INFINITY;
         return 0;
     }
+    if (!(mu < 1e9)) {
+        /* an intensity this large (or infinite, from an overflowing exp) has
+         * no count that an int32 map can hold reliably: saturate */
+        if (margin) *margin = INFINITY;
+        return INT32_MAX;
+    }
     if (mu > 700.0) return or_icdf_large(U, mu, margin);
     return or_icdf_small(U, mu, margin);
 }
@@ -684,8 +691,9 @@ void or_lognormal_poisson(const double* G, int64_t cells, int64_t nfields, doubl
 /* ======================================================================
  * Section 3.2, eq. (Def spec): P(l) = (1/V)(1/N_l) sum_{l' in bin} |phi~(l')|^2
  * over all Fourier modes of the map (both +k and -k), V = prod(n_i) cell^d,
- * phi~ = cell^d DFT(phi).  Bins are half-open [e_b, e_{b+1}) in |n|, the mode
- * index in fundamental units (n_i in (-n/2, n/2]); the DC mode is excluded.
+ * phi~ = cell^d DFT(phi).  Bins are half-open [e_b, e_{b+1}) in |k| in units
+ * of the fundamental frequency of the longest side (on a cube the mode index
+ * length |n|, n_i in (-n/2, n/2]); the DC mode is excluded.
  * ==================================================================== */
 void or_bin_edges(int32_t kind, int32_t nbins, double kmin, double kmax,
                   const double* edges_in, double* edges_out)

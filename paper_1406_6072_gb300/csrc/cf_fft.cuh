@@ -66,9 +66,21 @@ struct ColLayout {
 };
 
 // ---------------------------------------------------------------- radix kernels
-template <int SIGN, typename T>
-__device__ __forceinline__ void dft2(C2<T>& a, C2<T>& b) {
-    const C2<T> t = a;
+// Scalar type of the constants of a value type (C2<T>: T; CP: float).
+template <typename V>
+struct VScalar;
+template <typename T>
+struct VScalar<C2<T>> {
+    using type = T;
+};
+template <>
+struct VScalar<CP> {
+    using type = float;
+};
+
+template <int SIGN, typename V>
+__device__ __forceinline__ void dft2(V& a, V& b) {
+    const V t = a;
     a = t + b;
     b = t - b;
 }
@@ -81,29 +93,43 @@ __device__ __forceinline__ void dft4(C2<T>& a0, C2<T>& a1, C2<T>& a2, C2<T>& a3)
     a1 = t1 + t3;
     a3 = t1 - t3;
 }
+// paired lines: the product by SIGN i is folded into the additions
+template <int SIGN>
+__device__ __forceinline__ void dft4(CP& a0, CP& a1, CP& a2, CP& a3) {
+    const CP t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, d = a1 - a3;
+    a0 = t0 + t2;
+    a2 = t0 - t2;
+    a1 = add_si<SIGN>(t1, d);
+    a3 = sub_si<SIGN>(t1, d);
+}
 
 // multiply by exp(SIGN i theta) given (cos theta, sin theta)
 template <int SIGN, typename T>
 __device__ __forceinline__ C2<T> rot(C2<T> a, T c, T s) {
     return cmul(a, mk(c, SIGN > 0 ? s : -s));
 }
+template <int SIGN>
+__device__ __forceinline__ CP rot(CP a, float c, float s) {
+    return cmul_cs(a, c, SIGN > 0 ? s : -s);
+}
 
-template <int SIGN, typename T>
-__device__ __forceinline__ void dft8(C2<T>* v) {
+template <int SIGN, typename V>
+__device__ __forceinline__ void dft8(V* v) {
+    using T = typename VScalar<V>::type;
     dft4<SIGN>(v[0], v[2], v[4], v[6]);
     dft4<SIGN>(v[1], v[3], v[5], v[7]);
     const T h = (T)0.70710678118654752440;
-    const C2<T> o0 = v[1];
-    const C2<T> o1 = rot<SIGN>(v[3], h, h);
-    const C2<T> o2 = mul_si<SIGN>(v[5]);
-    const C2<T> o3 = rot<SIGN>(v[7], -h, h);
-    const C2<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    const V o0 = v[1];
+    const V o1 = rot<SIGN>(v[3], h, h);
+    const V o2 = v[5];  // times SIGN i, folded into the additions below
+    const V o3 = rot<SIGN>(v[7], -h, h);
+    const V e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
     v[0] = e0 + o0;
     v[4] = e0 - o0;
     v[1] = e1 + o1;
     v[5] = e1 - o1;
-    v[2] = e2 + o2;
-    v[6] = e2 - o2;
+    v[2] = add_si<SIGN>(e2, o2);
+    v[6] = sub_si<SIGN>(e2, o2);
     v[3] = e3 + o3;
     v[7] = e3 - o3;
 }
@@ -136,8 +162,8 @@ __device__ __forceinline__ void dft16(C2<T>* v) {
         for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
 }
 
-template <int R, int SIGN, typename T>
-__device__ __forceinline__ void dftR(C2<T>* v) {
+template <int R, int SIGN, typename V>
+__device__ __forceinline__ void dftR(V* v) {
     if constexpr (R == 2) {
         dft2<SIGN>(v[0], v[1]);
     } else if constexpr (R == 4) {
@@ -154,6 +180,12 @@ __device__ __forceinline__ C2<T> twiddle(const C2<T>* __restrict__ tw, int idx) 
     const C2<T> w = tw[idx];
     return SIGN > 0 ? w : mk(w.x, -w.y);
 }
+// broadcast table of the paired lines: (cos, cos, sin, sin)
+template <int SIGN>
+__device__ __forceinline__ float4 twiddle(const float4* __restrict__ tw, int idx) {
+    const float4 w = tw[idx];
+    return SIGN > 0 ? w : make_float4(w.x, w.y, -w.z, -w.w);
+}
 
 // ---------------------------------------------------------------- Stockham stages
 // v holds this thread's inputs of the stage with sub-transform size NS:
@@ -162,9 +194,9 @@ __device__ __forceinline__ C2<T> twiddle(const C2<T>* __restrict__ tw, int idx) 
 // out(line, point, value) receives each kept output of the last stage.
 // SYNC_OUT: barrier before the last stage emits its outputs, so that out()
 // may write into the exchange buffer sm itself.
-template <typename T, int L, int E, int SIGN, int KEEP, int NS, bool SYNC_OUT, class Lay, class Out>
-__device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, int j, C2<T> (&v)[E],
-                                          const C2<T>* __restrict__ tw, Out& out) {
+template <typename V, typename TW, int L, int E, int SIGN, int KEEP, int NS, bool SYNC_OUT, class Lay, class Out>
+__device__ __forceinline__ void fft_stage(V* sm, const Lay& lay, int line, int j, V (&v)[E],
+                                          const TW* __restrict__ tw, Out& out) {
     constexpr int R = (E < L / NS) ? E : (L / NS);
     constexpr int TL = L / E;
     constexpr int B = E / R;
@@ -206,7 +238,7 @@ __device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, i
         for (int b = 0; b < B2; ++b)
 #pragma unroll
             for (int q = 0; q < R2; ++q) v[b * R2 + q] = sm[lay(line, j + b * TL + q * STRIDE2)];
-        fft_stage<T, L, E, SIGN, KEEP, NS2, SYNC_OUT>(sm, lay, line, j, v, tw, out);
+        fft_stage<V, TW, L, E, SIGN, KEEP, NS2, SYNC_OUT>(sm, lay, line, j, v, tw, out);
     }
 }
 
@@ -216,7 +248,14 @@ __device__ __forceinline__ void fft_stage(C2<T>* sm, const Lay& lay, int line, i
 template <typename T, int L, int SIGN, int KEEP, bool SYNC_OUT = false, int E, class Lay, class Out>
 __device__ __forceinline__ void line_fft(C2<T>* sm, const Lay& lay, int line, int j, C2<T> (&v)[E],
                                          const C2<T>* __restrict__ tw, Out& out) {
-    fft_stage<T, L, E, SIGN, KEEP, 1, SYNC_OUT>(sm, lay, line, j, v, tw, out);
+    fft_stage<C2<T>, C2<T>, L, E, SIGN, KEEP, 1, SYNC_OUT>(sm, lay, line, j, v, tw, out);
+}
+
+// The same for two lines at once (CP values, broadcast twiddle table).
+template <int L, int SIGN, int KEEP, bool SYNC_OUT = false, int E, class Lay, class Out>
+__device__ __forceinline__ void line_fft_pair(CP* sm, const Lay& lay, int line, int j, CP (&v)[E],
+                                              const float4* __restrict__ tw, Out& out) {
+    fft_stage<CP, float4, L, E, SIGN, KEEP, 1, SYNC_OUT>(sm, lay, line, j, v, tw, out);
 }
 
 }  // namespace cf

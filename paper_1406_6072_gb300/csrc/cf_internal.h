@@ -69,6 +69,7 @@ cf_status enter(cudaStream_t s);
 cf_status enter_with(const cf_embedding* e, cudaStream_t s);
 const C2<float>* twiddles_f32();   // current device, TWN entries exp(+2 pi i j/TWN)
 const C2<double>* twiddles_f64();
+const float4* twiddles_f32x2();    // current device, (cos, cos, sin, sin) of the same angles
 
 inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int log2i(long long v) {

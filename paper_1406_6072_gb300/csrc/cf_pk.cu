@@ -26,6 +26,15 @@ namespace cf {
 
 constexpr int kMaxBins = 512;
 
+// Boxes the cubic power-of-two path below does not take (cf_pk_any.cu):
+// 1D, rectangular, sides that are not powers of two, unequal cells.
+bool pk_any_needed(const cf_grid* g);
+cf_status pk_any_workspace(const cf_grid* g, long long nfields, const cf_bins* b, cf_dtype dt, size_t* bytes);
+cf_status pk_any_run(const void* fields, int kind, const float* f, const cf_grid* g, long long nfields,
+                     const cf_bins* bins, double* pk_out, int64_t* nmodes_out, double* mean, double* cov, void* ws,
+                     size_t ws_bytes, cudaStream_t s);
+cf_status pk_bin_edges(const cf_bins* b, double kmax_default, double* e);
+
 struct Edges {
     double e[kMaxBins + 1];
 };
@@ -453,6 +462,33 @@ __global__ void __launch_bounds__(256) k_pk_cov(const double* __restrict__ pk, c
 }
 
 // ----------------------------------------------------------------- host side
+// Bin edges e[0..nbins] of a cf_bins (kmax <= 0: kmax_default).
+cf_status pk_bin_edges(const cf_bins* b, double kmax_default, double* e) {
+    const double kmax = b->kmax > 0.0 ? b->kmax : kmax_default;
+    const double kmin = b->kmin;
+    for (int i = 0; i <= b->nbins; ++i) {
+        if (b->kind == CF_BINS_LINEAR)
+            e[i] = kmin + (double)i * ((kmax - kmin) / (double)b->nbins);
+        else if (b->kind == CF_BINS_LOG) {
+            if (!(kmin > 0.0)) return fail(CF_ERR_ARG, "log bins need kmin > 0");
+            e[i] = kmin * exp((double)i * (log(kmax / kmin) / (double)b->nbins));
+        } else if (b->kind == CF_BINS_EDGES) {
+            if (!b->edges) return fail(CF_ERR_ARG, "CF_BINS_EDGES needs edges");
+            e[i] = b->edges[i];
+        } else
+            return fail(CF_ERR_ARG, "unknown bins kind %d", b->kind);
+        if (i > 0 && !(e[i] > e[i - 1])) return fail(CF_ERR_ARG, "bin edges must increase");
+    }
+    return CF_OK;
+}
+
+// pk = volfac * acc / N_b per field and bin, then the mean and unbiased
+// covariance over fields (scratch: nbins doubles for the mean when only the
+// covariance is wanted).
+cf_status pk_finish(const double* acc, const unsigned long long* nmodes, long long nfields, int nbins,
+                    double volfac, double* pk_out, int64_t* nmodes_out, double* mean, double* cov, double* scratch,
+                    cudaStream_t s);
+
 struct PkPlan {
     GridInfo g;         // survey grid (n used as the transform sizes)
     int nbins;
@@ -494,21 +530,7 @@ static cf_status make_plan(const cf_grid* grid, long long nfields, const cf_bins
     g.mtotal = g.ncell;
     if (b->nbins < 1 || b->nbins > kMaxBins) return fail(CF_ERR_ARG, "nbins must be 1..%d", kMaxBins);
     P->nbins = b->nbins;
-    const double kmax = b->kmax > 0.0 ? b->kmax : (double)(g.n[0] / 2);
-    const double kmin = b->kmin;
-    for (int i = 0; i <= b->nbins; ++i) {
-        if (b->kind == CF_BINS_LINEAR)
-            P->edges.e[i] = kmin + (double)i * ((kmax - kmin) / (double)b->nbins);
-        else if (b->kind == CF_BINS_LOG) {
-            if (!(kmin > 0.0)) return fail(CF_ERR_ARG, "log bins need kmin > 0");
-            P->edges.e[i] = kmin * exp((double)i * (log(kmax / kmin) / (double)b->nbins));
-        } else if (b->kind == CF_BINS_EDGES) {
-            if (!b->edges) return fail(CF_ERR_ARG, "CF_BINS_EDGES needs edges");
-            P->edges.e[i] = b->edges[i];
-        } else
-            return fail(CF_ERR_ARG, "unknown bins kind %d", b->kind);
-        if (i > 0 && !(P->edges.e[i] > P->edges.e[i - 1])) return fail(CF_ERR_ARG, "bin edges must increase");
-    }
+    CF_TRY(pk_bin_edges(b, (double)(g.n[0] / 2), P->edges.e));
     P->k2max = 0;
     for (int a = 0; a < g.ndim; ++a) P->k2max += (g.n[a] / 2) * (g.n[a] / 2);
     const long long nl = g.n[g.ndim - 1];
@@ -786,6 +808,22 @@ cf_status pk_from_halves_f32(const cf_grid* grid, long long F, const cf_bins* bi
     return CF_OK;
 }
 
+cf_status pk_finish(const double* acc, const unsigned long long* nmodes, long long nfields, int nbins,
+                    double volfac, double* pk_out, int64_t* nmodes_out, double* mean, double* cov, double* scratch,
+                    cudaStream_t s) {
+    ScopedKernelTimer kt(s, "pk_finalize");
+    k_pk_finalize<<<grid_blocks(nfields * nbins, 256, 1024), 256, 0, s>>>(acc, nullptr, nullptr, nullptr, nullptr, 1.0,
+                                                                          nmodes, nfields, nbins, volfac, pk_out,
+                                                                          nmodes_out);
+    if (mean || cov) {
+        double* mu = mean ? mean : scratch;
+        k_pk_mean<<<nbins, 256, 0, s>>>(pk_out, nfields, nbins, mu);
+        if (cov) k_pk_cov<<<dim3((nbins + 7) / 8, nbins), 256, 0, s>>>(pk_out, mu, nfields, nbins, cov);
+    }
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
 // Mean over rows and unbiased covariance of x [nrows][ncols] (binary64); used
 // for the power spectra and for the counts-in-cells histograms.
 cf_status launch_mean_cov(const double* x, long long nrows, int ncols, double* mean, double* cov, cudaStream_t s) {
@@ -809,6 +847,7 @@ extern "C" cf_status cf_power_spectrum_workspace_size(const cf_grid* g, int64_t 
     clear_error();
     if (!bytes) return fail(CF_ERR_ARG, "bytes is NULL");
     if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
+    if (pk_any_needed(g)) return pk_any_workspace(g, nfields, b, dt, bytes);
     PkPlan P;
     CF_TRY(make_plan(g, nfields, b, dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>), &P));
     *bytes = P.total;
@@ -822,6 +861,12 @@ static cf_status pk_common(const void* fields, int kind, cf_dtype dt, const floa
     if (!fields || !pk_out) return fail(CF_ERR_ARG, "fields and pk_out are required");
     if (nfields < 1) return fail(CF_ERR_ARG, "nfields must be >= 1");
     if (nfields > 65535) return fail(CF_ERR_UNSUPPORTED, "at most 65535 fields per call");
+    if (pk_any_needed(g)) {
+        CF_TRY(enter((cudaStream_t)s));
+        const int any_kind = kind == PK_COUNTS ? 2 : (dt == CF_F64 ? 1 : 0);
+        return pk_any_run(fields, any_kind, f, g, nfields, bins, pk_out, nmodes_out, mean, cov, ws, ws_bytes,
+                          (cudaStream_t)s);
+    }
     const size_t elem = dt == CF_F64 ? sizeof(C2<double>) : sizeof(C2<float>);
     PkPlan P;
     CF_TRY(make_plan(g, nfields, bins, elem, &P));

@@ -30,8 +30,9 @@ void clear_error() { g_last_error.clear(); }
 __device__ C2<float> g_tw32[TWN];
 __device__ C2<double> g_tw64[TWN];
 __device__ C2<DF> g_twdf[TWN];
+__device__ float4 g_tw32x2[TWN];  // (cos, cos, sin, sin): the paired-lines table
 
-__global__ void k_init_twiddles(C2<float>* tw32, C2<double>* tw64, C2<DF>* twdf) {
+__global__ void k_init_twiddles(C2<float>* tw32, C2<double>* tw64, C2<DF>* twdf, float4* tw32x2) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= TWN) return;
     double s, c;
@@ -39,6 +40,7 @@ __global__ void k_init_twiddles(C2<float>* tw32, C2<double>* tw64, C2<DF>* twdf)
     tw64[j] = mk(c, s);
     tw32[j] = mk((float)c, (float)s);
     twdf[j] = mk(df_from(c), df_from(s));
+    tw32x2[j] = make_float4((float)c, (float)c, (float)s, (float)s);
 }
 
 static constexpr int kMaxDevices = 64;
@@ -47,6 +49,7 @@ static bool g_inited[kMaxDevices];
 static C2<float>* g_tw32_ptr[kMaxDevices];
 static C2<double>* g_tw64_ptr[kMaxDevices];
 static C2<DF>* g_twdf_ptr[kMaxDevices];
+static float4* g_tw32x2_ptr[kMaxDevices];
 // Library memory pool per device: stream-ordered allocations of embeddings,
 // scratch and served results.  Freed blocks stay in the pool (release
 // threshold: unlimited), so that repeated embeddings do not map and unmap
@@ -68,15 +71,18 @@ cf_status ensure_device_init() {
     void* p32 = nullptr;
     void* p64 = nullptr;
     void* pdf = nullptr;
+    void* p32x2 = nullptr;
+    CF_CUDA(cudaGetSymbolAddress(&p32x2, g_tw32x2));
     CF_CUDA(cudaGetSymbolAddress(&p32, g_tw32));
     CF_CUDA(cudaGetSymbolAddress(&p64, g_tw64));
     CF_CUDA(cudaGetSymbolAddress(&pdf, g_twdf));
-    k_init_twiddles<<<(TWN + 255) / 256, 256>>>((C2<float>*)p32, (C2<double>*)p64, (C2<DF>*)pdf);
+    k_init_twiddles<<<(TWN + 255) / 256, 256>>>((C2<float>*)p32, (C2<double>*)p64, (C2<DF>*)pdf, (float4*)p32x2);
     CF_CHECK_LAUNCH();
     CF_CUDA(cudaDeviceSynchronize());
     g_tw32_ptr[dev] = (C2<float>*)p32;
     g_tw64_ptr[dev] = (C2<double>*)p64;
     g_twdf_ptr[dev] = (C2<DF>*)pdf;
+    g_tw32x2_ptr[dev] = (float4*)p32x2;
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -184,6 +190,7 @@ cf_status enter_with(const cf_embedding* e, cudaStream_t s) {
 const C2<float>* twiddles_f32() { return g_tw32_ptr[current_device()]; }
 const C2<double>* twiddles_f64() { return g_tw64_ptr[current_device()]; }
 const C2<DF>* twiddles_df() { return g_twdf_ptr[current_device()]; }
+const float4* twiddles_f32x2() { return g_tw32x2_ptr[current_device()]; }
 
 cf_status check_grid(const cf_grid* g, GridInfo* gi) {
     if (!g) return fail(CF_ERR_ARG, "grid is NULL");

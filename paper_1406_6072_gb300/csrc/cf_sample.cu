@@ -119,10 +119,139 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     line_fft<T, L, +1, L / 2>(sm, RowLayout<G::PADE, G::PADDED>(), line, j, v, tw, sink);
 }
 
+// --------------------------------------------------------------------------
+// Pass 1 in binary32 with two realizations per thread (rows of realizations
+// 2b and 2b + 1 of the chunk): each value holds the same point of both rows
+// (CP), so the noise's polynomials, the scaling and every transform stage run
+// as paired binary32 instructions, the amplitudes are read once for both,
+// the twiddles are shared, and the shared-memory exchange moves 16 bytes per
+// access.  E = 8 points per line and thread.  The draws are bit-identical to
+// k_sample_rows's (the same operations per lane); the transform's rounding
+// differs only by its radix order.
+// --------------------------------------------------------------------------
+#ifndef CF_SROWS2_THREADS
+#define CF_SROWS2_THREADS 128
+#endif
+#ifndef CF_SROWS2_MINB
+#define CF_SROWS2_MINB 8
+#endif
+
+template <int L>
+struct SRowsPairCfg {
+    static constexpr int E = L < 8 ? L : 8;
+    static constexpr int TL = L / E;
+    static constexpr int LINES = TL >= CF_SROWS2_THREADS ? 1 : (CF_SROWS2_THREADS / TL > 32 ? 32 : CF_SROWS2_THREADS / TL);
+    static constexpr int THREADS = LINES * TL;
+    static constexpr int MINB =
+        THREADS * CF_SROWS2_MINB <= 1024 ? CF_SROWS2_MINB : (1024 / THREADS > 0 ? 1024 / THREADS : 1);
+    static constexpr int PADDED = L + L / E;
+    static constexpr size_t SMEM = sizeof(CP) * (size_t)LINES * (size_t)PADDED;
+};
+
+template <int L, bool DESC>
+__global__ void __launch_bounds__(SRowsPairCfg<L>::THREADS, SRowsPairCfg<L>::MINB)
+    k_sample_rows_pair(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
+                       long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
+                       const float4* __restrict__ tw, const RealDesc* __restrict__ desc) {
+    using Cfg = SRowsPairCfg<L>;
+    constexpr int E = Cfg::E;
+    constexpr int STEP = L / E;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CP* sm = reinterpret_cast<CP*>(smraw);
+    const int line = threadIdx.x / Cfg::TL;
+    const int j = threadIdx.x % Cfg::TL;
+    const long long row = (long long)blockIdx.x * Cfg::LINES + line;
+    const int ra = 2 * blockIdx.y, rb = ra + 1;
+    const bool valid = row < nrows, valid_b = rb < chunk;
+    const long long rw = valid ? row : 0;
+    // lane A: realization ra, lane B: rb (its own parameters in a batched launch)
+    const float* sa_row = s + (size_t)rw * L;
+    const float* sb_row = sa_row;
+    float amp_a = amp_scale, amp_b = amp_scale;
+    uint32_t ka0 = key0, ka1 = key1, kb0 = key0, kb1 = key1, r_a = r0 + (uint32_t)ra, r_b = r0 + (uint32_t)rb;
+    if constexpr (DESC) {
+        const RealDesc& da = desc[ra];
+        const RealDesc& db = desc[valid_b ? rb : ra];
+        sa_row = da.s + (size_t)rw * L;
+        sb_row = db.s + (size_t)rw * L;
+        amp_a = da.amp_scale;
+        amp_b = db.amp_scale;
+        ka0 = da.key0;
+        ka1 = da.key1;
+        kb0 = db.key0;
+        kb1 = db.key1;
+        r_a = da.r;
+        r_b = db.r;
+    }
+    CP v[E];
+#pragma unroll
+    for (int q = 0; q < E / 2; ++q) {
+        const int col = j + q * STEP;
+        float sal, sah, sbl, sbh;
+        sal = __fmul_rn(__ldg(sa_row + col), amp_a);
+        sah = __fmul_rn(__ldg(sa_row + col + L / 2), amp_a);
+        if constexpr (DESC) {
+            sbl = __fmul_rn(__ldg(sb_row + col), amp_b);
+            sbh = __fmul_rn(__ldg(sb_row + col + L / 2), amp_b);
+        } else {
+            sbl = sal;
+            sbh = sah;
+        }
+        CP lo, hi;
+        noise_pair_f32x2((unsigned long long)rw * (L / 2) + col, r_a, ka0, ka1, r_b, kb0, kb1, lo, hi);
+        const float2 fl = make_float2(sal, sbl), fh = make_float2(sah, sbh);
+        v[q] = CP{f2mul(lo.re, fl), f2mul(lo.im, fl)};
+        v[q + E / 2] = CP{f2mul(hi.re, fh), f2mul(hi.im, fh)};
+    }
+    C2<float>* oa = out + ((size_t)ra * nrows + row) * keep;
+    C2<float>* ob = out + ((size_t)rb * nrows + row) * keep;
+    auto sink = [&](int, int p, CP val) {
+        if (!valid || p >= keep) return;
+        oa[p] = mk(val.re.x, val.im.x);
+        if (valid_b) ob[p] = mk(val.re.y, val.im.y);
+    };
+    line_fft_pair<L, +1, L / 2>(sm, RowLayout<E, Cfg::PADDED>(), line, j, v, tw, sink);
+}
+
+// Row pass of the paired kernel: used for binary32 rows of 16..4096 points
+// when pair_rows() is on (CF_SROWS_PAIR=0 in the environment turns it off).
+static bool pair_rows() {
+    static const bool on = [] {
+        const char* e = getenv("CF_SROWS_PAIR");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+static cf_status launch_sample_rows_pair(long long L, int keep, const float* s, float amp_scale, uint64_t seed,
+                                         uint32_t r0, int chunk, long long nrows, C2<float>* out, cudaStream_t st,
+                                         const RealDesc* desc) {
+    return dispatch_line(L, [&](auto Lc) -> cf_status {
+        constexpr int LL = decltype(Lc)::value;
+        if constexpr (LL < 16) {
+            return fail(CF_ERR_UNSUPPORTED, "paired rows need 16 points or more");
+        } else {
+            using Cfg = SRowsPairCfg<LL>;
+            auto kern = desc ? k_sample_rows_pair<LL, true> : k_sample_rows_pair<LL, false>;
+            CF_TRY(prepare_smem(kern, Cfg::SMEM));
+            dim3 grid((unsigned)((nrows + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((chunk + 1) / 2));
+            ScopedKernelTimer kt(st, "sample_rows_f32", LL);
+            kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
+                                                        nrows, keep, chunk, out, twiddles_f32x2(), desc);
+            CF_CHECK_LAUNCH();
+            return CF_OK;
+        }
+    });
+}
+
 template <typename T>
 static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_scale, uint64_t seed, uint32_t r0,
                                     int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
                                     cudaStream_t st, const RealDesc* desc = nullptr) {
+    if constexpr (sizeof(T) == 4) {
+        if (mode == 0 && L >= 16 && pair_rows())
+            return launch_sample_rows_pair(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc);
+    }
     return dispatch_line(L, [&](auto Lc) -> cf_status {
         constexpr int LL = decltype(Lc)::value;
         using Cfg = SRowsCfg<T, LL>;
@@ -653,6 +782,7 @@ static cf_status spectra_layout(const cf_embedding* e, int32_t R, const cf_bins*
     if (g.ndim != 2 || g.n[0] != g.n[1] || g.m[0] != 2 * g.n[0] || g.m[1] != 2 * g.n[1] || g.m[0] < 256 ||
         g.m[0] > 4096)
         return fail(CF_ERR_UNSUPPORTED, "fused spectra need a square 2D survey of side 128..2048 embedded in 2n");
+    if (g.cell[0] != g.cell[1]) return fail(CF_ERR_UNSUPPORTED, "fused spectra need equal cell sides");
     if (R < 1 || 2ll * R > 65535) return fail(CF_ERR_ARG, "R must be 1..32767");
     *grid = cf_grid{};
     grid->ndim = 2;

@@ -68,12 +68,21 @@ def test_argument_errors_before_any_cuda_call(cfmod):
     assert lib.cf_draw_noise(0, 2**32 - 1, 2, 16, 4, cfmod.CF_F32, C.c_void_p(8), None) == cfmod.CF_ERR_ARG
     n = C.c_size_t()
     b = cfmod.make_bins(8)
-    g1 = cfmod.make_grid((16,))
-    assert lib.cf_power_spectrum_workspace_size(C.byref(g1), 4, C.byref(b), cfmod.CF_F32, C.byref(n)) == \
-        cfmod.CF_ERR_UNSUPPORTED
-    gr = cfmod.make_grid((16, 32))
-    assert lib.cf_power_spectrum_workspace_size(C.byref(gr), 4, C.byref(b), cfmod.CF_F32, C.byref(n)) == \
-        cfmod.CF_ERR_UNSUPPORTED
+    # any box: 1D, rectangular and non-power-of-two sides are accepted ...
+    for shape in ((16,), (16, 32), (100, 60), (48, 80, 40)):
+        gq = cfmod.make_grid(shape)
+        assert lib.cf_power_spectrum_workspace_size(C.byref(gq), 4, C.byref(b), cfmod.CF_F32, C.byref(n)) == \
+            cfmod.CF_OK
+        assert n.value > 0
+    # ... up to 2048 points for other lengths (Bluestein) and 4096 for powers of two
+    for shape in ((3000, 16), (8192, 2)):
+        gq = cfmod.make_grid(shape)
+        assert lib.cf_power_spectrum_workspace_size(C.byref(gq), 4, C.byref(b), cfmod.CF_F32, C.byref(n)) == \
+            cfmod.CF_ERR_UNSUPPORTED
+    g4b = cfmod.make_grid((4, 4, 4))
+    g4b.ndim = 4
+    assert lib.cf_power_spectrum_workspace_size(C.byref(g4b), 4, C.byref(b), cfmod.CF_F32, C.byref(n)) == \
+        cfmod.CF_ERR_ARG
     gs = cfmod.make_grid((16, 16))
     assert lib.cf_power_spectrum_workspace_size(C.byref(gs), 4, C.byref(b), cfmod.CF_F32, C.byref(n)) == cfmod.CF_OK
     assert n.value > 0

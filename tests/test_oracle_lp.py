@@ -45,6 +45,18 @@ def test_icdf_zero_intensity(orc):
         assert orc.poisson_icdf(U, -1.0)[0] == 0
 
 
+def test_icdf_large_intensity(orc):
+    """Up to 1e9 the walk from the mode still matches scipy; from 1e9 on (and
+    for an infinite intensity, an overflowing exp) the count saturates at the
+    int32 maximum instead of walking billions of terms."""
+    for mu in (2e5, 3e7, 9.9e8):
+        for U in (0.01, 0.5, 0.97):
+            n, _ = orc.poisson_icdf(U, mu)
+            assert abs(n - stats.poisson.ppf(U, mu)) <= 1, (mu, U, n)
+    for mu in (1e9, 1e12, np.inf):
+        assert orc.poisson_icdf(0.5, mu)[0] == 2**31 - 1
+
+
 def test_margin_flips_decision(orc):
     rng = np.random.default_rng(4)
     for _ in range(400):
