@@ -698,6 +698,8 @@ def run_serving(args):
         lock = th.Lock()
         done_flag = [False]
 
+        parts = []  # (latency, queue, run, cache hit) per request
+
         def waiter():
             k = 0
             clamped = 0
@@ -714,6 +716,8 @@ def run_serving(args):
                     continue
                 r = cf.cf_serve_wait(sv, t, -1)
                 clamped += r["embed"]["clamped"]
+                if r["status"] == cf.CF_OK:
+                    parts.append((r["latency_ms"], r["queue_ms"], r["run_ms"], r["cache_hit"]))
                 cf.cf_serve_release(sv, t)
                 k += 1
             waiter.clamped = clamped
@@ -737,6 +741,16 @@ def run_serving(args):
         cf.cf_serve_destroy(sv)
         st["wall_s"] = wall
         st["clamped_requests"] = waiter.clamped
+        # where the time goes: queueing (waiting for a slot, memory or the
+        # spectrum's build) against running, and cache hits against misses
+        a = np.asarray(parts, dtype=np.float64).reshape(-1, 4)
+        pct = lambda x, q: float(np.percentile(x, q)) if x.size else None
+        hit, miss = a[a[:, 3] == 1], a[a[:, 3] == 0]
+        st["attribution"] = {"p50_queue_ms": pct(a[:, 1], 50), "p99_queue_ms": pct(a[:, 1], 99),
+                             "p50_run_ms": pct(a[:, 2], 50), "p99_run_ms": pct(a[:, 2], 99),
+                             "p99_ms_cache_hit": pct(hit[:, 0], 99), "p99_ms_cache_miss": pct(miss[:, 0], 99),
+                             "p50_ms_cache_miss": pct(miss[:, 0], 50),
+                             "miss_fraction": float(miss.shape[0] / max(1, a.shape[0]))}
         return st
 
     n_cap = min(1000, len(base))
@@ -754,7 +768,7 @@ def run_serving(args):
                               "realizations_per_s": st["realizations_per_s"], "batches": st["batches"],
                               "batched_requests": st["batched_requests"], "cache_hits": st["cache_hits"],
                               "cache_misses": st["cache_misses"], "peak_gb": st["bytes_peak"] / 1e9,
-                              "clamped_requests": st["clamped_requests"]}
+                              "clamped_requests": st["clamped_requests"], "attribution": st["attribution"]}
     # sequential binary64 path on a subsample
     rng = np.random.default_rng(7)
     sub = [base[i] for i in rng.choice(len(base), size=min(200, len(base)), replace=False)]
@@ -934,7 +948,8 @@ def main():
         with torch.cuda.stream(stream):
             pipe.embed()
             chunk, tms = pipe.tune()
-            tuned = {"chunk": chunk, "ms_per_realization": tms}
+            _, rshape, cshape = cf.cf_tune_info(pipe.emb, pipe.dtype)
+            tuned = {"chunk": chunk, "rows_shape": rshape, "cols_shape": cshape, "ms_per_realization": tms}
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
             run_step(k)
@@ -993,7 +1008,7 @@ def main():
                        "cells_per_step": cells_all, "realizations_per_s": R * world / (ms_max * 1e-3),
                        "l2": "each step writes %d MiB of fields and counts (> 129 MB L2)"
                              % (2 * pipe.cells_per_step * 4 >> 20),
-                       "parallelism": "replicas x%d" % world, "tuned_chunk": tuned,
+                       "parallelism": "replicas x%d" % world, "tuned_schedule": tuned,
                        "fused_spectra": bool(pipe.fused), "eigenvalue_transforms": "double-float" if args.embed_df
                        else "binary64", "lanes": len(lanes)},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,

@@ -255,16 +255,30 @@ CF_API cf_status cf_sample(const cf_embedding* e, uint64_t seed, uint64_t r0, in
 CF_API cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uint64_t r0, int32_t R,
                                    void* fields_out, cf_stream_t s);
 
-/* Autotuner of the sampler's chunk schedule (realizations per launch of the
- * transform passes).  Times cf_sample on R realizations of e for each
- * candidate chunk that fits ws_bytes (1, 2, 4, ... up to R), writing into
- * fields_scratch ([R][2][n...] of dt), and records the fastest for this
- * device, grid shape and dtype; later cf_sample / cf_sample_lp /
- * cf_sample_workspace_size calls with that shape use it.  Synchronises s.
- * *chunk_out (may be NULL) receives the chosen chunk, *ms_out (may be NULL)
- * its time per realization. */
+/* Autotuner of the sampler's schedule.  Times cf_sample on R realizations of
+ * e for each candidate chunk that fits ws_bytes (realizations per launch of
+ * the transform passes: 1, 2, 4, ... up to R), then, in binary32 on grids
+ * with a side of 256 or more, each of the 3 CTA shapes of the paired row
+ * pass (and of the paired column pass, where it is enabled) at the best
+ * chunk, writing into fields_scratch
+ * ([R][2][n...] of dt), and records the fastest for this device, grid shape
+ * and dtype; later cf_sample / cf_sample_lp / cf_sample_workspace_size calls
+ * and served batches with that shape use it (cf_tune_info reads it).
+ * Synchronises s.  *chunk_out (may be NULL) receives the chosen chunk,
+ * *ms_out (may be NULL) its time per realization. */
 CF_API cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, void* ws, size_t ws_bytes,
                                 void* fields_scratch, cf_stream_t s, int32_t* chunk_out, double* ms_out);
+
+/* The sampler schedule recorded for e's grid and dt on the current device:
+ * realizations per launch (0: the default, chunks of up to 1 GiB of
+ * intermediate) and the CTA shapes (0, 1, 2; 0 the default) of the binary32
+ * passes with two realizations per thread.  cf_tune_sample records the
+ * fastest; cf_tune_set records a given one (chunk 0 and shapes 0 clear the
+ * record).  Shapes and chunks change no result bit. */
+CF_API cf_status cf_tune_info(const cf_embedding* e, cf_dtype dt, int32_t* chunk, int32_t* rows_shape,
+                              int32_t* cols_shape);
+CF_API cf_status cf_tune_set(const cf_embedding* e, cf_dtype dt, int32_t chunk, int32_t rows_shape,
+                             int32_t cols_shape);
 
 /* Tensor-core modes: number of tensor-core waits that ran out of time (1 s
  * each) on the current device since the last call; synchronises s and

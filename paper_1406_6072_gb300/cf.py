@@ -137,6 +137,8 @@ _sigs = {
     "cf_plan_destroy": [_P],
     "cf_tune_sample": [_P, C.c_int32, C.c_int32, _P, C.c_size_t, _P, _S, C.POINTER(C.c_int32),
                        C.POINTER(C.c_double)],
+    "cf_tune_info": [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "cf_tune_set": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
     "cf_lognormal_poisson": [_P, C.c_int32, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, C.c_uint64,
                              C.c_uint64, _P, _P, _S],
     "cf_power_spectrum_workspace_size": [C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), C.c_int32,
@@ -345,6 +347,17 @@ def cf_tune_sample(emb, dtype, R, ws, ws_bytes, fields_scratch, stream=None):
     _check(_lib.cf_tune_sample(emb.handle, dtype, R, _ptr(ws), ws_bytes, _ptr(fields_scratch), _stream(stream),
                                C.byref(c), C.byref(ms)), "cf_tune_sample")
     return c.value, ms.value
+
+
+def cf_tune_info(emb, dtype):
+    """The recorded sampler schedule: (chunk, rows_shape, cols_shape)."""
+    c, r, k = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib.cf_tune_info(emb.handle, dtype, C.byref(c), C.byref(r), C.byref(k)), "cf_tune_info")
+    return c.value, r.value, k.value
+
+
+def cf_tune_set(emb, dtype, chunk=0, rows_shape=0, cols_shape=0):
+    _check(_lib.cf_tune_set(emb.handle, dtype, chunk, rows_shape, cols_shape), "cf_tune_set")
 
 
 def cf_cic_histogram(counts, cells, nfields, f, nbins, hist_out, mean=None, cov=None, stream=None):

@@ -249,6 +249,227 @@ __global__ void __launch_bounds__(PkRowsCfg<T, L>::THREADS, PkRowsCfg<T, L>::MIN
     }
 }
 
+// --------------------------------------------------------------------------
+// Binary32 row and binning passes on two lines per thread (CP values, paired
+// f32x2 instructions, 16-byte shared-memory exchanges, shared twiddles).
+// Rows: lane A carries fields (fa, fa+1) as z = a + i b, lane B fields
+// (fa+2, fa+3): four fields per thread.  Binning: lane A field fa, lane B
+// field fa+1 at the same column, so both take the same bin decisions.  The
+// spectra equal the one-line kernels' up to the rounding of the transform's
+// radix order.
+// --------------------------------------------------------------------------
+template <int L, int TARGET>
+struct PkPairCfg {
+    static constexpr int E = L < 8 ? L : 8;
+    static constexpr int TL = L / E;
+    static constexpr int LINES = TL >= TARGET ? 1 : (TARGET / TL > 32 ? 32 : TARGET / TL);
+    static constexpr int THREADS = LINES * TL;
+    static constexpr int MINB = 1024 / THREADS > 8 ? 8 : (1024 / THREADS > 0 ? 1024 / THREADS : 1);
+    static constexpr int PADDED = L + L / E;
+    static constexpr size_t SMEM = sizeof(CP) * (size_t)LINES * (size_t)PADDED;
+};
+#ifndef CF_PKR2_THREADS
+#define CF_PKR2_THREADS 128
+#endif
+#ifndef CF_PKC2_THREADS
+#define CF_PKC2_THREADS 256
+#endif
+
+template <int L, int KIND>
+__global__ void __launch_bounds__(PkPairCfg<L, CF_PKR2_THREADS>::THREADS, PkPairCfg<L, CF_PKR2_THREADS>::MINB)
+    k_pk_rows_pair(const void* __restrict__ fields, const float* __restrict__ f, unsigned long long* __restrict__ ntot,
+                   long long rows, long long cells, long long nfields, long long f0, C2<float>* __restrict__ out,
+                   const float4* __restrict__ tw) {
+    using Cfg = PkPairCfg<L, CF_PKR2_THREADS>;
+    constexpr int E = Cfg::E;
+    constexpr int STEP = L / E;
+    constexpr int H = L / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CP* sm = reinterpret_cast<CP*>(smraw);
+    const int line = threadIdx.x / Cfg::TL;
+    const int j = threadIdx.x % Cfg::TL;
+    const long long row = (long long)blockIdx.x * Cfg::LINES + line;
+    const bool valid = row < rows;
+    const long long rw = valid ? row : 0;
+    const long long fa = f0 + 4ll * blockIdx.y;  // fields fa .. fa + 3
+    bool has[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) has[q] = fa + q < nfields;
+    unsigned long long nsum[4] = {0, 0, 0, 0};
+    CP v[E];
+    if constexpr (KIND == PK_FLOAT) {
+        const float* src[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) src[q] = (const float*)fields + (size_t)(has[q] ? fa + q : fa) * cells + (size_t)rw * L;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int p = j + q * STEP;
+            const float a = src[0][p], b = has[1] ? src[1][p] : 0.0f;
+            const float c = has[2] ? src[2][p] : 0.0f, d = has[3] ? src[3][p] : 0.0f;
+            v[q] = CP{make_float2(a, c), make_float2(b, d)};
+        }
+    } else {
+        const int32_t* src[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            src[q] = (const int32_t*)fields + (size_t)(has[q] ? fa + q : fa) * cells + (size_t)rw * L;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int p = j + q * STEP;
+            int32_t n[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) n[k] = has[k] ? src[k][p] : 0;
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nsum[k] += (unsigned long long)(long long)n[k];
+            }
+            float x[4];
+            if (f) {
+                const float fi = f[rw * L + p];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x[k] = fi != 0.0f ? (float)n[k] / fi : 0.0f;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x[k] = (float)n[k];
+            }
+            v[q] = CP{make_float2(x[0], x[2]), make_float2(x[1], x[3])};
+        }
+        // totals of the block: warp sums, one atomic per block and field
+        constexpr int NW = Cfg::THREADS / 32 > 0 ? Cfg::THREADS / 32 : 1;
+        __shared__ unsigned long long s_n[4][NW];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            for (int o = 16; o > 0; o >>= 1) nsum[k] += __shfl_down_sync(0xffffffffu, nsum[k], o);
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_n[k][threadIdx.x >> 5] = nsum[k];
+        __syncthreads();
+        if (threadIdx.x < 4 && has[threadIdx.x]) {
+            unsigned long long t = 0;
+            for (int w = 0; w < NW; ++w) t += s_n[threadIdx.x][w];
+            if (t) atomicAdd(&ntot[fa + threadIdx.x], t);
+        }
+    }
+    RowLayout<E, Cfg::PADDED> lay;
+    auto to_smem = [&](int ln, int p, CP val) { sm[lay(ln, p)] = val; };
+    line_fft_pair<L, -1, L, true>(sm, lay, line, j, v, tw, to_smem);
+    __syncthreads();
+    if (!valid) return;
+    C2<float>* o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = out + ((size_t)(fa + q - f0) * rows + row) * H;
+    const float2 half = make_float2(0.5f, 0.5f);
+    for (int k = j; k < H; k += Cfg::TL) {
+        const CP zk = sm[lay(line, k & (L - 1))];
+        const CP zm = sm[lay(line, (L - k) & (L - 1))];
+        // lanes: (field fa, fa+2) for the real parts' spectra, (fa+1, fa+3) for the imaginary parts'
+        const float2 ar = f2mul(half, f2add(zk.re, zm.re)), ai = f2mul(half, f2sub(zk.im, zm.im));
+        const float2 br = f2mul(half, f2add(zk.im, zm.im)), bi = f2mul(half, f2sub(zm.re, zk.re));
+        o[0][k] = mk(ar.x, ai.x);
+        if (has[1]) o[1][k] = mk(br.x, bi.x);
+        if (has[2]) o[2][k] = mk(ar.y, ai.y);
+        if (has[3]) o[3][k] = mk(br.y, bi.y);
+    }
+}
+
+// Binning pass of fields fa = 2 blockIdx.y and fa + 1 of the chunk (no mask
+// cross term): the transform along axis 0 of their half spectra, then the
+// weighted powers of both, summed per run of equal bins and added to
+// shared bins.
+template <int L>
+__global__ void __launch_bounds__(PkPairCfg<L, CF_PKC2_THREADS>::THREADS, PkPairCfg<L, CF_PKC2_THREADS>::MINB)
+    k_pk_cols_pair(const C2<float>* __restrict__ in, long long inner, long long H, long long n_mid, long long n_last,
+                   const int16_t* __restrict__ bin_of, long long k2max, int nbins, long long nchunk,
+                   double* __restrict__ acc, long long f0, const float4* __restrict__ tw) {
+    using Cfg = PkPairCfg<L, CF_PKC2_THREADS>;
+    constexpr int E = Cfg::E;
+    constexpr int C = Cfg::LINES;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CP* sm = reinterpret_cast<CP*>(smraw);
+    float* sbin = reinterpret_cast<float*>(sm + (size_t)C * Cfg::PADDED);  // [2][nbins]
+    int* sthr = reinterpret_cast<int*>(sbin + 2 * nbins);
+    const int* thr = bin_thresholds(bin_of, k2max);
+    for (int b = threadIdx.x; b < 2 * nbins; b += blockDim.x) sbin[b] = 0.0f;
+    for (int b = threadIdx.x; b <= nbins; b += blockDim.x) sthr[b] = thr[b];
+    const int ln = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    const long long i = (long long)blockIdx.x * C + ln;
+    const long long oa = 2ll * blockIdx.y, ob = oa + 1;
+    const bool valid = i < inner, has_b = ob < nchunk;
+    const size_t col = (size_t)(valid ? i : 0);
+    const C2<float>* sa = in + (size_t)oa * L * (size_t)inner + col;
+    const C2<float>* sb = in + (size_t)(has_b ? ob : oa) * L * (size_t)inner + col;
+    CP v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const size_t at = (size_t)(j + q * (L / E)) * (size_t)inner;
+        const C2<float> a = sa[at], b = sb[at];
+        v[q] = CP{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+    }
+    ColLayout<E, C> lay;
+    auto to_smem = [&](int lnn, int p, CP val) { sm[lay(lnn, p)] = val; };
+    line_fft_pair<L, -1, L, true>(sm, lay, ln, j, v, tw, to_smem);
+    __syncthreads();
+    if (valid) {
+        const int il = (int)(i % H);
+        const int smid = (int)signed_mode(i / H, n_mid);
+        const int c2 = smid * smid + il * il;
+        const float w = (il == 0 || 2 * (long long)il == n_last) ? 1.0f : 2.0f;
+        const float2 ww = make_float2(w, w);
+        const int t_first = sthr[0], t_end = sthr[nbins];
+        int cur = -1;
+        int lo_t = 0, hi_t = 0;
+        float2 run = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+        for (int t = 0; t < E; ++t) {
+            const int p = j * E + t;
+            const CP x = sm[lay(ln, p)];
+            const int s0 = p <= L / 2 ? p : p - L;
+            const int k2 = s0 * s0 + c2;
+            int b = cur;
+            if (k2 < lo_t || k2 >= hi_t) {
+                if (k2 < t_first || k2 >= t_end) {
+                    b = -1;
+                    lo_t = hi_t = 0;
+                } else {
+                    if (cur >= 0) {
+                        b = cur;
+                        while (k2 >= sthr[b + 1]) ++b;
+                        while (k2 < sthr[b]) --b;
+                    } else {
+                        int lo = 0, hi = nbins;
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sthr[mid] <= k2) lo = mid; else hi = mid;
+                        }
+                        b = lo;
+                    }
+                    lo_t = sthr[b];
+                    hi_t = sthr[b + 1];
+                }
+            }
+            if (b != cur) {
+                if (cur >= 0) {
+                    atomicAdd(&sbin[cur], run.x);
+                    atomicAdd(&sbin[nbins + cur], run.y);
+                }
+                cur = b;
+                run = make_float2(0.0f, 0.0f);
+            }
+            if (b >= 0) run = f2fma(ww, f2fma(x.re, x.re, f2mul(x.im, x.im)), run);
+        }
+        if (cur >= 0) {
+            atomicAdd(&sbin[cur], run.x);
+            atomicAdd(&sbin[nbins + cur], run.y);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        if (sbin[b] != 0.0f) atomicAdd(&acc[(size_t)(f0 + oa) * nbins + b], (double)sbin[b]);
+        if (has_b && sbin[nbins + b] != 0.0f) atomicAdd(&acc[(size_t)(f0 + ob) * nbins + b], (double)sbin[nbins + b]);
+    }
+}
+
 // Modes per bin over the full grid, counted on the half spectrum with the
 // mirror weights; with a mask spectrum also sum w |DFT I|^2 per bin.
 template <typename T>
@@ -683,6 +904,47 @@ static cf_status launch_pk_cols(const C2<T>* in, long long inner, long long n_mi
     return CF_OK;
 }
 
+// The paired binary32 row and binning passes (off with CF_PK_PAIR=0 in the
+// environment); the masked count maps' cross term keeps the one-line kernels.
+static bool pk_pair() {
+    static const bool on = [] {
+        const char* e = getenv("CF_PK_PAIR");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+template <int L>
+static cf_status launch_pk_rows_pair(const void* fields, int kind, const float* f, unsigned long long* ntot,
+                                     const PkPlan& P, long long nfields, long long f0, long long nchunk,
+                                     C2<float>* out, cudaStream_t s) {
+    using Cfg = PkPairCfg<L, CF_PKR2_THREADS>;
+    auto kern = kind == PK_COUNTS ? k_pk_rows_pair<L, PK_COUNTS> : k_pk_rows_pair<L, PK_FLOAT>;
+    CF_TRY(prepare_smem(kern, Cfg::SMEM));
+    dim3 grid((unsigned)((P.rows + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((nchunk + 3) / 4));
+    ScopedKernelTimer kt(s, "pk_rows_f32", L);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(fields, f, ntot, P.rows, P.g.ncell, nfields, f0, out,
+                                               twiddles_f32x2());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+template <int L>
+static cf_status launch_pk_cols_pair(const C2<float>* in, long long inner, long long n_mid, const PkPlan& P,
+                                     const int16_t* bin_of, double* acc, long long f0, long long nchunk,
+                                     cudaStream_t s) {
+    using Cfg = PkPairCfg<L, CF_PKC2_THREADS>;
+    auto kern = k_pk_cols_pair<L>;
+    const size_t smem = Cfg::SMEM + 2 * sizeof(float) * (size_t)P.nbins + sizeof(int) * (size_t)(P.nbins + 1);
+    CF_TRY(prepare_smem(kern, smem));
+    dim3 grid((unsigned)((inner + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((nchunk + 1) / 2));
+    ScopedKernelTimer kt(s, "pk_cols_f32", L);
+    kern<<<grid, Cfg::THREADS, smem, s>>>(in, inner, P.H, n_mid, P.g.n[P.g.ndim - 1], bin_of, P.k2max, P.nbins,
+                                          nchunk, acc, f0, twiddles_f32x2());
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
 // Transform along the remaining axes of half spectra [nc][rows][H] in place
 // except the first axis (3D: axis 1).
 template <typename T>
@@ -734,15 +996,26 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
             g.n[0], n_mid, P.H, nl, bin_of, P.k2max, P.nbins, mask_spec, nullptr, mpow);
     }
     CF_CHECK_LAUNCH();
+    const bool paired = sizeof(T) == 4 && pk_pair() && (kind == PK_FLOAT || kind == PK_COUNTS);
     for (long long f0 = 0; f0 < nfields; f0 += P.chunk) {
         const long long nc = (nfields - f0) < P.chunk ? (nfields - f0) : P.chunk;
         CF_TRY(dispatch_line(nl, [&](auto Lc) -> cf_status {
-            return launch_pk_rows<T, decltype(Lc)::value>(fields, kind, f, ntot, fsum, P, nfields, f0, nc, half, s);
+            constexpr int LL = decltype(Lc)::value;
+            if constexpr (sizeof(T) == 4 && LL >= 16) {
+                if (paired)
+                    return launch_pk_rows_pair<LL>(fields, kind, f, ntot, P, nfields, f0, nc, (C2<float>*)half, s);
+            }
+            return launch_pk_rows<T, LL>(fields, kind, f, ntot, fsum, P, nfields, f0, nc, half, s);
         }));
         CF_TRY(pk_middle_axis<T>(P, half, nc, s));
         CF_TRY(dispatch_line(g.n[0], [&](auto Lc) -> cf_status {
-            return launch_pk_cols<T, decltype(Lc)::value>(half, inner, n_mid, P, bin_of, acc, masked ? cross : nullptr,
-                                                          masked ? mask_spec : nullptr, f0, nc, s);
+            constexpr int LL = decltype(Lc)::value;
+            if constexpr (sizeof(T) == 4 && LL >= 16) {
+                if (paired && !masked)
+                    return launch_pk_cols_pair<LL>((const C2<float>*)half, inner, n_mid, P, bin_of, acc, f0, nc, s);
+            }
+            return launch_pk_cols<T, LL>(half, inner, n_mid, P, bin_of, acc, masked ? cross : nullptr,
+                                         masked ? mask_spec : nullptr, f0, nc, s);
         }));
     }
     double volfac = 1.0;

@@ -119,102 +119,18 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
     line_fft<T, L, +1, L / 2>(sm, RowLayout<G::PADE, G::PADDED>(), line, j, v, tw, sink);
 }
 
-// --------------------------------------------------------------------------
-// Pass 1 in binary32 with two realizations per thread (rows of realizations
-// 2b and 2b + 1 of the chunk): each value holds the same point of both rows
-// (CP), so the noise's polynomials, the scaling and every transform stage run
-// as paired binary32 instructions, the amplitudes are read once for both,
-// the twiddles are shared, and the shared-memory exchange moves 16 bytes per
-// access.  E = 8 points per line and thread.  The draws are bit-identical to
-// k_sample_rows's (the same operations per lane); the transform's rounding
-// differs only by its radix order.
-// --------------------------------------------------------------------------
-#ifndef CF_SROWS2_THREADS
-#define CF_SROWS2_THREADS 128
-#endif
-#ifndef CF_SROWS2_MINB
-#define CF_SROWS2_MINB 8
-#endif
+// Paired binary32 passes (cf_sample_pair.cu): two realizations (or two
+// slabs) per thread in f32x2 instructions; `shape` picks the CTA shape
+// (0 = default; all shapes give identical results).
+constexpr int kPairShapes = 3;
+cf_status launch_rows_pair(long long L, int keep, const float* s, float amp_scale, uint64_t seed, uint32_t r0,
+                           int chunk, long long nrows, C2<float>* out, cudaStream_t st, const RealDesc* desc,
+                           int shape);
+cf_status launch_cols_pair(long long L, const C2<float>* in, long long outer, long long inner, C2<float>* out,
+                           int mode, const FieldEpi<float>& epi, cudaStream_t st, long long keep, int shape);
 
-template <int L>
-struct SRowsPairCfg {
-    static constexpr int E = L < 8 ? L : 8;
-    static constexpr int TL = L / E;
-    static constexpr int LINES = TL >= CF_SROWS2_THREADS ? 1 : (CF_SROWS2_THREADS / TL > 32 ? 32 : CF_SROWS2_THREADS / TL);
-    static constexpr int THREADS = LINES * TL;
-    static constexpr int MINB =
-        THREADS * CF_SROWS2_MINB <= 1024 ? CF_SROWS2_MINB : (1024 / THREADS > 0 ? 1024 / THREADS : 1);
-    static constexpr int PADDED = L + L / E;
-    static constexpr size_t SMEM = sizeof(CP) * (size_t)LINES * (size_t)PADDED;
-};
-
-template <int L, bool DESC>
-__global__ void __launch_bounds__(SRowsPairCfg<L>::THREADS, SRowsPairCfg<L>::MINB)
-    k_sample_rows_pair(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
-                       long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
-                       const float4* __restrict__ tw, const RealDesc* __restrict__ desc) {
-    using Cfg = SRowsPairCfg<L>;
-    constexpr int E = Cfg::E;
-    constexpr int STEP = L / E;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    CP* sm = reinterpret_cast<CP*>(smraw);
-    const int line = threadIdx.x / Cfg::TL;
-    const int j = threadIdx.x % Cfg::TL;
-    const long long row = (long long)blockIdx.x * Cfg::LINES + line;
-    const int ra = 2 * blockIdx.y, rb = ra + 1;
-    const bool valid = row < nrows, valid_b = rb < chunk;
-    const long long rw = valid ? row : 0;
-    // lane A: realization ra, lane B: rb (its own parameters in a batched launch)
-    const float* sa_row = s + (size_t)rw * L;
-    const float* sb_row = sa_row;
-    float amp_a = amp_scale, amp_b = amp_scale;
-    uint32_t ka0 = key0, ka1 = key1, kb0 = key0, kb1 = key1, r_a = r0 + (uint32_t)ra, r_b = r0 + (uint32_t)rb;
-    if constexpr (DESC) {
-        const RealDesc& da = desc[ra];
-        const RealDesc& db = desc[valid_b ? rb : ra];
-        sa_row = da.s + (size_t)rw * L;
-        sb_row = db.s + (size_t)rw * L;
-        amp_a = da.amp_scale;
-        amp_b = db.amp_scale;
-        ka0 = da.key0;
-        ka1 = da.key1;
-        kb0 = db.key0;
-        kb1 = db.key1;
-        r_a = da.r;
-        r_b = db.r;
-    }
-    CP v[E];
-#pragma unroll
-    for (int q = 0; q < E / 2; ++q) {
-        const int col = j + q * STEP;
-        float sal, sah, sbl, sbh;
-        sal = __fmul_rn(__ldg(sa_row + col), amp_a);
-        sah = __fmul_rn(__ldg(sa_row + col + L / 2), amp_a);
-        if constexpr (DESC) {
-            sbl = __fmul_rn(__ldg(sb_row + col), amp_b);
-            sbh = __fmul_rn(__ldg(sb_row + col + L / 2), amp_b);
-        } else {
-            sbl = sal;
-            sbh = sah;
-        }
-        CP lo, hi;
-        noise_pair_f32x2((unsigned long long)rw * (L / 2) + col, r_a, ka0, ka1, r_b, kb0, kb1, lo, hi);
-        const float2 fl = make_float2(sal, sbl), fh = make_float2(sah, sbh);
-        v[q] = CP{f2mul(lo.re, fl), f2mul(lo.im, fl)};
-        v[q + E / 2] = CP{f2mul(hi.re, fh), f2mul(hi.im, fh)};
-    }
-    C2<float>* oa = out + ((size_t)ra * nrows + row) * keep;
-    C2<float>* ob = out + ((size_t)rb * nrows + row) * keep;
-    auto sink = [&](int, int p, CP val) {
-        if (!valid || p >= keep) return;
-        oa[p] = mk(val.re.x, val.im.x);
-        if (valid_b) ob[p] = mk(val.re.y, val.im.y);
-    };
-    line_fft_pair<L, +1, L / 2>(sm, RowLayout<E, Cfg::PADDED>(), line, j, v, tw, sink);
-}
-
-// Row pass of the paired kernel: used for binary32 rows of 16..4096 points
-// when pair_rows() is on (CF_SROWS_PAIR=0 in the environment turns it off).
+// Binary32 row pass with two realizations per thread (CF_SROWS_PAIR=0 in the
+// environment turns it off).
 static bool pair_rows() {
     static const bool on = [] {
         const char* e = getenv("CF_SROWS_PAIR");
@@ -223,34 +139,40 @@ static bool pair_rows() {
     return on;
 }
 
-static cf_status launch_sample_rows_pair(long long L, int keep, const float* s, float amp_scale, uint64_t seed,
-                                         uint32_t r0, int chunk, long long nrows, C2<float>* out, cudaStream_t st,
-                                         const RealDesc* desc) {
-    return dispatch_line(L, [&](auto Lc) -> cf_status {
-        constexpr int LL = decltype(Lc)::value;
-        if constexpr (LL < 16) {
-            return fail(CF_ERR_UNSUPPORTED, "paired rows need 16 points or more");
-        } else {
-            using Cfg = SRowsPairCfg<LL>;
-            auto kern = desc ? k_sample_rows_pair<LL, true> : k_sample_rows_pair<LL, false>;
-            CF_TRY(prepare_smem(kern, Cfg::SMEM));
-            dim3 grid((unsigned)((nrows + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((chunk + 1) / 2));
-            ScopedKernelTimer kt(st, "sample_rows_f32", LL);
-            kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
-                                                        nrows, keep, chunk, out, twiddles_f32x2(), desc);
-            CF_CHECK_LAUNCH();
-            return CF_OK;
-        }
-    });
+// Paired column passes of the binary32 sampler: off unless CF_SCOLS_PAIR=1
+// in the environment.  Measured slower than k_cols on the 512^2 workload
+// (0.327 against 0.296 ms per step): the column pass is bound by its
+// lognormal + Poisson epilogue, which runs per line, and 8 points per thread
+// take one more exchange stage than k_cols's 16.  Its fields differ from
+// k_cols's (and from the fused spectra path's) in rounding only.
+static bool pair_cols() {
+    static const bool on = [] {
+        const char* e = getenv("CF_SCOLS_PAIR");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+// Column pass of the sampler over in[outer][L][inner] keeping `keep` < = L/2
+// outputs: the paired kernel in binary32 (lines of 16 points or more), else
+// k_cols.
+template <typename T>
+static cf_status launch_sampler_cols(long long L, const C2<T>* in, long long outer, long long inner, C2<T>* out,
+                                     int mode, const FieldEpi<T>& epi, cudaStream_t st, long long keep,
+                                     int shape = 0) {
+    if constexpr (sizeof(T) == 4) {
+        if (L >= 16 && pair_cols()) return launch_cols_pair(L, in, outer, inner, out, mode, epi, st, keep, shape);
+    }
+    return launch_cols<T, +1, 1>(L, in, outer, inner, out, mode, epi, st, keep);
 }
 
 template <typename T>
 static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_scale, uint64_t seed, uint32_t r0,
                                     int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
-                                    cudaStream_t st, const RealDesc* desc = nullptr) {
+                                    cudaStream_t st, const RealDesc* desc = nullptr, int shape = 0) {
     if constexpr (sizeof(T) == 4) {
         if (mode == 0 && L >= 16 && pair_rows())
-            return launch_sample_rows_pair(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc);
+            return launch_rows_pair(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc, shape);
     }
     return dispatch_line(L, [&](auto Lc) -> cf_status {
         constexpr int LL = decltype(Lc)::value;
@@ -383,9 +305,16 @@ size_t tc_header_bytes();
 cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0, int R, float* fields, void* ws,
                     size_t ws_bytes, int chunk, double amp_scale, cudaStream_t st);
 
-// Tuned chunk per (device, grid shape, element size), set by cf_tune_sample.
+// Tuned schedule per (device, grid shape, element size), set by
+// cf_tune_sample: realizations per launch and the CTA shapes of the paired
+// binary32 row and column passes (0: not tuned / default).
+struct SamplerTuning {
+    int chunk = 0;
+    int rows_shape = 0;
+    int cols_shape = 0;
+};
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tuned_chunk;
+static std::map<std::string, SamplerTuning> g_tuned;
 
 static std::string tune_key(const GridInfo& g, size_t elem) {
     int dev = 0;
@@ -395,11 +324,13 @@ static std::string tune_key(const GridInfo& g, size_t elem) {
     return b;
 }
 
-static int tuned_chunk(const GridInfo& g, size_t elem) {
+static SamplerTuning tuned_of(const GridInfo& g, size_t elem) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned_chunk.find(tune_key(g, elem));
-    return it == g_tuned_chunk.end() ? 0 : it->second;
+    auto it = g_tuned.find(tune_key(g, elem));
+    return it == g_tuned.end() ? SamplerTuning{} : it->second;
 }
+
+static int tuned_chunk(const GridInfo& g, size_t elem) { return tuned_of(g, elem).chunk; }
 
 // Binary32 workspaces end with the list of Poisson decisions left to the
 // binary64 walk (a counter, then entries; about 4e-4 of the counts at
@@ -481,6 +412,7 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
                              cudaStream_t st, C2<float>* spec_half = nullptr) {
     const GridInfo& g = e->grid;
     const size_t elem = sizeof(C2<T>);
+    const SamplerTuning tn = tuned_of(g, elem);
     const int chunk = pick_chunk(g, elem, R, ws_bytes);
     if (chunk < 1) return fail(CF_ERR_NOMEM, "workspace of %zu bytes holds no realization (%zu needed)", ws_bytes,
                                per_realization_bytes(g, elem));
@@ -517,7 +449,8 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
         if (d == 1) {
             CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, nullptr, 1, epi, st));
         } else if (d == 2) {
-            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
+            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st, nullptr,
+                                             tn.rows_shape));
             // pass 2: columns of [chunk][M0][N1], keep N0, fields epilogue
             if constexpr (sizeof(T) == 4) {
                 if (spec_half) {
@@ -526,13 +459,16 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
                     continue;
                 }
             }
-            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0])));
+            CF_TRY(launch_sampler_cols<T>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0], tn.cols_shape));
         } else {
-            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st));
+            CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, buf1, 0, epi, st, nullptr,
+                                             tn.rows_shape));
             // pass 2: axis 1 of [chunk*M0][M1][N2] -> [chunk*M0][N1][N2]
-            CF_TRY((launch_cols<T, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1])));
+            CF_TRY(launch_sampler_cols<T>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1],
+                                          tn.cols_shape));
             // pass 3: axis 0 of [chunk][M0][N1*N2] -> fields
-            CF_TRY((launch_cols<T, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0])));
+            CF_TRY(launch_sampler_cols<T>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0],
+                                          tn.cols_shape));
         }
         CF_TRY(defer_end(defer, st));
     }
@@ -586,6 +522,7 @@ __global__ void k_noise_f64(uint32_t key0, uint32_t key1, uint32_t r0, long long
 cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, void* ws, size_t ws_bytes,
                            cudaStream_t st) {
     const size_t elem = sizeof(C2<float>);
+    const SamplerTuning tn = tuned_of(g, elem);
     const int chunk = pick_chunk(g, elem, nreal, ws_bytes);
     if (chunk < 1) return fail(CF_ERR_NOMEM, "batch workspace too small");
     const long long cells = g.ncell;
@@ -605,12 +542,16 @@ cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, v
         if (d == 1) {
             CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, nullptr, 1, epi, st, desc + c0));
         } else if (d == 2) {
-            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
-            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0])));
+            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0,
+                                             tn.rows_shape));
+            CF_TRY(launch_sampler_cols<float>(g.m[0], buf1, nr, g.n[1], nullptr, 1, epi, st, g.n[0], tn.cols_shape));
         } else {
-            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0));
-            CF_TRY((launch_cols<float, +1, 1>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1])));
-            CF_TRY((launch_cols<float, +1, 1>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0])));
+            CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, buf1, 0, epi, st, desc + c0,
+                                             tn.rows_shape));
+            CF_TRY(launch_sampler_cols<float>(g.m[1], buf1, (long long)nr * g.m[0], g.n[2], buf2, 0, epi, st, g.n[1],
+                                              tn.cols_shape));
+            CF_TRY(launch_sampler_cols<float>(g.m[0], buf2, nr, g.n[1] * g.n[2], nullptr, 1, epi, st, g.n[0],
+                                              tn.cols_shape));
         }
         CF_TRY(defer_end(defer, st));
     }
@@ -688,6 +629,29 @@ extern "C" cf_status cf_sample_lp(const cf_embedding* e, uint64_t seed, uint64_t
     return sample_impl<float>(e, seed, r0, R, fields_out, lp, ws, ws_bytes, 1.0, (cudaStream_t)s);
 }
 
+// Time of sample_impl on R realizations under tuning t (one warm-up run,
+// then the mean of two), or a negative status.
+static cf_status time_schedule(const cf_embedding* e, cf_dtype dt, int32_t R, void* ws, size_t ws_bytes,
+                               void* fields, const std::string& key, SamplerTuning t, cudaStream_t st,
+                               cudaEvent_t a, cudaEvent_t b, float* ms) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = t;
+    }
+    cf_status r = CF_OK;
+    for (int rep = 0; rep < 3 && r == CF_OK; ++rep) {
+        if (rep == 1) CF_CUDA(cudaEventRecord(a, st));
+        r = dt == CF_F32 ? sample_impl<float>(e, 1, 0, R, fields, nullptr, ws, ws_bytes, 1.0, st)
+                         : sample_impl<double>(e, 1, 0, R, fields, nullptr, ws, ws_bytes, 1.0, st);
+    }
+    if (r != CF_OK) return r;
+    CF_CUDA(cudaEventRecord(b, st));
+    CF_CUDA(cudaEventSynchronize(b));
+    CF_CUDA(cudaEventElapsedTime(ms, a, b));
+    *ms *= 0.5f;
+    return CF_OK;
+}
+
 extern "C" cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, void* ws, size_t ws_bytes,
                                     void* fields_scratch, cf_stream_t s, int32_t* chunk_out, double* ms_out) {
     clear_error();
@@ -700,51 +664,102 @@ extern "C" cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t 
     const std::string key = tune_key(e->grid, elem);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned_chunk.erase(key);
+        g_tuned.erase(key);
     }
     cudaEvent_t a, b;
     CF_CUDA(cudaEventCreate(&a));
     CF_CUDA(cudaEventCreate(&b));
-    int best = 1;
-    float best_ms = 1e30f;
-    for (int c = 1; c <= R; c *= 2) {
-        if (per > 0 && per * (size_t)c > ws_bytes) break;
-        {
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned_chunk[key] = c;
-        }
-        cf_status r = CF_OK;
-        for (int rep = 0; rep < 3 && r == CF_OK; ++rep) {  // warm-up, then two timed runs
-            if (rep == 1) cudaEventRecord(a, st);
-            r = dt == CF_F32 ? sample_impl<float>(e, 1, 0, R, fields_scratch, nullptr, ws, ws_bytes, 1.0, st)
-                             : sample_impl<double>(e, 1, 0, R, fields_scratch, nullptr, ws, ws_bytes, 1.0, st);
-        }
-        cudaEventRecord(b, st);
+    auto done = [&](cf_status r) {
         if (r != CF_OK) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned_chunk.erase(key);
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
-            return r;
+            g_tuned.erase(key);
         }
-        CF_CUDA(cudaEventSynchronize(b));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return r;
+    };
+    SamplerTuning best{};
+    float best_ms = 1e30f;
+    // 1. realizations per launch, default CTA shapes
+    for (int c = 1; c <= R; c *= 2) {
+        if (per > 0 && per * (size_t)c > ws_bytes) break;
+        SamplerTuning t{};
+        t.chunk = c;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        ms *= 0.5f;
+        const cf_status r = time_schedule(e, dt, R, ws, ws_bytes, fields_scratch, key, t, st, a, b, &ms);
+        if (r != CF_OK) return done(r);
         if (ms < best_ms) {
             best_ms = ms;
-            best = c;
+            best = t;
         }
         if (per == 0) break;  // one-dimensional grids have no intermediate
     }
+    // 2. CTA shapes of the paired binary32 passes at that chunk (lines of
+    // 256 points or more have three shapes each; every shape gives the same
+    // results bit for bit)
+    bool shaped = false;
+    for (int a2 = 0; a2 < e->grid.ndim; ++a2) shaped = shaped || e->grid.m[a2] >= 256;
+    if (dt == CF_F32 && e->grid.ndim >= 2 && shaped && (pair_rows() || pair_cols())) {
+        const SamplerTuning base = best;
+        const int ncs = pair_cols() ? kPairShapes : 1;
+        for (int rs = 0; rs < (pair_rows() ? kPairShapes : 1); ++rs)
+            for (int cs = 0; cs < ncs; ++cs) {
+                if (rs == 0 && cs == 0) continue;
+                SamplerTuning t = base;
+                t.rows_shape = rs;
+                t.cols_shape = cs;
+                float ms = 0.f;
+                const cf_status r = time_schedule(e, dt, R, ws, ws_bytes, fields_scratch, key, t, st, a, b, &ms);
+                if (r != CF_OK) return done(r);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned_chunk[key] = best;
+        g_tuned[key] = best;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    if (chunk_out) *chunk_out = best;
+    if (chunk_out) *chunk_out = best.chunk;
     if (ms_out) *ms_out = (double)best_ms / (double)R;
+    return done(CF_OK);
+}
+
+extern "C" cf_status cf_tune_set(const cf_embedding* e, cf_dtype dt, int32_t chunk, int32_t rows_shape,
+                                 int32_t cols_shape) {
+    clear_error();
+    if (!e) return fail(CF_ERR_ARG, "embedding is NULL");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
+    if (chunk < 0 || chunk > 65535) return fail(CF_ERR_ARG, "chunk must be 0..65535");
+    if (rows_shape < 0 || rows_shape >= kPairShapes || cols_shape < 0 || cols_shape >= kPairShapes)
+        return fail(CF_ERR_ARG, "shapes must be 0..%d", kPairShapes - 1);
+    int dev = 0;
+    CF_CUDA(cudaGetDevice(&dev));
+    if (dev != e->device) CF_CUDA(cudaSetDevice(e->device));
+    const std::string key = tune_key(e->grid, dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>));
+    if (dev != e->device) CF_CUDA(cudaSetDevice(dev));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (chunk == 0 && rows_shape == 0 && cols_shape == 0)
+        g_tuned.erase(key);
+    else
+        g_tuned[key] = SamplerTuning{chunk, rows_shape, cols_shape};
+    return CF_OK;
+}
+
+extern "C" cf_status cf_tune_info(const cf_embedding* e, cf_dtype dt, int32_t* chunk, int32_t* rows_shape,
+                                  int32_t* cols_shape) {
+    clear_error();
+    if (!e) return fail(CF_ERR_ARG, "embedding is NULL");
+    if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
+    int dev = 0;
+    CF_CUDA(cudaGetDevice(&dev));
+    if (dev != e->device) CF_CUDA(cudaSetDevice(e->device));
+    const SamplerTuning t = tuned_of(e->grid, dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>));
+    if (dev != e->device) CF_CUDA(cudaSetDevice(dev));
+    if (chunk) *chunk = t.chunk;
+    if (rows_shape) *rows_shape = t.rows_shape;
+    if (cols_shape) *cols_shape = t.cols_shape;
     return CF_OK;
 }
 

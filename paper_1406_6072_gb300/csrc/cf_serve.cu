@@ -1,7 +1,8 @@
 // cf_serve.cu -- CUDA backend of the serving loop and its C ABI.
 //
 // Each slot is one stream with its own descriptor staging buffers and
-// completion event.  A batch is one chunked, descriptor-driven sampler launch
+// completion event; embeddings are built (by the scheduler's embedding
+// thread) on a stream of the highest priority.  A batch is one chunked, descriptor-driven sampler launch
 // (cf_sample.cu: sample_batch_f32) covering the realizations of all its
 // requests, followed by the optional host copies; results stay in
 // stream-ordered device allocations until the client releases them.
@@ -35,7 +36,12 @@ class CudaBackend : public cfserve::Backend {
   public:
     CudaBackend(int device, int nslots, int max_real) : device_(device), max_real_(max_real) {
         cudaSetDevice(device_);
-        ok_ = cudaStreamCreateWithFlags(&embed_stream_, cudaStreamNonBlocking) == cudaSuccess;
+        // spectra are built on the highest-priority stream: a request that
+        // waits for its embedding then does not also wait for the blocks of
+        // large batches already queued on the device
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        ok_ = cudaStreamCreateWithPriority(&embed_stream_, cudaStreamNonBlocking, greatest) == cudaSuccess;
         slots_.resize(nslots);
         for (auto& s : slots_) {
             ok_ = ok_ && cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess;

@@ -1,12 +1,17 @@
 // cf_serve_core.h -- scheduling core of the serving loop, free of CUDA.
 //
-// Requests wait in a FIFO queue; a worker thread admits the head while a slot
-// is free and its device memory fits the budget, batches queued requests of
-// the same grid shape with it (up to max_batch_realizations), keeps the
-// embeddings of recent spectra in an LRU cache (at amplitude 1; the request's
-// amplitude is applied at sampling) and retires finished batches.  All device
-// work goes through a Backend: the CUDA one lives in cf_serve.cu; the tests
-// drive this core with a fake one on the CPU.
+// Requests wait in a FIFO queue; a worker thread admits, while a slot is free
+// and device memory fits the budget, the first queued request whose spectrum
+// is resident, batches queued requests of the same grid shape with it (up to
+// max_batch_realizations), keeps the embeddings of recent spectra in an LRU
+// cache (at amplitude 1; the request's amplitude is applied at sampling) and
+// retires finished batches.  A spectrum that is not resident is built by a
+// second thread (the binary64 embedding with its positivity report takes
+// milliseconds and waits on the device); requests waiting for it are passed
+// over meanwhile, so a build never holds up requests whose spectra are ready,
+// nor the retiring of finished batches.  All device work goes through a
+// Backend: the CUDA one lives in cf_serve.cu; the tests drive this core with
+// a fake one on the CPU.
 #pragma once
 #include <stdint.h>
 #include <string.h>
@@ -38,6 +43,7 @@ struct Job {
     cf_status status = CF_OK;
     double t_submit = 0, t_start = 0, t_done = 0;
     int cache_hit = 0;
+    bool built_for = false;       // its spectrum was missing and built for it (a cache miss)
     cf_embed_report rep{};
     CacheEntry* emb = nullptr;
     size_t result_bytes = 0;
@@ -49,7 +55,8 @@ struct CacheEntry {
     std::string key;
     void* handle = nullptr;       // backend embedding (null when the spectrum failed)
     size_t bytes = 0;
-    int refs = 0;                 // running jobs using it
+    int refs = 0;                 // running jobs using it (+1 while it is built)
+    bool building = false;        // queued for or in the embedding thread
     uint64_t last_use = 0;
     cf_status status = CF_OK;
     cf_embed_report rep_unit{};   // report at amplitude 1
@@ -60,7 +67,8 @@ class Backend {
     virtual ~Backend() {}
     // Bytes the embedding of this request's spectrum will hold (and need while built).
     virtual size_t embed_bytes(const cf_request& r) = 0;
-    // Builds the embedding of r's spectrum at amplitude 1 (blocking).
+    // Builds the embedding of r's spectrum at amplitude 1 (blocking; called
+    // from the scheduler's embedding thread, concurrently with the others).
     virtual cf_status embed(const cf_request& r, void** handle, cf_embed_report* rep) = 0;
     virtual void free_embedding(void* handle) = 0;
     virtual size_t result_bytes(const cf_request& r) = 0;
@@ -119,6 +127,7 @@ class Scheduler {
         if (cfg_.max_batch_realizations < 1) cfg_.max_batch_realizations = 1;
         slots_.resize(cfg_.max_inflight);
         worker_ = std::thread([this] { run(); });
+        embedder_ = std::thread([this] { build_loop(); });
     }
 
     ~Scheduler() { stop(); }
@@ -232,6 +241,13 @@ class Scheduler {
             cv_work_.notify_all();
         }
         if (worker_.joinable()) worker_.join();
+        {
+            // the build in progress ends; pending ones are dropped
+            std::lock_guard<std::mutex> lk(mu_);
+            builds_stop_ = true;
+            cv_build_.notify_all();
+        }
+        if (embedder_.joinable()) embedder_.join();
         std::lock_guard<std::mutex> lk(mu_);
         for (auto& kv : jobs_) {
             Job* j = kv.second;
@@ -335,19 +351,15 @@ class Scheduler {
         return any;
     }
 
-    // Makes the spectrum of queued job j available (blocking embed with the
-    // lock released); returns the entry, or null if the budget has no room yet.
-    CacheEntry* ensure_embedding(std::unique_lock<std::mutex>& lk, Job* j, bool* rejected) {
+    // Starts building the spectrum of queued job j on the embedding thread
+    // (its bytes reserved, the entry pinned while it is built); returns the
+    // new entry, or null if the budget has no room for it yet (*rejected:
+    // never, even with nothing else in memory).
+    CacheEntry* start_build(Job* j, bool* rejected) {
         *rejected = false;
-        const std::string key = spectrum_key(j->req);
-        CacheEntry* e = find_entry(key);
-        if (e) {
-            e->last_use = ++use_clock_;
-            return e;
-        }
         const size_t need = be_->embed_bytes(j->req);
         if (!make_room(need)) {
-            if (!anything_in_flight() && need > cfg_.hbm_budget) *rejected = true;
+            if (!anything_in_flight() && builds_in_progress() == 0 && need > cfg_.hbm_budget) *rejected = true;
             return nullptr;
         }
         while ((int)cache_.size() >= cfg_.cache_entries) {
@@ -362,31 +374,71 @@ class Scheduler {
         }
         in_use_ += need;  // reserved while building
         peak_ = std::max(peak_, in_use_);
+        CacheEntry ce;
+        ce.key = spectrum_key(j->req);
+        ce.bytes = need;
+        ce.refs = 1;
+        ce.building = true;
+        ce.last_use = ++use_clock_;
+        cache_.push_back(ce);
         cf_request unit = j->req;
         unit.xi.amp = 1.0;
-        void* handle = nullptr;
-        cf_embed_report rep{};
-        lk.unlock();
-        const cf_status st = be_->embed(unit, &handle, &rep);
-        lk.lock();
+        builds_.push_back(Build{&cache_.back(), unit});
         ++cache_misses_;
-        CacheEntry ce;
-        ce.key = key;
-        ce.handle = st == CF_OK ? handle : nullptr;
-        ce.bytes = st == CF_OK ? need : 0;
-        ce.status = st;
-        ce.rep_unit = rep;
-        ce.last_use = ++use_clock_;
-        if (st != CF_OK) in_use_ -= need;
-        cache_.push_back(ce);
-        CacheEntry* out = &cache_.back();
-        out->refs = 0;
-        j->cache_hit = 0;
-        return out;
+        j->built_for = true;
+        cv_build_.notify_one();
+        return &cache_.back();
     }
 
-    // Admits the head of the queue (and batch mates) into a free slot.
-    bool admit(std::unique_lock<std::mutex>& lk) {
+    int builds_in_progress() const {
+        int n = 0;
+        for (auto& e : cache_) n += e.building ? 1 : 0;
+        return n;
+    }
+
+    // The embedding thread: builds queued spectra one at a time, with the
+    // lock released while the backend works.
+    void build_loop() {
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_build_.wait(lk, [this] { return builds_stop_ || !builds_.empty(); });
+            if (builds_stop_) break;
+            const Build b = builds_.front();
+            builds_.pop_front();
+            void* handle = nullptr;
+            cf_embed_report rep{};
+            lk.unlock();
+            const cf_status st = be_->embed(b.req, &handle, &rep);
+            lk.lock();
+            CacheEntry* e = b.entry;
+            e->handle = st == CF_OK ? handle : nullptr;
+            e->status = st;
+            e->rep_unit = rep;
+            e->building = false;
+            e->refs -= 1;
+            if (st != CF_OK) {
+                in_use_ -= e->bytes;
+                e->bytes = 0;
+            }
+            cv_work_.notify_all();
+        }
+        // builds that never ran: their entries hold no embedding
+        for (const Build& b : builds_) {
+            b.entry->building = false;
+            b.entry->refs -= 1;
+            b.entry->status = CF_ERR_BUSY;
+            in_use_ -= b.entry->bytes;
+            b.entry->bytes = 0;
+        }
+        builds_.clear();
+    }
+
+    // Admits the first queued request whose spectrum is resident (and its
+    // batch mates) into a free slot; starts the builds of missing spectra on
+    // the way (at most kMaxBuilds at a time) and completes requests whose
+    // spectrum failed.  True if the queue or a slot changed.
+    static constexpr int kMaxBuilds = 4;
+    bool admit(std::unique_lock<std::mutex>&) {
         int slot = -1;
         for (int i = 0; i < (int)slots_.size(); ++i)
             if (slots_[i].jobs.empty()) {
@@ -394,40 +446,50 @@ class Scheduler {
                 break;
             }
         if (slot < 0 || queue_.empty()) return false;
-        Job* head = queue_.front();
-        const bool was_cached = find_entry(spectrum_key(head->req)) != nullptr;
-        bool rejected = false;
-        CacheEntry* e = ensure_embedding(lk, head, &rejected);
-        if (queue_.empty() || queue_.front() != head) return true;  // changed while unlocked
-        if (!e) {
-            if (rejected) {
-                queue_.pop_front();
-                complete(head, CF_ERR_NOMEM, now_s());
+        Job* head = nullptr;
+        CacheEntry* e = nullptr;
+        for (size_t q = 0; q < queue_.size() && q < 256 && !head; ++q) {
+            Job* j = queue_[q];
+            CacheEntry* ce = find_entry(spectrum_key(j->req));
+            if (!ce) {
+                if (builds_in_progress() >= kMaxBuilds) continue;
+                bool rejected = false;
+                ce = start_build(j, &rejected);
+                if (rejected) {
+                    queue_.erase(queue_.begin() + (long)q);
+                    complete(j, CF_ERR_NOMEM, now_s());
+                    return true;
+                }
+                continue;  // being built, or waiting for memory to build it
+            }
+            if (ce->building) continue;
+            if (ce->status != CF_OK) {
+                queue_.erase(queue_.begin() + (long)q);
+                if (!j->built_for) {
+                    j->cache_hit = 1;
+                    ++cache_hits_;
+                }
+                j->rep = scale_report(ce->rep_unit, j->req.xi.amp);
+                complete(j, ce->status, now_s());
                 return true;
             }
-            return false;
+            head = j;
+            e = ce;
         }
-        if (was_cached) {
-            ++cache_hits_;
-            head->cache_hit = 1;
-        }
-        if (e->status != CF_OK) {
-            queue_.pop_front();
-            head->rep = scale_report(e->rep_unit, head->req.xi.amp);
-            complete(head, e->status, now_s());
-            return true;
-        }
+        if (!head) return false;
+        e->last_use = ++use_clock_;
         // batch: the head plus queued requests of the same shape whose
         // spectrum is already resident
         std::vector<Job*> batch{head};
         int nreal = head->req.R;
         const std::string sk = shape_key(head->req);
-        for (size_t q = 1; q < queue_.size() && q < 256; ++q) {
+        const size_t at = (size_t)(std::find(queue_.begin(), queue_.end(), head) - queue_.begin());
+        for (size_t q = at + 1; q < queue_.size() && q < 256; ++q) {
             Job* c = queue_[q];
             if (nreal + c->req.R > cfg_.max_batch_realizations) break;
             if (shape_key(c->req) != sk) continue;
             CacheEntry* ce = find_entry(spectrum_key(c->req));
-            if (!ce || ce->status != CF_OK) continue;
+            if (!ce || ce->building || ce->status != CF_OK) continue;
             batch.push_back(c);
             nreal += c->req.R;
         }
@@ -451,13 +513,13 @@ class Scheduler {
         const bool fits = in_use_ + need <= cfg_.hbm_budget || make_room(need);
         for (CacheEntry* ce : pinned) ce->refs -= 1;
         if (!fits) {
-            if (!anything_in_flight() && in_use_ + need > cfg_.hbm_budget) {
+            if (!anything_in_flight() && builds_in_progress() == 0 && in_use_ + need > cfg_.hbm_budget) {
                 // cannot run even alone after everything evictable is gone
                 bool others = false;
                 for (auto& kv : jobs_)
                     if (kv.second->state == DONE && kv.second->result_bytes) others = true;
                 if (!others) {
-                    queue_.pop_front();
+                    queue_.erase(std::find(queue_.begin(), queue_.end(), head));
                     complete(head, CF_ERR_NOMEM, now_s());
                     return true;
                 }
@@ -473,7 +535,7 @@ class Scheduler {
             CacheEntry* ce = find_entry(spectrum_key(b->req));
             ce->refs += 1;
             ce->last_use = ++use_clock_;
-            if (b != head) {
+            if (!b->built_for) {
                 b->cache_hit = 1;
                 ++cache_hits_;
             }
@@ -531,7 +593,14 @@ class Scheduler {
     Backend* be_;
     std::mutex mu_;
     std::condition_variable cv_work_, cv_done_;
-    std::thread worker_;
+    std::thread worker_, embedder_;
+    struct Build {
+        CacheEntry* entry;
+        cf_request req;  // at amplitude 1
+    };
+    std::deque<Build> builds_;
+    std::condition_variable cv_build_;
+    bool builds_stop_ = false;
     std::deque<Job*> queue_;
     std::map<uint64_t, Job*> jobs_;
     std::list<CacheEntry> cache_;

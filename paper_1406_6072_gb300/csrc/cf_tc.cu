@@ -348,7 +348,7 @@ __device__ __forceinline__ C2<float> unpack2(uint32_t u) {
 
 // ---------------------------------------------------------------- pass 1
 // Rows of the embedded grid (L = M1 = RF * LS): noise, scale, transform, keep
-// n1 = L/2.  Block: WGS * LPW consecutive rows of realization r0 + blockIdx.y,
+// n1 = L/2.  Block: WGS * LPW consecutive rows of realization r0 + blockIdx.x,
 // LPW per warpgroup (RF sub-lines each).
 template <int S, int RF, bool BF16, int WGS>
 __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
@@ -362,30 +362,53 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     constexpr int LPW = SLPW / RF;                  // lines per warpgroup
     static_assert(LPW >= 1, "line does not fit a warpgroup");
     extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ float s_alpha;
+    // the input scale in binary64 once per block (the prologue's barrier
+    // publishes it): per thread it kept the slow binary64 pipe busy
+    if (threadIdx.x == 0) s_alpha = input_scale(sumsq, factor, false);
     const int wg = threadIdx.x >> 7, wtid = threadIdx.x & 127;
     const TcShared sh = tc_prologue<BF16, WGS>(tc_smem, tw, wg);
-    const float alpha = input_scale(sumsq, factor, false);
-    const uint32_t r = r0 + blockIdx.y;
-    const long long row0 = (long long)blockIdx.x * (WGS * LPW) + wg * LPW;
+    const float alpha = s_alpha;
+    // blockIdx.x: realization, blockIdx.y: block of rows, so that the blocks
+    // running at the same time read the same rows of sqrt(lambda) (L2 hits)
+    const uint32_t r = r0 + blockIdx.x;
+    const long long row0 = (long long)blockIdx.y * (WGS * LPW) + wg * LPW;
     if constexpr (RF == 1) {
         // columns col and col + L/2 share one Philox call.  Within a warp,
         // lanes take rows j + (lane & 7) of one row group and column groups
         // (lane >> 3) + 4 b of the A operand (col = row + RPL * group): 32 banks.
-#pragma unroll 2
-        for (int t = wtid; t < LPW * (L / 2); t += 128) {
-            const int g = t / (L / 2), e = t % (L / 2);
-            const int lane = e & 31, w = e >> 5;
-            const int rr = (lane & 7) + 8 * (w % (RPL / 8));
-            const int grp = (lane >> 3) + 4 * (w / (RPL / 8));
-            const int col = rr + RPL * grp;
-            const long long row = row0 + g;
-            C2<float> lo, hi;
-            noise_pair_f32((unsigned long long)row * (L / 2) + col, r, key0, key1, lo, hi);
-            const float* srow = s + (size_t)row * L;
-            const C2<float> xl = cscale(cscale(lo, srow[col] * amp_scale), alpha);
-            const C2<float> xh = cscale(cscale(hi, srow[col + L / 2] * amp_scale), alpha);
-            *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * grp)) = pack2<BF16>(xl.x, xl.y);
-            *reinterpret_cast<uint32_t*>(sh.A + a_off(g * RPL + rr, 2 * (grp + 8))) = pack2<BF16>(xh.x, xh.y);
+        // tasks t and t + 128 of this thread draw their noise together (paired
+        // Box-Muller, the same draws as one at a time)
+        static_assert((LPW * (L / 2)) % 256 == 0, "tasks come in pairs");
+#pragma unroll 1
+        for (int t0 = wtid; t0 < LPW * (L / 2); t0 += 256) {
+            int gq[2], rrq[2], grpq[2], colq[2];
+            long long rowq[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = t0 + 128 * h;
+                const int g = t / (L / 2), e = t % (L / 2);
+                const int lane = e & 31, w = e >> 5;
+                gq[h] = g;
+                rrq[h] = (lane & 7) + 8 * (w % (RPL / 8));
+                grpq[h] = (lane >> 3) + 4 * (w / (RPL / 8));
+                colq[h] = rrq[h] + RPL * grpq[h];
+                rowq[h] = row0 + g;
+            }
+            CP lo, hi;
+            noise_pair_f32x2((unsigned long long)rowq[0] * (L / 2) + colq[0], r, key0, key1,
+                             (unsigned long long)rowq[1] * (L / 2) + colq[1], r, key0, key1, lo, hi);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float* srow = s + (size_t)rowq[h] * L;
+                const C2<float> l = h ? mk(lo.re.y, lo.im.y) : mk(lo.re.x, lo.im.x);
+                const C2<float> u = h ? mk(hi.re.y, hi.im.y) : mk(hi.re.x, hi.im.x);
+                const C2<float> xl = cscale(cscale(l, srow[colq[h]] * amp_scale), alpha);
+                const C2<float> xh = cscale(cscale(u, srow[colq[h] + L / 2] * amp_scale), alpha);
+                *reinterpret_cast<uint32_t*>(sh.A + a_off(gq[h] * RPL + rrq[h], 2 * grpq[h])) = pack2<BF16>(xl.x, xl.y);
+                *reinterpret_cast<uint32_t*>(sh.A + a_off(gq[h] * RPL + rrq[h], 2 * (grpq[h] + 8))) =
+                    pack2<BF16>(xh.x, xh.y);
+            }
         }
     } else {
         // task (line g, point n' of the sub-lines): the RF inputs n' + LS j;
@@ -416,7 +439,7 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     tc::fence_proxy_async_smem();
     tc::bar_sync(1 + wg, 128);
     uint32_t phase = 0;
-    uint32_t* out = inter + ((size_t)blockIdx.y * nrows + row0) * (L / 2);
+    uint32_t* out = inter + ((size_t)blockIdx.x * nrows + row0) * (L / 2);
     run_stages<S, BF16, WGS>(sh.A, sh.a_addr, sh.bhi, sh.blo, sh.tmem, sh.bar, phase, tw, wg,
                              [&](int sl, int p, float re, float im) {
                                  const int g = sl / RF, q = sl % RF + RF * p;
@@ -442,9 +465,11 @@ __global__ void __launch_bounds__(Geo<WGS>::kThreads, 1)
     constexpr int LC = WGS * LPW;
     static_assert(LPW >= 1, "line does not fit a warpgroup");
     extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ float s_inv_alpha;
+    if (threadIdx.x == 0) s_inv_alpha = input_scale(sumsq, factor, true);
     const int wg = threadIdx.x >> 7;
     const TcShared sh = tc_prologue<BF16, WGS>(tc_smem, tw, wg);
-    const float inv_alpha = input_scale(sumsq, factor, true);
+    const float inv_alpha = s_inv_alpha;
     const long long cta0 = (long long)blockIdx.x * LC;
     const uint32_t* in = inter + (size_t)blockIdx.y * L * n1;
     if constexpr (RF == 1 && LC == 8) {
@@ -612,7 +637,7 @@ cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0
         float* f = fields + (size_t)c0 * 2 * (size_t)cells;
         if (d == 2) {
             // rows (noise, axis 1) -> [M0][n1]; columns (axis 0) -> fields
-            const dim3 g1((unsigned)(g.m[0] / tc_lines_per_block(g.m[1])), (unsigned)nr);
+            const dim3 g1((unsigned)nr, (unsigned)(g.m[0] / tc_lines_per_block(g.m[1])));
             const dim3 g2((unsigned)(g.n[1] / tc_lines_per_block(g.m[0])), (unsigned)nr);
             CF_TRY(launch(g.m[1], true, g1, rr, g.m[0], inter, g.n[1], nullptr, nullptr));
             CF_TRY(launch(g.m[0], false, g2, 0, 0, inter, g.n[1], f, nullptr));
@@ -621,7 +646,7 @@ cf_status sample_tc(const cf_embedding* e, bool bf16, uint64_t seed, uint64_t r0
             // axis 0 -> fields
             uint32_t* inter2 = inter + (size_t)nr * g.m[0] * g.m[1] * g.n[2];
             const long long rows = g.m[0] * g.m[1];
-            const dim3 g1((unsigned)(rows / tc_lines_per_block(g.m[2])), (unsigned)nr);
+            const dim3 g1((unsigned)nr, (unsigned)(rows / tc_lines_per_block(g.m[2])));
             const dim3 g2((unsigned)(g.n[2] / tc_lines_per_block(g.m[1])), (unsigned)(nr * g.m[0]));
             const dim3 g3((unsigned)(g.n[1] * g.n[2] / tc_lines_per_block(g.m[0])), (unsigned)nr);
             CF_TRY(launch(g.m[2], true, g1, rr, rows, inter, g.n[2], nullptr, nullptr));

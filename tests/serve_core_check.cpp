@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <set>
+#include <thread>
 
 #include "../paper_1406_6072_gb300/csrc/cf_serve_core.h"
 
@@ -26,6 +27,8 @@ struct FakeBackend : Backend {
     size_t embed_bytes(const cf_request& r) override { return (size_t)cells(r) * (1 << r.grid.ndim) * 36; }
     cf_status embed(const cf_request& r, void** h, cf_embed_report* rep) override {
         embeds++;
+        if (r.xi.scale > 40.0 && r.xi.scale < 60.0)  // stands for a slow build (a large 3D spectrum)
+            std::this_thread::sleep_for(std::chrono::milliseconds(300));
         memset(rep, 0, sizeof *rep);
         rep->lambda_max = 1.0;
         if (r.xi.scale > 100.0) {  // stands for a non-PSD spectrum
@@ -219,10 +222,22 @@ int main() {
                (unsigned long long)st.cache_evictions, (unsigned long long)st.cache_misses,
                (unsigned long long)st.cache_hits);
     }
-    // 9. FIFO: requests of one shape start in submission order
+    // 9. FIFO: requests of one shape whose spectra are resident start in
+    // submission order (the three spectra are built first)
     {
         FakeBackend be(2);
         Scheduler s(make_cfg(1ull << 30, 2, 1000, 8, 3), &be);
+        for (int i = 0; i < 3; ++i) {
+            uint64_t k;
+            s.submit(make_req(16, 2, 1, 2.0 + i), &k);
+            cf_result r;
+            s.wait(k, 5000000, &r);
+            s.release(k);
+        }
+        {
+            std::lock_guard<std::mutex> lk(be.m);
+            be.start_order.clear();
+        }
         std::vector<uint64_t> t;
         for (int i = 0; i < 30; ++i) {
             uint64_t k;
@@ -242,6 +257,39 @@ int main() {
             max_delay = std::max(max_delay, (long)i - submitted_pos);
         }
         printf("{\"scenario\": \"fifo\", \"started\": %zu, \"max_delay\": %ld}\n", be.start_order.size(), max_delay);
+    }
+    // 10. a slow build does not hold up requests whose spectrum is resident:
+    // they are admitted and complete while it runs; then it completes too
+    {
+        FakeBackend be(2);
+        Scheduler s(make_cfg(1ull << 30, 2, 1000, 8, 8), &be);
+        uint64_t warm;
+        s.submit(make_req(16, 2, 1, 2.0), &warm);
+        cf_result r;
+        s.wait(warm, 5000000, &r);
+        s.release(warm);
+        uint64_t slow;
+        s.submit(make_req(32, 3, 2, 50.0), &slow);  // its spectrum takes 300 ms to build
+        std::vector<uint64_t> fast;
+        for (int i = 0; i < 10; ++i) {
+            uint64_t k;
+            s.submit(make_req(16, 2, 1 + i % 3, 2.0), &k);
+            fast.push_back(k);
+        }
+        int fast_ok = 0;
+        double fast_max = 0;
+        for (auto k : fast) {
+            cf_result rr;
+            if (s.wait(k, 5000000, &rr) == CF_OK && rr.status == CF_OK) ++fast_ok;
+            fast_max = std::max(fast_max, rr.latency_ms);
+            s.release(k);
+        }
+        cf_result rs;
+        const cf_status ws = s.wait(slow, 5000000, &rs);
+        printf("{\"scenario\": \"overtake\", \"fast_ok\": %d, \"fast_max_ms\": %.3f, \"slow\": %d, "
+               "\"slow_status\": %d, \"slow_ms\": %.3f, \"slow_hit\": %d}\n",
+               fast_ok, fast_max, (int)ws, (int)rs.status, rs.latency_ms, rs.cache_hit);
+        s.release(slow);
     }
     {  // a request larger than one batch is refused at submission
         FakeBackend be(1);

@@ -125,10 +125,11 @@ def test_padded_grid_refusals():
         with pytest.raises(cf.CfError) as ei:
             cf.cf_embed_periodic(cf.make_grid(n, factor=p), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 2.0), 2, 4, 2)
         assert ei.value.status == cf.CF_ERR_UNSUPPORTED
-    # the power spectrum still needs power-of-two sides
+    # the power spectrum takes any side up to 2048 (Bluestein) or 4096 (powers of two)
     bins = cf.make_bins(4)
+    assert cf.cf_power_spectrum_workspace_size(cf.make_grid((100, 100)), 2, bins, cf.CF_F32) > 0
     with pytest.raises(cf.CfError) as ei:
-        cf.cf_power_spectrum_workspace_size(cf.make_grid((100, 100)), 2, bins, cf.CF_F32)
+        cf.cf_power_spectrum_workspace_size(cf.make_grid((3000, 100)), 2, bins, cf.CF_F32)
     assert ei.value.status == cf.CF_ERR_UNSUPPORTED
 
 

@@ -1,6 +1,8 @@
-"""GPU tests of the sampler's chunk autotuner: it picks one of the candidate
-chunks, the chosen schedule is used afterwards (the workspace size follows
-it), and tuning changes no result (chunking never changes a field bit)."""
+"""GPU tests of the sampler's autotuner: it picks one of the candidate chunks
+and CTA shapes, the chosen schedule is used afterwards (the workspace size
+follows it), and no schedule changes a result bit (chunking and the CTA
+shape of the paired passes leave every operation of every output as it
+is)."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -46,4 +48,60 @@ def test_tune_rejects_bad_arguments():
     with pytest.raises(cf.CfError) as ei:
         cf.cf_tune_sample(emb, cf.CF_F32, 0, None, 0, None)
     assert ei.value.status == cf.CF_ERR_ARG
+    emb.close()
+
+
+def _run_lp(emb, n, R, ws_bytes):
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=DEV)
+    out = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+    counts = torch.empty((R, 2) + n, dtype=torch.int32, device=DEV)
+    cf.cf_sample_lp(emb, 91, 5, R, cf.CF_F32, out, cf.make_lp(0.8, 2.0, counts, 92), ws, ws_bytes)
+    torch.cuda.synchronize()
+    return out, counts
+
+
+@pytest.mark.parametrize("n,R", [((256, 256), 5), ((128, 64, 128), 3)])
+def test_every_cta_shape_gives_the_same_bits(n, R):
+    """The paired binary32 passes compute every output with the same
+    operations whatever the CTA shape: all 3 x 3 row/column shapes (and a
+    chunk of two realizations, with its odd tail) give identical fields and
+    counts."""
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_EXPONENTIAL, 1.0, 3.0), cf.CF_EMBED_CLAMP)
+    wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+    ref_f, ref_c = _run_lp(emb, n, R, wsb)
+    for rs in range(3):
+        for cs in range(3):
+            for chunk in (0, 2):
+                cf.cf_tune_set(emb, cf.CF_F32, chunk, rs, cs)
+                assert cf.cf_tune_info(emb, cf.CF_F32) == (chunk, rs, cs)
+                f, c = _run_lp(emb, n, R, cf.cf_sample_workspace_size(emb, R, cf.CF_F32))
+                assert torch.equal(f, ref_f), (rs, cs, chunk)
+                assert torch.equal(c, ref_c), (rs, cs, chunk)
+    cf.cf_tune_set(emb, cf.CF_F32, 0, 0, 0)
+    assert cf.cf_tune_info(emb, cf.CF_F32) == (0, 0, 0)
+    emb.close()
+
+
+def test_tuner_picks_shapes_and_changes_no_result():
+    n, R = (256, 256), 8
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 4.0))
+    before = _run(emb, n, R, cf.CF_F32, cf.cf_sample_workspace_size(emb, R, cf.CF_F32))
+    wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
+    scratch = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+    chunk, ms = cf.cf_tune_sample(emb, cf.CF_F32, R, ws, wsb, scratch)
+    c, rs, cs = cf.cf_tune_info(emb, cf.CF_F32)
+    assert c == chunk and 0 <= rs < 3 and 0 <= cs < 3 and ms > 0
+    after = _run(emb, n, R, cf.CF_F32, cf.cf_sample_workspace_size(emb, R, cf.CF_F32))
+    assert torch.equal(before, after)
+    cf.cf_tune_set(emb, cf.CF_F32)
+    emb.close()
+
+
+def test_tune_set_rejects_bad_shapes():
+    emb = cf.cf_embed(cf.make_grid((32, 32)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 2.0))
+    for args in ((0, 3, 0), (0, 0, -1), (-1, 0, 0)):
+        with pytest.raises(cf.CfError) as ei:
+            cf.cf_tune_set(emb, cf.CF_F32, *args)
+        assert ei.value.status == cf.CF_ERR_ARG
     emb.close()

@@ -83,6 +83,14 @@ def test_no_request_is_overtaken_by_more_than_a_batch(scenarios):
     assert s["max_delay"] <= 3  # max_batch_realizations
 
 
+def test_slow_build_does_not_hold_up_ready_requests(scenarios):
+    s = scenarios["overtake"]
+    assert s["fast_ok"] == 10
+    assert s["fast_max_ms"] < 150          # well under the 300 ms build
+    assert s["slow"] == 0 and s["slow_status"] == 0
+    assert s["slow_ms"] >= 300 and s["slow_hit"] == 0
+
+
 def test_request_larger_than_a_batch_is_refused(scenarios):
     s = scenarios["oversize"]
     assert s["too_big"] == 1  # CF_ERR_ARG
