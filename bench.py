@@ -53,9 +53,12 @@ def parse_args():
                    help="mock_n128 workload: realizations per method (default 2000)")
     p.add_argument("--graph", action="store_true",
                    help="time replays of a captured plan (embedding computed once, per-realization path replayed)")
-    p.add_argument("--lanes", type=int, default=1,
+    p.add_argument("--lanes", type=int, default=2,
                    help="pipelines that alternate steps (own buffers and streams), so that one step's "
                         "sampler overlaps the previous step's spectra")
+    p.add_argument("--embed-priority", default="high", choices=["high", "normal"],
+                   help="priority of the embeddings' stream (high: the next step's embedding is not held up "
+                        "behind the current step's sampler blocks)")
     p.add_argument("--embed-df", action="store_true",
                    help="eigenvalues through double-float transforms (CF_EMBED_DF) instead of binary64")
     p.add_argument("--fused", action="store_true",
@@ -925,14 +928,16 @@ def main():
     # embeddings on their own stream: step k+1's binary64 embedding overlaps
     # step k's sampler and spectra (every step still embeds, samples and
     # computes its spectra; the timed region covers all of it)
-    pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev), fused=args.fused,
+    prio = -1 if args.embed_priority == "high" else 0  # lower numbers run first
+    pipe = FieldPipeline(wl, dev, stream=stream, embed_stream=torch.cuda.Stream(dev, priority=prio), fused=args.fused,
                          embed_df=args.embed_df)
     R = pipe.R
     # lanes: step k runs on pipeline k % lanes (its own fields, counts,
     # workspaces and streams), so that step k+1's sampler overlaps step k's
     # spectra; every step still embeds, samples and computes both spectra
-    lanes = [pipe] + [FieldPipeline(wl, dev, stream=torch.cuda.Stream(dev), embed_stream=torch.cuda.Stream(dev),
-                                    fused=args.fused, embed_df=args.embed_df) for _ in range(max(1, args.lanes) - 1)]
+    lanes = [pipe] + [FieldPipeline(wl, dev, stream=torch.cuda.Stream(dev),
+                                    embed_stream=torch.cuda.Stream(dev, priority=prio), fused=args.fused,
+                                    embed_df=args.embed_df) for _ in range(max(1, args.lanes) - 1)]
 
     def run_step(k):
         ln = lanes[k % len(lanes)]
@@ -978,12 +983,31 @@ def main():
         clk = clocks.stop()
     for ln in lanes[1:]:
         ln.close()
+    # the dominant kernel's own duration: inside the timed region its launches
+    # share the GPU with the other lane's spectra and the next embedding, so
+    # their event times include the time they were held back; timed alone
+    # here (the sampler on one stream, nothing else on the device)
+    n_alone = 5
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        cf.cf_kernel_timing(1)
+        for k in range(n_alone):
+            pipe.sample(r0=replicas.realization_start(rank, world, args.warmup + args.steps + k, R))
+        torch.cuda.synchronize()
+        alone = cf.cf_kernel_timing_read()
+        cf.cf_kernel_timing(0)
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = replicas.max_over_ranks(ms, dist, dev)
     cells_all = pipe.cells_per_step * world
     value = cells_all / (ms_max * 1e-3)
     hbm_peak, peak_kind = measured_peaks()
-    roof, per_kernel = roofline(wl, R, timing, args.steps, hbm_peak, peak_kind, clk.get("sm_mhz"))
+    roof_step, per_kernel = roofline(wl, R, timing, args.steps, hbm_peak, peak_kind, clk.get("sm_mhz"))
+    roof, _ = roofline(wl, R, alone, n_alone, hbm_peak, peak_kind, clk.get("sm_mhz"))
+    if roof is not None and roof_step is not None:
+        roof["timing"] = ("average of %d launches of the kernel timed alone after the timed region (the sampler "
+                          "on one stream, nothing else on the device); in_step: its launches inside the timed "
+                          "region, overlapped with the other streams' kernels" % n_alone)
+        roof["in_step"] = {k: roof_step[k] for k in ("achieved", "frac", "avg_launch_ms", "launches")}
     launches = sum(v[0] for v in per_kernel.values())
 
     e2e = None
@@ -1010,7 +1034,7 @@ def main():
                              % (2 * pipe.cells_per_step * 4 >> 20),
                        "parallelism": "replicas x%d" % world, "tuned_schedule": tuned,
                        "fused_spectra": bool(pipe.fused), "eigenvalue_transforms": "double-float" if args.embed_df
-                       else "binary64", "lanes": len(lanes)},
+                       else "binary64", "lanes": len(lanes), "embed_priority": args.embed_priority},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report, "cufft_reference": cufft,

@@ -278,8 +278,8 @@ struct PkPairCfg {
 template <int L, int KIND>
 __global__ void __launch_bounds__(PkPairCfg<L, CF_PKR2_THREADS>::THREADS, PkPairCfg<L, CF_PKR2_THREADS>::MINB)
     k_pk_rows_pair(const void* __restrict__ fields, const float* __restrict__ f, unsigned long long* __restrict__ ntot,
-                   long long rows, long long cells, long long nfields, long long f0, C2<float>* __restrict__ out,
-                   const float4* __restrict__ tw) {
+                   long long rows, long long cells, long long nfields, long long f0, long long nchunk,
+                   C2<float>* __restrict__ out, const float4* __restrict__ tw) {
     using Cfg = PkPairCfg<L, CF_PKR2_THREADS>;
     constexpr int E = Cfg::E;
     constexpr int STEP = L / E;
@@ -292,9 +292,12 @@ __global__ void __launch_bounds__(PkPairCfg<L, CF_PKR2_THREADS>::THREADS, PkPair
     const bool valid = row < rows;
     const long long rw = valid ? row : 0;
     const long long fa = f0 + 4ll * blockIdx.y;  // fields fa .. fa + 3
+    // fields of this chunk only: its half spectra hold nchunk fields (a chunk
+    // need not be a multiple of four)
+    const long long f_end = f0 + nchunk < nfields ? f0 + nchunk : nfields;
     bool has[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) has[q] = fa + q < nfields;
+    for (int q = 0; q < 4; ++q) has[q] = fa + q < f_end;
     unsigned long long nsum[4] = {0, 0, 0, 0};
     CP v[E];
     if constexpr (KIND == PK_FLOAT) {
@@ -923,7 +926,7 @@ static cf_status launch_pk_rows_pair(const void* fields, int kind, const float* 
     CF_TRY(prepare_smem(kern, Cfg::SMEM));
     dim3 grid((unsigned)((P.rows + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((nchunk + 3) / 4));
     ScopedKernelTimer kt(s, "pk_rows_f32", L);
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(fields, f, ntot, P.rows, P.g.ncell, nfields, f0, out,
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(fields, f, ntot, P.rows, P.g.ncell, nfields, f0, nchunk, out,
                                                twiddles_f32x2());
     CF_CHECK_LAUNCH();
     return CF_OK;

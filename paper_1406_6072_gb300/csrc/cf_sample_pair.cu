@@ -87,12 +87,31 @@ __global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
             sbl = __fmul_rn(__ldg(sb_row + col), amp_b);
             sbh = __fmul_rn(__ldg(sb_row + col + L / 2), amp_b);
         }
-        CP lo, hi;
-        const unsigned long long pc = (unsigned long long)rw * (L / 2) + col;
-        noise_pair_f32x2(pc, r_a, ka0, ka1, pc, r_b, kb0, kb1, lo, hi);
-        const float2 fl = make_float2(sal, sbl), fh = make_float2(sah, sbh);
-        v[q] = CP{f2mul(lo.re, fl), f2mul(lo.im, fl)};
-        v[q + E / 2] = CP{f2mul(hi.re, fh), f2mul(hi.im, fh)};
+        // where sqrt(lambda+) is zero (a clamped or zeroed eigenvalue) the
+        // scaled draw is zero whatever the noise: a warp whose amplitudes of
+        // a half are all zero skips that half's Box-Muller, and the Philox
+        // call when both halves are zero (every other draw is unchanged:
+        // the generator is counter-based)
+        const bool need_lo = __any_sync(0xffffffffu, sal != 0.0f || sbl != 0.0f);
+        const bool need_hi = __any_sync(0xffffffffu, sah != 0.0f || sbh != 0.0f);
+        CP lo = CP{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}, hi = lo;
+        if (need_lo || need_hi) {
+            const unsigned long long pc = (unsigned long long)rw * (L / 2) + col;
+            const uint4 xa = philox4x32_10(make_uint4((uint32_t)pc, (uint32_t)(pc >> 32), r_a, 0u), ka0, ka1);
+            const uint4 xb = philox4x32_10(make_uint4((uint32_t)pc, (uint32_t)(pc >> 32), r_b, 0u), kb0, kb1);
+            if (need_lo) {
+                const CP e = box_muller_f32x2(xa.x, xa.y, xb.x, xb.y);
+                const float2 fl = make_float2(sal, sbl);
+                lo = CP{f2mul(e.re, fl), f2mul(e.im, fl)};
+            }
+            if (need_hi) {
+                const CP e = box_muller_f32x2(xa.z, xa.w, xb.z, xb.w);
+                const float2 fh = make_float2(sah, sbh);
+                hi = CP{f2mul(e.re, fh), f2mul(e.im, fh)};
+            }
+        }
+        v[q] = lo;
+        v[q + E / 2] = hi;
     }
     C2<float>* oa = out + ((size_t)ra * nrows + row) * keep;
     C2<float>* ob = out + ((size_t)rb * nrows + row) * keep;
