@@ -675,6 +675,78 @@ def run_graph(args):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------- small requests
+def run_small_requests(args):
+    """Launch-bound small requests (the serving mix's 64^2 and 32^3 surveys):
+    binary32 sampler + lognormal/Poisson per call, with one launch per pass
+    (the default), as one persistent cooperative launch (cf_tune_set), and as
+    the replay of a captured plan; per call: device time (back-to-back calls,
+    CUDA events) and latency (each call synchronised, host clock)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_6072_gb300 import cf
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    calls = max(50, args.steps)
+    out = {}
+    with torch.cuda.stream(stream):
+        for n, R in (((64, 64), 1), ((64, 64), 8), ((32, 32, 32), 1), ((32, 32, 32), 8)):
+            emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 4.0), cf.CF_EMBED_CLAMP, stream)
+            fields = torch.empty((R, 2) + n, dtype=torch.float32, device=dev)
+            counts = torch.empty((R, 2) + n, dtype=torch.int32, device=dev)
+            lp = cf.make_lp(1.0, 2.0, counts, 9)
+            row = {}
+            for mode in ("per_pass", "persistent", "graph"):
+                cf.cf_tune_set(emb, cf.CF_F32, 0, 0, 0, 1 if mode == "persistent" else 0)
+                wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+                ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+                plan = cf.Plan(emb, 1, 0, R, fields, lp=lp, stream=stream) if mode == "graph" else None
+
+                def call(k):
+                    if plan is not None:
+                        plan.launch(stream)
+                    else:
+                        cf.cf_sample_lp(emb, 1, R * k, R, cf.CF_F32, fields, lp, ws, wsb, stream)
+
+                for k in range(args.warmup + 3):
+                    call(k)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for k in range(calls):
+                    call(k)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dev_us = 1e3 * e0.elapsed_time(e1) / calls
+                lat = []
+                for k in range(calls):
+                    t0 = time.perf_counter()
+                    call(k)
+                    stream.synchronize()
+                    lat.append(1e6 * (time.perf_counter() - t0))
+                row[mode] = {"us_per_call_back_to_back": round(dev_us, 2),
+                             "latency_us_p50": round(float(np.percentile(lat, 50)), 2),
+                             "latency_us_p99": round(float(np.percentile(lat, 99)), 2)}
+                if plan is not None:
+                    plan.close()
+                del ws
+            cf.cf_tune_set(emb, cf.CF_F32)
+            emb.close()
+            out["%s R=%d" % ("x".join(map(str, n)), R)] = row
+    best = min(v["per_pass"]["us_per_call_back_to_back"] / v["persistent"]["us_per_call_back_to_back"]
+               for v in out.values())
+    line = {"metric": "small-request sampler calls: one launch per pass vs one persistent launch vs graph replay",
+            "value": best, "unit": "speed-up of the persistent launch (smallest over the shapes)", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "small_requests", "calls": calls,
+                       "text": "2D 64^2 (embedded 128^2) and 3D 32^3 (64^3) Gaussian xi, 1 or 8 realizations, "
+                               "lognormal + Poisson nbar = 2"},
+            "results": out}
+    print(json.dumps(line))
+
+
 # --------------------------------------------------------------------- serving
 def run_serving(args):
     """Mixed request stream through cf_serve_* (continuous batching), against
@@ -696,12 +768,13 @@ def run_serving(args):
 
     def serve(reqs, rate):
         sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=4, cache_entries=96, max_batch_realizations=256,
-                                                  hbm_budget=96 << 30))
+                                                  hbm_budget=96 << 30, small_request_cells=1 << 20))
         tickets = []
         lock = th.Lock()
         done_flag = [False]
 
-        parts = []  # (latency, queue, run, cache hit) per request
+        parts = []  # (latency, queue, run, cache hit, output cells) per request
+        work = {}   # ticket -> output cells (2 R prod n)
 
         def waiter():
             k = 0
@@ -720,7 +793,7 @@ def run_serving(args):
                 r = cf.cf_serve_wait(sv, t, -1)
                 clamped += r["embed"]["clamped"]
                 if r["status"] == cf.CF_OK:
-                    parts.append((r["latency_ms"], r["queue_ms"], r["run_ms"], r["cache_hit"]))
+                    parts.append((r["latency_ms"], r["queue_ms"], r["run_ms"], r["cache_hit"], work[t]))
                 cf.cf_serve_release(sv, t)
                 k += 1
             waiter.clamped = clamped
@@ -735,6 +808,7 @@ def run_serving(args):
                     time.sleep(delay)
             tk = cf.cf_serve_submit(sv, req_of(q))
             with lock:
+                work[tk] = 2 * q["R"] * int(np.prod(q["n"]))
                 tickets.append(tk)
         with lock:
             done_flag[0] = True
@@ -746,14 +820,22 @@ def run_serving(args):
         st["clamped_requests"] = waiter.clamped
         # where the time goes: queueing (waiting for a slot, memory or the
         # spectrum's build) against running, and cache hits against misses
-        a = np.asarray(parts, dtype=np.float64).reshape(-1, 4)
+        a = np.asarray(parts, dtype=np.float64).reshape(-1, 5)
         pct = lambda x, q: float(np.percentile(x, q)) if x.size else None
         hit, miss = a[a[:, 3] == 1], a[a[:, 3] == 0]
+        # requests span 4 orders of magnitude of work (64^2 x 1 to 128^3 x 32
+        # realizations): latency per class of output cells
+        classes = {}
+        for name, lo, hi in (("small <1M cells", 0, 1 << 20), ("medium 1M-16M", 1 << 20, 1 << 24),
+                             ("large >=16M", 1 << 24, 1 << 62)):
+            c = a[(a[:, 4] >= lo) & (a[:, 4] < hi)]
+            classes[name] = {"requests": int(c.shape[0]), "p50_ms": pct(c[:, 0], 50), "p99_ms": pct(c[:, 0], 99),
+                             "p99_queue_ms": pct(c[:, 1], 99)}
         st["attribution"] = {"p50_queue_ms": pct(a[:, 1], 50), "p99_queue_ms": pct(a[:, 1], 99),
                              "p50_run_ms": pct(a[:, 2], 50), "p99_run_ms": pct(a[:, 2], 99),
                              "p99_ms_cache_hit": pct(hit[:, 0], 99), "p99_ms_cache_miss": pct(miss[:, 0], 99),
                              "p50_ms_cache_miss": pct(miss[:, 0], 50),
-                             "miss_fraction": float(miss.shape[0] / max(1, a.shape[0]))}
+                             "miss_fraction": float(miss.shape[0] / max(1, a.shape[0])), "by_work": classes}
         return st
 
     n_cap = min(1000, len(base))
@@ -900,6 +982,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "small_requests":
+        return run_small_requests(args)
     if args.workload.endswith("_sweep"):
         return run_sweep(args)
     if args.workload == "cauchy2d_n512_padding":
@@ -953,8 +1037,9 @@ def main():
         with torch.cuda.stream(stream):
             pipe.embed()
             chunk, tms = pipe.tune()
-            _, rshape, cshape = cf.cf_tune_info(pipe.emb, pipe.dtype)
-            tuned = {"chunk": chunk, "rows_shape": rshape, "cols_shape": cshape, "ms_per_realization": tms}
+            _, rshape, cshape, persist = cf.cf_tune_info(pipe.emb, pipe.dtype)
+            tuned = {"chunk": chunk, "rows_shape": rshape, "cols_shape": cshape, "persistent": persist,
+                     "ms_per_realization": tms}
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
             run_step(k)
@@ -1039,6 +1124,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk, "embed_report": pipe.emb.report, "cufft_reference": cufft,
             "kernels": {k: {"launches": v[0], "ms_per_step": v[1] / args.steps} for k, v in sorted(per_kernel.items())},
+            "sampler_alone_ms_per_step": {k.split("<")[0]: v[1] / n_alone for k, v in sorted(alone.items())},
         }
         print(json.dumps(line))
     pipe.close()

@@ -262,8 +262,9 @@ CF_API cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uint64_
  * pass (and of the paired column pass, where it is enabled) at the best
  * chunk, writing into fields_scratch
  * ([R][2][n...] of dt), and records the fastest for this device, grid shape
- * and dtype; later cf_sample / cf_sample_lp / cf_sample_workspace_size calls
- * and served batches with that shape use it (cf_tune_info reads it).
+ * and dtype (on small binary32 grids also the persistent single launch);
+ * later cf_sample / cf_sample_lp / cf_sample_workspace_size calls and served
+ * batches with that shape use it (cf_tune_info reads it).
  * Synchronises s.  *chunk_out (may be NULL) receives the chosen chunk,
  * *ms_out (may be NULL) its time per realization. */
 CF_API cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, void* ws, size_t ws_bytes,
@@ -271,14 +272,17 @@ CF_API cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, v
 
 /* The sampler schedule recorded for e's grid and dt on the current device:
  * realizations per launch (0: the default, chunks of up to 1 GiB of
- * intermediate) and the CTA shapes (0, 1, 2; 0 the default) of the binary32
- * passes with two realizations per thread.  cf_tune_sample records the
- * fastest; cf_tune_set records a given one (chunk 0 and shapes 0 clear the
- * record).  Shapes and chunks change no result bit. */
+ * intermediate), the CTA shapes (0, 1, 2; 0 the default) of the binary32
+ * passes with two realizations per thread, and whether each chunk runs as one
+ * persistent cooperative launch (1; binary32 grids whose embedded sides are
+ * all 64 or 128, else CF_ERR_UNSUPPORTED) instead of one launch per pass (0).
+ * cf_tune_sample records the fastest; cf_tune_set records a given one (all
+ * zero clears the record).  No schedule changes a result bit.  Output
+ * pointers may be NULL. */
 CF_API cf_status cf_tune_info(const cf_embedding* e, cf_dtype dt, int32_t* chunk, int32_t* rows_shape,
-                              int32_t* cols_shape);
+                              int32_t* cols_shape, int32_t* persistent);
 CF_API cf_status cf_tune_set(const cf_embedding* e, cf_dtype dt, int32_t chunk, int32_t rows_shape,
-                             int32_t cols_shape);
+                             int32_t cols_shape, int32_t persistent);
 
 /* Tensor-core modes: number of tensor-core waits that ran out of time (1 s
  * each) on the current device since the last call; synchronises s and
@@ -484,7 +488,10 @@ typedef struct {
     int32_t queue_capacity;          /* queued requests before submit returns CF_ERR_BUSY  */
     int32_t cache_entries;           /* embeddings kept on the device                      */
     int32_t max_batch_realizations;  /* realizations per batched launch (and per request)  */
-    int32_t pad_;
+    int32_t small_request_cells;     /* > 0: one more slot, on a stream of the highest
+                                        priority, reserved for requests of at most this many
+                                        output cells (2 R prod n), so that they need not wait
+                                        behind large batches; 0: none                       */
     size_t hbm_budget;               /* bytes: cached embeddings + in-flight + unreleased results */
 } cf_serve_cfg;
 

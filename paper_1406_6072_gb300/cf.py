@@ -72,8 +72,8 @@ class cf_bins(C.Structure):
 
 class cf_serve_cfg(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_inflight", C.c_int32), ("queue_capacity", C.c_int32),
-                ("cache_entries", C.c_int32), ("max_batch_realizations", C.c_int32), ("pad_", C.c_int32),
-                ("hbm_budget", C.c_size_t)]
+                ("cache_entries", C.c_int32), ("max_batch_realizations", C.c_int32),
+                ("small_request_cells", C.c_int32), ("hbm_budget", C.c_size_t)]
 
 
 class cf_request(C.Structure):
@@ -137,8 +137,9 @@ _sigs = {
     "cf_plan_destroy": [_P],
     "cf_tune_sample": [_P, C.c_int32, C.c_int32, _P, C.c_size_t, _P, _S, C.POINTER(C.c_int32),
                        C.POINTER(C.c_double)],
-    "cf_tune_info": [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
-    "cf_tune_set": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
+    "cf_tune_info": [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                     C.POINTER(C.c_int32)],
+    "cf_tune_set": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
     "cf_lognormal_poisson": [_P, C.c_int32, C.c_int64, C.c_int64, C.c_double, C.c_double, _P, C.c_uint64,
                              C.c_uint64, _P, _P, _S],
     "cf_power_spectrum_workspace_size": [C.POINTER(cf_grid), C.c_int64, C.POINTER(cf_bins), C.c_int32,
@@ -350,14 +351,14 @@ def cf_tune_sample(emb, dtype, R, ws, ws_bytes, fields_scratch, stream=None):
 
 
 def cf_tune_info(emb, dtype):
-    """The recorded sampler schedule: (chunk, rows_shape, cols_shape)."""
-    c, r, k = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(_lib.cf_tune_info(emb.handle, dtype, C.byref(c), C.byref(r), C.byref(k)), "cf_tune_info")
-    return c.value, r.value, k.value
+    """The recorded sampler schedule: (chunk, rows_shape, cols_shape, persistent)."""
+    c, r, k, p = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib.cf_tune_info(emb.handle, dtype, C.byref(c), C.byref(r), C.byref(k), C.byref(p)), "cf_tune_info")
+    return c.value, r.value, k.value, p.value
 
 
-def cf_tune_set(emb, dtype, chunk=0, rows_shape=0, cols_shape=0):
-    _check(_lib.cf_tune_set(emb.handle, dtype, chunk, rows_shape, cols_shape), "cf_tune_set")
+def cf_tune_set(emb, dtype, chunk=0, rows_shape=0, cols_shape=0, persistent=0):
+    _check(_lib.cf_tune_set(emb.handle, dtype, chunk, rows_shape, cols_shape, persistent), "cf_tune_set")
 
 
 def cf_cic_histogram(counts, cells, nfields, f, nbins, hist_out, mean=None, cov=None, stream=None):
@@ -481,8 +482,9 @@ def cf_power_spectrum_counts(counts, f, grid, nfields, bins, pk_out, nmodes_out,
 
 # ----------------------------------------------------------------- serving
 def make_serve_cfg(device=0, max_inflight=4, queue_capacity=100000, cache_entries=64, max_batch_realizations=256,
-                   hbm_budget=32 << 30):
+                   hbm_budget=32 << 30, small_request_cells=0):
     c = cf_serve_cfg()
+    c.small_request_cells = int(small_request_cells)
     c.device, c.max_inflight, c.queue_capacity = device, max_inflight, queue_capacity
     c.cache_entries, c.max_batch_realizations, c.hbm_budget = cache_entries, max_batch_realizations, hbm_budget
     return c

@@ -177,11 +177,12 @@ struct ColsCfg : TileCfg<T, L, ColsShape<T, L, WIDE>::E, ColsShape<T, L, WIDE>::
         TileCfg<T, L, ColsShape<T, L, WIDE>::E, ColsShape<T, L, WIDE>::THREADS, ColsShape<T, L, WIDE>::MINB>::LINES;
 };
 
+// The body of one block of k_cols: column tile bx of outer slice o (a
+// persistent kernel calls it for several tiles in turn).
 template <typename T, int L, int SIGN, int KEEP_HALF>
-__global__ void __launch_bounds__(ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>::THREADS,
-                                  ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>::MINB)
-    k_cols(const C2<T>* in, long long inner, int keep, C2<T>* out, int mode, FieldEpi<T> epi,
-           const C2<T>* __restrict__ tw) {
+__device__ __forceinline__ void cols_block(long long bx, long long o, const C2<T>* in, long long inner, int keep,
+                                           C2<T>* out, int mode, const FieldEpi<T>& epi,
+                                           const C2<T>* __restrict__ tw) {
     using Cfg = ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>;
     using G = typename Cfg::G;
     constexpr int KEEP = KEEP_HALF ? L / 2 : L;
@@ -189,8 +190,7 @@ __global__ void __launch_bounds__(ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>::THREAD
     C2<T>* sm = reinterpret_cast<C2<T>*>(smraw);
     const int ln = threadIdx.x % Cfg::C;
     const int j = threadIdx.x / Cfg::C;
-    const long long i = (long long)blockIdx.x * Cfg::C + ln;
-    const long long o = blockIdx.y;
+    const long long i = bx * Cfg::C + ln;
     const bool valid = i < inner;
     const C2<T>* src = in + (size_t)o * L * (size_t)inner + (size_t)(valid ? i : 0);
     C2<T> v[G::E];
@@ -204,6 +204,14 @@ __global__ void __launch_bounds__(ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>::THREAD
             epi((int)o, (long long)p * inner + i, val);
     };
     line_fft<T, L, SIGN, KEEP>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+}
+
+template <typename T, int L, int SIGN, int KEEP_HALF>
+__global__ void __launch_bounds__(ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>::THREADS,
+                                  ColsCfg<T, L, (SIGN > 0 && KEEP_HALF)>::MINB)
+    k_cols(const C2<T>* in, long long inner, int keep, C2<T>* out, int mode, FieldEpi<T> epi,
+           const C2<T>* __restrict__ tw) {
+    cols_block<T, L, SIGN, KEEP_HALF>(blockIdx.x, blockIdx.y, in, inner, keep, out, mode, epi, tw);
 }
 
 // --------------------------------------------------------------------------

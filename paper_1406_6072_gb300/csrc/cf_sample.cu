@@ -128,6 +128,12 @@ cf_status launch_rows_pair(long long L, int keep, const float* s, float amp_scal
                            int shape);
 cf_status launch_cols_pair(long long L, const C2<float>* in, long long outer, long long inner, C2<float>* out,
                            int mode, const FieldEpi<float>& epi, cudaStream_t st, long long keep, int shape);
+// The whole binary32 sampler of a chunk in one cooperative launch (small
+// grids, persistent_ok).
+bool persistent_ok(const GridInfo& g);
+cf_status launch_sample_persistent(const GridInfo& g, const float* s, float amp_scale, uint64_t seed, uint32_t r0,
+                                   int nr, C2<float>* buf1, C2<float>* buf2, const FieldEpi<float>& epi,
+                                   const PoissonDefer& defer, const RealDesc* desc, cudaStream_t st);
 
 // Binary32 row pass with two realizations per thread (CF_SROWS_PAIR=0 in the
 // environment turns it off).
@@ -312,6 +318,7 @@ struct SamplerTuning {
     int chunk = 0;
     int rows_shape = 0;
     int cols_shape = 0;
+    int persistent = 0;  // one cooperative launch per chunk (small binary32 grids)
 };
 static std::mutex g_tune_mu;
 static std::map<std::string, SamplerTuning> g_tuned;
@@ -445,6 +452,13 @@ static cf_status sample_impl(const cf_embedding* e, uint64_t seed, uint64_t r0, 
         const uint32_t rr0 = (uint32_t)(r0 + (uint64_t)c0);
         const long long Ml = g.m[d - 1];
         const long long nrows = g.mtotal / Ml;
+        if constexpr (sizeof(T) == 4) {
+            if (tn.persistent && !spec_half && persistent_ok(g)) {
+                CF_TRY(launch_sample_persistent(g, s, (float)amp_scale, seed, rr0, nr, buf1, buf2, epi, defer, nullptr,
+                                                st));
+                continue;
+            }
+        }
         CF_TRY(defer_begin(defer, st));
         if (d == 1) {
             CF_TRY(launch_sample_rows<T>(Ml, (int)g.n[d - 1], s, (T)amp_scale, seed, rr0, nr, nrows, nullptr, 1, epi, st));
@@ -538,6 +552,10 @@ cf_status sample_batch_f32(const GridInfo& g, const RealDesc* desc, int nreal, v
         epi.cells = cells;
         epi.desc = desc + c0;
         epi.defer = defer;
+        if (tn.persistent && persistent_ok(g)) {
+            CF_TRY(launch_sample_persistent(g, nullptr, 1.0f, 0, 0, nr, buf1, buf2, epi, defer, desc + c0, st));
+            continue;
+        }
         CF_TRY(defer_begin(defer, st));
         if (d == 1) {
             CF_TRY(launch_sample_rows<float>(Ml, (int)g.n[d - 1], nullptr, 1.0f, 0, 0, nr, nrows, nullptr, 1, epi, st, desc + c0));
@@ -717,6 +735,18 @@ extern "C" cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t 
                 }
             }
     }
+    // 3. the whole chunk in one persistent cooperative launch (small binary32 grids)
+    if (dt == CF_F32 && persistent_ok(e->grid)) {
+        SamplerTuning t = best;
+        t.persistent = 1;
+        float ms = 0.f;
+        const cf_status r = time_schedule(e, dt, R, ws, ws_bytes, fields_scratch, key, t, st, a, b, &ms);
+        if (r != CF_OK) return done(r);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = best;
@@ -727,28 +757,31 @@ extern "C" cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t 
 }
 
 extern "C" cf_status cf_tune_set(const cf_embedding* e, cf_dtype dt, int32_t chunk, int32_t rows_shape,
-                                 int32_t cols_shape) {
+                                 int32_t cols_shape, int32_t persistent) {
     clear_error();
     if (!e) return fail(CF_ERR_ARG, "embedding is NULL");
     if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
     if (chunk < 0 || chunk > 65535) return fail(CF_ERR_ARG, "chunk must be 0..65535");
     if (rows_shape < 0 || rows_shape >= kPairShapes || cols_shape < 0 || cols_shape >= kPairShapes)
         return fail(CF_ERR_ARG, "shapes must be 0..%d", kPairShapes - 1);
+    if (persistent != 0 && persistent != 1) return fail(CF_ERR_ARG, "persistent must be 0 or 1");
+    if (persistent && (dt != CF_F32 || !persistent_ok(e->grid)))
+        return fail(CF_ERR_UNSUPPORTED, "the persistent sampler takes binary32 grids with embedded sides 64 or 128");
     int dev = 0;
     CF_CUDA(cudaGetDevice(&dev));
     if (dev != e->device) CF_CUDA(cudaSetDevice(e->device));
     const std::string key = tune_key(e->grid, dt == CF_F32 ? sizeof(C2<float>) : sizeof(C2<double>));
     if (dev != e->device) CF_CUDA(cudaSetDevice(dev));
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (chunk == 0 && rows_shape == 0 && cols_shape == 0)
+    if (chunk == 0 && rows_shape == 0 && cols_shape == 0 && persistent == 0)
         g_tuned.erase(key);
     else
-        g_tuned[key] = SamplerTuning{chunk, rows_shape, cols_shape};
+        g_tuned[key] = SamplerTuning{chunk, rows_shape, cols_shape, persistent};
     return CF_OK;
 }
 
 extern "C" cf_status cf_tune_info(const cf_embedding* e, cf_dtype dt, int32_t* chunk, int32_t* rows_shape,
-                                  int32_t* cols_shape) {
+                                  int32_t* cols_shape, int32_t* persistent) {
     clear_error();
     if (!e) return fail(CF_ERR_ARG, "embedding is NULL");
     if (dt != CF_F32 && dt != CF_F64) return fail(CF_ERR_UNSUPPORTED, "dtype %d", dt);
@@ -760,6 +793,7 @@ extern "C" cf_status cf_tune_info(const cf_embedding* e, cf_dtype dt, int32_t* c
     if (chunk) *chunk = t.chunk;
     if (rows_shape) *rows_shape = t.rows_shape;
     if (cols_shape) *cols_shape = t.cols_shape;
+    if (persistent) *persistent = t.persistent;
     return CF_OK;
 }
 

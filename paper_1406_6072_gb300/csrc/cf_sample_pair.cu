@@ -15,6 +15,8 @@
 // fit).  Every shape computes every output with the same operations, so the
 // choice changes no result bit; the sampler's autotuner (cf_tune_sample)
 // picks the fastest per grid.
+#include <cooperative_groups.h>
+
 #include "cf_kernels.cuh"
 
 namespace cf {
@@ -35,16 +37,16 @@ struct PairCfg {
     static constexpr size_t SMEM = sizeof(CP) * (size_t)LINES * (size_t)PADDED;
 };
 
-// Row pass: rows of realizations ra = 2 blockIdx.y and rb = ra + 1 of the
-// chunk (rb absent in an odd tail); lane A draws realization ra's noise, lane
+// Row pass (block (bx, by)): rows of realizations ra = 2 by and rb = ra + 1
+// of the chunk (rb absent in an odd tail); lane A draws realization ra's noise, lane
 // B rb's (each with its own amplitudes and key in a batched launch), scales
 // it by sqrt(lambda+/M^d), transforms the row and keeps the first `keep`
 // outputs: intermediate [chunk][nrows][keep].
 template <int L, bool DESC, int LW>
-__global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
-    k_sample_rows_pair(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
-                       long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
-                       const float4* __restrict__ tw, const RealDesc* __restrict__ desc) {
+__device__ __forceinline__ void rows_pair_block(long long bx, long long by, const float* __restrict__ s,
+                                                float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
+                                                long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
+                                                const float4* __restrict__ tw, const RealDesc* __restrict__ desc) {
     using Cfg = PairCfg<L, LW>;
     constexpr int E = Cfg::E;
     constexpr int STEP = L / E;
@@ -52,8 +54,8 @@ __global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
     CP* sm = reinterpret_cast<CP*>(smraw);
     const int line = threadIdx.x / Cfg::TL;
     const int j = threadIdx.x % Cfg::TL;
-    const long long row = (long long)blockIdx.x * Cfg::LINES + line;
-    const int ra = 2 * blockIdx.y, rb = ra + 1;
+    const long long row = bx * Cfg::LINES + line;
+    const int ra = 2 * (int)by, rb = ra + 1;
     const bool valid = row < nrows, valid_b = rb < chunk;
     const long long rw = valid ? row : 0;
     const float* sa_row = s + (size_t)rw * L;
@@ -87,31 +89,12 @@ __global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
             sbl = __fmul_rn(__ldg(sb_row + col), amp_b);
             sbh = __fmul_rn(__ldg(sb_row + col + L / 2), amp_b);
         }
-        // where sqrt(lambda+) is zero (a clamped or zeroed eigenvalue) the
-        // scaled draw is zero whatever the noise: a warp whose amplitudes of
-        // a half are all zero skips that half's Box-Muller, and the Philox
-        // call when both halves are zero (every other draw is unchanged:
-        // the generator is counter-based)
-        const bool need_lo = __any_sync(0xffffffffu, sal != 0.0f || sbl != 0.0f);
-        const bool need_hi = __any_sync(0xffffffffu, sah != 0.0f || sbh != 0.0f);
-        CP lo = CP{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}, hi = lo;
-        if (need_lo || need_hi) {
-            const unsigned long long pc = (unsigned long long)rw * (L / 2) + col;
-            const uint4 xa = philox4x32_10(make_uint4((uint32_t)pc, (uint32_t)(pc >> 32), r_a, 0u), ka0, ka1);
-            const uint4 xb = philox4x32_10(make_uint4((uint32_t)pc, (uint32_t)(pc >> 32), r_b, 0u), kb0, kb1);
-            if (need_lo) {
-                const CP e = box_muller_f32x2(xa.x, xa.y, xb.x, xb.y);
-                const float2 fl = make_float2(sal, sbl);
-                lo = CP{f2mul(e.re, fl), f2mul(e.im, fl)};
-            }
-            if (need_hi) {
-                const CP e = box_muller_f32x2(xa.z, xa.w, xb.z, xb.w);
-                const float2 fh = make_float2(sah, sbh);
-                hi = CP{f2mul(e.re, fh), f2mul(e.im, fh)};
-            }
-        }
-        v[q] = lo;
-        v[q + E / 2] = hi;
+        CP lo, hi;
+        const unsigned long long pc = (unsigned long long)rw * (L / 2) + col;
+        noise_pair_f32x2(pc, r_a, ka0, ka1, pc, r_b, kb0, kb1, lo, hi);
+        const float2 fl = make_float2(sal, sbl), fh = make_float2(sah, sbh);
+        v[q] = CP{f2mul(lo.re, fl), f2mul(lo.im, fl)};
+        v[q + E / 2] = CP{f2mul(hi.re, fh), f2mul(hi.im, fh)};
     }
     C2<float>* oa = out + ((size_t)ra * nrows + row) * keep;
     C2<float>* ob = out + ((size_t)rb * nrows + row) * keep;
@@ -121,6 +104,15 @@ __global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
         if (valid_b) ob[p] = mk(val.re.y, val.im.y);
     };
     line_fft_pair<L, +1, L / 2>(sm, RowLayout<E, Cfg::PADDED>(), line, j, v, tw, sink);
+}
+
+template <int L, bool DESC, int LW>
+__global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
+    k_sample_rows_pair(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
+                       long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
+                       const float4* __restrict__ tw, const RealDesc* __restrict__ desc) {
+    rows_pair_block<L, DESC, LW>(blockIdx.x, blockIdx.y, s, amp_scale, key0, key1, r0, nrows, keep, chunk, out, tw,
+                                 desc);
 }
 
 // Column pass: lines o = 2 blockIdx.y and o + 1 of in[outer][L][inner], the
@@ -229,6 +221,163 @@ cf_status launch_cols_pair(long long L, const C2<float>* in, long long outer, lo
             });
         }
     });
+}
+
+// --------------------------------------------------------------------------
+// The whole binary32 sampler of one chunk in one cooperative launch, for the
+// small grids where launch and dependency overheads weigh most (2D embedded
+// sides of 64 or 128, 3D of 64 or 128): the blocks stay resident and walk the
+// tiles of the row pass, then (after a grid-wide barrier) those of the
+// column passes, then the deferred binary64 Poisson decisions.  Every tile
+// runs the same code as the separate kernels (rows_pair_block, cols_block),
+// so the results are identical bit for bit.  256 threads per block: the row
+// pass with the 256-thread shape, the column passes with their default shape
+// for lines of at most 128 points.
+// --------------------------------------------------------------------------
+namespace cgp = cooperative_groups;
+
+struct PersistArgs {
+    const float* s;
+    float amp_scale;
+    uint32_t key0, key1, r0;
+    int chunk;
+    const RealDesc* desc;
+    long long m0, m1, n0, n1, n2;  // 2D: m1 = M_last, n2 unused
+    C2<float>* buf1;
+    C2<float>* buf2;
+    FieldEpi<float> epi;
+    PoissonDefer defer;
+};
+
+constexpr int kPersistThreads = 256;
+
+// LL: last axis (rows), LM: middle axis (3D; 0 in 2D), L0: axis 0.
+template <int LL, int LM, int L0, bool DESC>
+__global__ void __launch_bounds__(kPersistThreads, 2)
+    k_sample_persistent(PersistArgs a, const float4* __restrict__ tw4, const C2<float>* __restrict__ tw) {
+    cgp::grid_group grid = cgp::this_grid();
+    static_assert(PairCfg<LL, kPersistThreads>::THREADS == kPersistThreads, "row shape");
+    static_assert(ColsCfg<float, L0, true>::THREADS == kPersistThreads, "column shape");
+    const bool three = LM > 0;
+    const long long nrows = three ? a.m0 * a.m1 : a.m0;
+    const int keep_last = (int)(three ? a.n2 : a.n1);
+    {
+        using RC = PairCfg<LL, kPersistThreads>;
+        const long long nbx = (nrows + RC::LINES - 1) / RC::LINES, nby = (a.chunk + 1) / 2;
+        for (long long it = blockIdx.x; it < nbx * nby; it += gridDim.x) {
+            rows_pair_block<LL, DESC, kPersistThreads>(it % nbx, it / nbx, a.s, a.amp_scale, a.key0, a.key1, a.r0,
+                                                       nrows, keep_last, a.chunk, a.buf1, tw4, a.desc);
+            __syncthreads();
+        }
+    }
+    grid.sync();
+    if constexpr (LM > 0) {
+        static_assert(ColsCfg<float, LM, true>::THREADS == kPersistThreads, "middle shape");
+        // axis 1 of [chunk M0][M1][n2] -> [chunk M0][n1][n2]
+        using CC = ColsCfg<float, LM, true>;
+        const long long tiles = (a.n2 + CC::C - 1) / CC::C, outer = (long long)a.chunk * a.m0;
+        for (long long it = blockIdx.x; it < tiles * outer; it += gridDim.x) {
+            cols_block<float, LM, +1, 1>(it % tiles, it / tiles, a.buf1, a.n2, (int)a.n1, a.buf2, 0, a.epi, tw);
+            __syncthreads();
+        }
+        grid.sync();
+    }
+    {
+        // axis 0 with the field epilogue
+        using CC = ColsCfg<float, L0, true>;
+        const long long inner = three ? a.n1 * a.n2 : a.n1;
+        const long long tiles = (inner + CC::C - 1) / CC::C;
+        const C2<float>* in = three ? a.buf2 : a.buf1;
+        for (long long it = blockIdx.x; it < tiles * a.chunk; it += gridDim.x) {
+            cols_block<float, L0, +1, 1>(it % tiles, it / tiles, in, inner, (int)a.n0, nullptr, 1, a.epi, tw);
+            __syncthreads();
+        }
+    }
+    if (a.defer.items) {
+        grid.sync();
+        const unsigned int n = *a.defer.count < a.defer.capacity ? *a.defer.count : a.defer.capacity;
+        for (unsigned int i = blockIdx.x * kPersistThreads + threadIdx.x; i < n; i += gridDim.x * kPersistThreads) {
+            const PoissonTodo t = a.defer.items[i];
+            *t.dst = poisson_count_f64(t.G, t.half_sigma2, t.nbar, t.f, t.ubits);
+        }
+    }
+}
+
+// Grids the persistent kernel takes: binary32, 2D with embedded sides 64 or
+// 128 on both axes, 3D with 64 or 128 on all three.
+bool persistent_ok(const GridInfo& g) {
+    auto ok = [](long long m) { return m == 64 || m == 128; };
+    if (g.ndim == 2) return ok(g.m[0]) && ok(g.m[1]);
+    if (g.ndim == 3) return ok(g.m[0]) && ok(g.m[1]) && ok(g.m[2]);
+    return false;
+}
+
+template <int LL, int LM, int L0, bool DESC>
+static cf_status launch_persistent_t(PersistArgs& a, cudaStream_t st) {
+    auto kern = k_sample_persistent<LL, LM, L0, DESC>;
+    const size_t smem = std::max(PairCfg<LL, kPersistThreads>::SMEM,
+                                 std::max(ColsCfg<float, L0, true>::SMEM, LM > 0 ? ColsCfg<float, (LM > 0 ? LM : 64), true>::SMEM : (size_t)0));
+    CF_TRY(prepare_smem(kern, smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    CF_CUDA(cudaGetDevice(&dev));
+    CF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, smem));
+    if (per_sm < 1) return fail(CF_ERR_UNSUPPORTED, "persistent sampler does not fit an SM");
+    // as many blocks as the largest phase has tiles, at most all resident ones
+    const long long nrows = LM > 0 ? a.m0 * a.m1 : a.m0;
+    long long want = ((nrows + PairCfg<LL, kPersistThreads>::LINES - 1) / PairCfg<LL, kPersistThreads>::LINES) *
+                     ((a.chunk + 1) / 2);
+    const long long cap = (long long)per_sm * sms;
+    const unsigned blocks = (unsigned)(want < 1 ? 1 : (want > cap ? cap : want));
+    const float4* tw4 = twiddles_f32x2();
+    const C2<float>* tw = twiddles_f32();
+    void* args[] = {(void*)&a, (void*)&tw4, (void*)&tw};
+    ScopedKernelTimer kt(st, "sample_persistent_f32", LL);
+    CF_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kPersistThreads), args, smem, st));
+    CF_CHECK_LAUNCH();
+    return CF_OK;
+}
+
+template <bool DESC>
+static cf_status launch_persistent_d(const GridInfo& g, PersistArgs& a, cudaStream_t st) {
+    if (g.ndim == 2) {
+        if (g.m[0] == 64 && g.m[1] == 64) return launch_persistent_t<64, 0, 64, DESC>(a, st);
+        if (g.m[0] == 64 && g.m[1] == 128) return launch_persistent_t<128, 0, 64, DESC>(a, st);
+        if (g.m[0] == 128 && g.m[1] == 64) return launch_persistent_t<64, 0, 128, DESC>(a, st);
+        if (g.m[0] == 128 && g.m[1] == 128) return launch_persistent_t<128, 0, 128, DESC>(a, st);
+    } else if (g.ndim == 3 && g.m[0] == g.m[1] && g.m[1] == g.m[2]) {
+        if (g.m[0] == 64) return launch_persistent_t<64, 64, 64, DESC>(a, st);
+        if (g.m[0] == 128) return launch_persistent_t<128, 128, 128, DESC>(a, st);
+    }
+    return fail(CF_ERR_UNSUPPORTED, "no persistent sampler for this grid");
+}
+
+// One chunk of nr realizations through the persistent kernel: buf1 / buf2 as
+// in the separate passes; the deferred-decision list's counter is cleared on
+// st before the launch (as the separate passes do).
+cf_status launch_sample_persistent(const GridInfo& g, const float* s, float amp_scale, uint64_t seed, uint32_t r0,
+                                   int nr, C2<float>* buf1, C2<float>* buf2, const FieldEpi<float>& epi,
+                                   const PoissonDefer& defer, const RealDesc* desc, cudaStream_t st) {
+    if (!persistent_ok(g)) return fail(CF_ERR_UNSUPPORTED, "no persistent sampler for this grid");
+    PersistArgs a{};
+    a.s = s;
+    a.amp_scale = amp_scale;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.r0 = r0;
+    a.chunk = nr;
+    a.desc = desc;
+    a.m0 = g.m[0];
+    a.m1 = g.ndim == 3 ? g.m[1] : g.m[1];
+    a.n0 = g.n[0];
+    a.n1 = g.n[1];
+    a.n2 = g.ndim == 3 ? g.n[2] : 1;
+    a.buf1 = buf1;
+    a.buf2 = buf2;
+    a.epi = epi;
+    a.defer = defer;
+    if (defer.items) CF_CUDA(cudaMemsetAsync(defer.count, 0, sizeof(unsigned int), st));
+    return desc ? launch_persistent_d<true>(g, a, st) : launch_persistent_d<false>(g, a, st);
 }
 
 }  // namespace cf

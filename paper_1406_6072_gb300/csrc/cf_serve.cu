@@ -34,7 +34,10 @@ struct CudaSlot {
 
 class CudaBackend : public cfserve::Backend {
   public:
-    CudaBackend(int device, int nslots, int max_real) : device_(device), max_real_(max_real) {
+    // nslots streams; with `priority_last`, the last one (the slot reserved
+    // for small requests) has the highest priority
+    CudaBackend(int device, int nslots, int max_real, bool priority_last)
+        : device_(device), max_real_(max_real) {
         cudaSetDevice(device_);
         // spectra are built on the highest-priority stream: a request that
         // waits for its embedding then does not also wait for the blocks of
@@ -43,8 +46,10 @@ class CudaBackend : public cfserve::Backend {
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
         ok_ = cudaStreamCreateWithPriority(&embed_stream_, cudaStreamNonBlocking, greatest) == cudaSuccess;
         slots_.resize(nslots);
-        for (auto& s : slots_) {
-            ok_ = ok_ && cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < nslots; ++i) {
+            CudaSlot& s = slots_[i];
+            const int prio = (priority_last && i == nslots - 1) ? greatest : least;
+            ok_ = ok_ && cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio) == cudaSuccess;
             ok_ = ok_ && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess;
             ok_ = ok_ && cudaMallocHost((void**)&s.host_desc, sizeof(RealDesc) * (size_t)max_real) == cudaSuccess;
             ok_ = ok_ && cudaMalloc((void**)&s.dev_desc, sizeof(RealDesc) * (size_t)max_real) == cudaSuccess;
@@ -214,7 +219,7 @@ extern "C" cf_status cf_serve_create(const cf_serve_cfg* cfg, cf_server** out) {
     if (!cfg || !out) return fail(CF_ERR_ARG, "cfg and out are required");
     *out = nullptr;
     if (cfg->max_inflight < 1 || cfg->queue_capacity < 1 || cfg->cache_entries < 1 ||
-        cfg->max_batch_realizations < 1 || cfg->hbm_budget == 0)
+        cfg->max_batch_realizations < 1 || cfg->hbm_budget == 0 || cfg->small_request_cells < 0)
         return fail(CF_ERR_ARG, "cfg fields must be positive");
     int ndev = 0;
     CF_CUDA(cudaGetDeviceCount(&ndev));
@@ -222,7 +227,9 @@ extern "C" cf_status cf_serve_create(const cf_serve_cfg* cfg, cf_server** out) {
     CF_CUDA(cudaSetDevice(cfg->device));
     CF_TRY(ensure_device_init());
     cf_server* sv = new cf_server();
-    sv->backend.reset(new CudaBackend(cfg->device, cfg->max_inflight, cfg->max_batch_realizations));
+    const bool reserved = cfg->small_request_cells > 0;
+    sv->backend.reset(new CudaBackend(cfg->device, cfg->max_inflight + (reserved ? 1 : 0),
+                                      cfg->max_batch_realizations, reserved));
     if (!sv->backend->ok()) {
         delete sv;
         cudaGetLastError();

@@ -125,7 +125,10 @@ class Scheduler {
         if (cfg_.queue_capacity < 1) cfg_.queue_capacity = 1;
         if (cfg_.cache_entries < 1) cfg_.cache_entries = 1;
         if (cfg_.max_batch_realizations < 1) cfg_.max_batch_realizations = 1;
-        slots_.resize(cfg_.max_inflight);
+        if (cfg_.small_request_cells < 0) cfg_.small_request_cells = 0;
+        // slots [0, max_inflight) take any request; slot max_inflight (if
+        // small_request_cells > 0) only small ones
+        slots_.resize(cfg_.max_inflight + (cfg_.small_request_cells > 0 ? 1 : 0));
         worker_ = std::thread([this] { run(); });
         embedder_ = std::thread([this] { build_loop(); });
     }
@@ -438,18 +441,32 @@ class Scheduler {
     // the way (at most kMaxBuilds at a time) and completes requests whose
     // spectrum failed.  True if the queue or a slot changed.
     static constexpr int kMaxBuilds = 4;
+    static long long cells_of(const cf_request& r) {
+        long long c = 2ll * r.R;
+        for (int a = 0; a < r.grid.ndim; ++a) c *= r.grid.n[a];
+        return c;
+    }
+    bool small(const Job* j) const {
+        return cfg_.small_request_cells > 0 && cells_of(j->req) <= (long long)cfg_.small_request_cells;
+    }
+
     bool admit(std::unique_lock<std::mutex>&) {
         int slot = -1;
-        for (int i = 0; i < (int)slots_.size(); ++i)
+        for (int i = 0; i < cfg_.max_inflight; ++i)
             if (slots_[i].jobs.empty()) {
                 slot = i;
                 break;
             }
+        // the reserved slot, for small requests only
+        const bool small_only = slot < 0 && (int)slots_.size() > cfg_.max_inflight &&
+                                slots_[cfg_.max_inflight].jobs.empty();
+        if (small_only) slot = cfg_.max_inflight;
         if (slot < 0 || queue_.empty()) return false;
         Job* head = nullptr;
         CacheEntry* e = nullptr;
         for (size_t q = 0; q < queue_.size() && q < 256 && !head; ++q) {
             Job* j = queue_[q];
+            if (small_only && !small(j)) continue;
             CacheEntry* ce = find_entry(spectrum_key(j->req));
             if (!ce) {
                 if (builds_in_progress() >= kMaxBuilds) continue;
@@ -488,6 +505,7 @@ class Scheduler {
             Job* c = queue_[q];
             if (nreal + c->req.R > cfg_.max_batch_realizations) break;
             if (shape_key(c->req) != sk) continue;
+            if (small_only && !small(c)) continue;
             CacheEntry* ce = find_entry(spectrum_key(c->req));
             if (!ce || ce->building || ce->status != CF_OK) continue;
             batch.push_back(c);

@@ -291,6 +291,47 @@ int main() {
                fast_ok, fast_max, (int)ws, (int)rs.status, rs.latency_ms, rs.cache_hit);
         s.release(slow);
     }
+    // 11. a slot reserved for small requests: with the only general slot busy
+    // on a long batch, small requests still run (and large ones wait)
+    {
+        FakeBackend be(2);
+        cf_serve_cfg c = make_cfg(1ull << 30, 1, 1000, 8, 64);
+        c.small_request_cells = 2 * 4 * 16 * 16;  // up to 4 realizations of 16^2
+        Scheduler s(c, &be);
+        uint64_t warm;
+        s.submit(make_req(16, 2, 1, 2.0), &warm);
+        cf_result r;
+        s.wait(warm, 5000000, &r);
+        s.release(warm);
+        be.per_real = 0.02;                          // the large batch takes 40 x 20 ms
+        uint64_t big, big2;
+        s.submit(make_req(16, 2, 40, 2.0), &big);    // 2 * 40 * 256 cells: not small
+        std::this_thread::sleep_for(std::chrono::milliseconds(20));
+        be.per_real = 1e-4;
+        s.submit(make_req(16, 2, 40, 2.0), &big2);   // waits for the general slot
+        std::vector<uint64_t> sm;
+        for (int i = 0; i < 6; ++i) {
+            uint64_t k;
+            s.submit(make_req(16, 2, 1 + i % 4, 2.0), &k);
+            sm.push_back(k);
+        }
+        double small_max = 0;
+        int small_ok = 0;
+        for (auto k : sm) {
+            cf_result rr;
+            if (s.wait(k, 5000000, &rr) == CF_OK && rr.status == CF_OK) ++small_ok;
+            small_max = std::max(small_max, rr.latency_ms);
+            s.release(k);
+        }
+        cf_result rb, rb2;
+        s.wait(big, 10000000, &rb);
+        s.wait(big2, 10000000, &rb2);
+        printf("{\"scenario\": \"reserved\", \"small_ok\": %d, \"small_max_ms\": %.3f, \"big_ms\": %.3f, "
+               "\"big2_status\": %d, \"big2_queue_ms\": %.3f}\n",
+               small_ok, small_max, rb.latency_ms, (int)rb2.status, rb2.queue_ms);
+        s.release(big);
+        s.release(big2);
+    }
     {  // a request larger than one batch is refused at submission
         FakeBackend be(1);
         Scheduler s(make_cfg(1ull << 30, 1, 10, 2, 8), &be);

@@ -73,12 +73,12 @@ def test_every_cta_shape_gives_the_same_bits(n, R):
         for cs in range(3):
             for chunk in (0, 2):
                 cf.cf_tune_set(emb, cf.CF_F32, chunk, rs, cs)
-                assert cf.cf_tune_info(emb, cf.CF_F32) == (chunk, rs, cs)
+                assert cf.cf_tune_info(emb, cf.CF_F32) == (chunk, rs, cs, 0)
                 f, c = _run_lp(emb, n, R, cf.cf_sample_workspace_size(emb, R, cf.CF_F32))
                 assert torch.equal(f, ref_f), (rs, cs, chunk)
                 assert torch.equal(c, ref_c), (rs, cs, chunk)
     cf.cf_tune_set(emb, cf.CF_F32, 0, 0, 0)
-    assert cf.cf_tune_info(emb, cf.CF_F32) == (0, 0, 0)
+    assert cf.cf_tune_info(emb, cf.CF_F32) == (0, 0, 0, 0)
     emb.close()
 
 
@@ -90,7 +90,7 @@ def test_tuner_picks_shapes_and_changes_no_result():
     ws = torch.empty(wsb, dtype=torch.uint8, device=DEV)
     scratch = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
     chunk, ms = cf.cf_tune_sample(emb, cf.CF_F32, R, ws, wsb, scratch)
-    c, rs, cs = cf.cf_tune_info(emb, cf.CF_F32)
+    c, rs, cs, _ = cf.cf_tune_info(emb, cf.CF_F32)
     assert c == chunk and 0 <= rs < 3 and 0 <= cs < 3 and ms > 0
     after = _run(emb, n, R, cf.CF_F32, cf.cf_sample_workspace_size(emb, R, cf.CF_F32))
     assert torch.equal(before, after)
@@ -100,8 +100,35 @@ def test_tuner_picks_shapes_and_changes_no_result():
 
 def test_tune_set_rejects_bad_shapes():
     emb = cf.cf_embed(cf.make_grid((32, 32)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 2.0))
-    for args in ((0, 3, 0), (0, 0, -1), (-1, 0, 0)):
+    for args in ((0, 3, 0), (0, 0, -1), (-1, 0, 0), (0, 0, 0, 2)):
         with pytest.raises(cf.CfError) as ei:
             cf.cf_tune_set(emb, cf.CF_F32, *args)
         assert ei.value.status == cf.CF_ERR_ARG
+    big = cf.cf_embed(cf.make_grid((256, 256)), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 2.0))
+    with pytest.raises(cf.CfError) as ei:  # no persistent sampler for 512^2 embeddings
+        cf.cf_tune_set(big, cf.CF_F32, 0, 0, 0, 1)
+    assert ei.value.status == cf.CF_ERR_UNSUPPORTED
+    emb.close()
+    big.close()
+
+
+@pytest.mark.parametrize("n,R,lp", [((64, 64), 5, True), ((32, 64), 3, False), ((32, 32, 32), 4, True),
+                                    ((64, 64, 64), 3, True), ((20, 50), 2, True)])
+def test_persistent_sampler_gives_the_same_bits(n, R, lp):
+    """The whole chunk in one cooperative launch (rows, a grid-wide barrier,
+    the column passes, the deferred binary64 decisions) runs the same tiles
+    as the separate launches: identical fields and counts, for whole and
+    chunked batches (an odd tail included)."""
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GEN_CAUCHY, 0.9, 3.0, 0.4), cf.CF_EMBED_CLAMP)
+    wsb = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+    ref = _run_lp(emb, n, R, wsb) if lp else (_run(emb, n, R, cf.CF_F32, wsb), None)
+    for chunk in (0, 2):
+        cf.cf_tune_set(emb, cf.CF_F32, chunk, 0, 0, 1)
+        assert cf.cf_tune_info(emb, cf.CF_F32)[3] == 1
+        wsb2 = cf.cf_sample_workspace_size(emb, R, cf.CF_F32)
+        got = _run_lp(emb, n, R, wsb2) if lp else (_run(emb, n, R, cf.CF_F32, wsb2), None)
+        assert torch.equal(got[0], ref[0]), chunk
+        if lp:
+            assert torch.equal(got[1], ref[1]), chunk
+    cf.cf_tune_set(emb, cf.CF_F32)
     emb.close()

@@ -91,6 +91,14 @@ def test_slow_build_does_not_hold_up_ready_requests(scenarios):
     assert s["slow_ms"] >= 300 and s["slow_hit"] == 0
 
 
+def test_reserved_slot_serves_small_requests_beside_a_long_batch(scenarios):
+    s = scenarios["reserved"]
+    assert s["small_ok"] == 6
+    assert s["small_max_ms"] < 200        # the long batch runs 800 ms
+    assert s["big_ms"] >= 700
+    assert s["big2_status"] == 0 and s["big2_queue_ms"] >= 500  # large requests keep to the general slot
+
+
 def test_request_larger_than_a_batch_is_refused(scenarios):
     s = scenarios["oversize"]
     assert s["too_big"] == 1  # CF_ERR_ARG

@@ -48,6 +48,23 @@ def test_noalloc_matches_workspace_sampler_twice(n):
     emb.close()
 
 
+def test_noalloc_takes_no_device_memory():
+    """After the first call (its one-time set-up), further calls leave the
+    device's free memory as it is: nothing is allocated or freed."""
+    n, R = (128, 64), 4
+    emb = cf.cf_embed(cf.make_grid(n), cf.make_xi(cf.CF_XI_GAUSSIAN, 1.0, 3.0))
+    out = torch.empty((R, 2) + n, dtype=torch.float32, device=DEV)
+    cf.cf_sample_noalloc(emb, 5, 0, R, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    for k in range(3):
+        cf.cf_sample_noalloc(emb, 6 + k, 10 * k, R, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 == free0
+    emb.close()
+
+
 def test_noalloc_rejects_grids_beyond_the_static_array():
     # 3D 64x64x128: one realization needs 24 MiB of intermediate
     emb = cf.cf_embed(cf.make_grid((64, 64, 128)), cf.make_xi(cf.CF_XI_EXPONENTIAL, 1.0, 2.0))
