@@ -922,21 +922,41 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
     from paper_1406_6072_gb300 import replicas
     from paper_1406_6072_gb300.pipeline import FieldPipeline
     m = wl.m
-    ax = [np.arange(v) for v in m]
-    lag = [np.where(a < n, a, a - 2 * n).astype(np.float64) * c for a, n, c in zip(ax, wl.n, wl.cell)]
-    r2 = lag[0][:, None] ** 2 + lag[1][None, :] ** 2
-    table = (wl.amp / (1.0 + r2 / wl.scale ** 2) ** wl.beta) if wl.xi_kind == 1 else None
-    if table is None:
-        return None
-    h_table = torch.from_numpy(np.ascontiguousarray(table)).pin_memory()
+    # The step's input as a user passes it.  2D: the embedded first row of the
+    # workload's two-point function tabulated on the host (a measured
+    # correlation function), copied in every step.  3D: the analytic xi, whose
+    # three parameters travel by value (a 256^3 table would be 134 MB per step).
+    table = None
+    if len(m) <= 2:
+        ax = [np.arange(v) for v in m]
+        lag = [np.where(a < n, a, a - 2 * n).astype(np.float64) * c for a, n, c in zip(ax, wl.n, wl.cell)]
+        r2 = np.zeros(tuple(int(v) for v in m))
+        for a, l in enumerate(lag):
+            r2 = r2 + (l ** 2).reshape([-1 if b == a else 1 for b in range(len(m))])
+        if wl.xi_kind == cf.CF_XI_GEN_CAUCHY:
+            table = wl.amp / (1.0 + r2 / wl.scale ** 2) ** wl.beta
+        elif wl.xi_kind == cf.CF_XI_GAUSSIAN:
+            table = wl.amp * np.exp(-r2 / (2.0 * wl.scale ** 2))
+        elif wl.xi_kind == cf.CF_XI_EXPONENTIAL:
+            table = wl.amp * np.exp(-np.sqrt(r2) / wl.scale)
+        else:
+            return None
+    h_table = torch.from_numpy(np.ascontiguousarray(table)).pin_memory() if table is not None else None
     other = FieldPipeline(wl, pipe.dev, stream=torch.cuda.Stream(pipe.dev), fused=pipe.fused,
                           embed_df=bool(pipe.flags & cf.CF_EMBED_DF))
     lanes = []
     for p in (pipe, other):
-        d_table = torch.empty_like(h_table, device=p.dev)
-        outs = [p.fields, p.counts, p.pk, p.mean, p.cov, p.pkg, p.meang, p.covg]
+        if h_table is not None:
+            d_table = torch.empty_like(h_table, device=p.dev)
+            xi = cf.make_xi(cf.CF_XI_TABLE, table=d_table, table_on_device=1)
+        else:
+            d_table = None
+            xi = cf.make_xi(wl.xi_kind, wl.amp, wl.scale, wl.beta)
+        # every result the step computes: fields, counts, both spectra with
+        # their mean and covariance (those of the pipeline's configuration)
+        outs = [o for o in (getattr(p, a, None) for a in ("fields", "counts", "pk", "mean", "cov", "pkg",
+                                                           "meang", "covg")) if o is not None]
         h_outs = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
-        xi = cf.make_xi(cf.CF_XI_TABLE, table=d_table, table_on_device=1)
         lanes.append({"p": p, "d_table": d_table, "outs": outs, "h_outs": h_outs, "xi": xi,
                       "copy": torch.cuda.Stream(p.dev), "computed": torch.cuda.Event(),
                       "done": torch.cuda.Event()})
@@ -948,8 +968,9 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
         # copies have read the previous results
         ln = lanes[k % 2]
         p = ln["p"]
-        with torch.cuda.stream(p.embed_stream):
-            ln["d_table"].copy_(h_table, non_blocking=True)  # read by the embedding, in its stream order
+        if h_table is not None:
+            with torch.cuda.stream(p.embed_stream):
+                ln["d_table"].copy_(h_table, non_blocking=True)  # read by the embedding, in its stream order
         with torch.cuda.stream(p.stream):
             p.embed(ln["xi"])
             p.stream.wait_event(ln["done"])
@@ -971,9 +992,10 @@ def e2e_run(pipe, wl, steps, warmup, rank, world=1):
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     other.close()
-    h2d = h_table.numel() * 8
+    h2d = h_table.numel() * 8 if h_table is not None else 0
     d2h = sum(h.numel() * h.element_size() for h in lanes[0]["h_outs"])
-    return ms, h2d, d2h
+    return ms, h2d, d2h, ("tabulated xi, %d doubles copied in per step" % h_table.numel()) if h_table is not None \
+        else "analytic xi (parameters by value)"
 
 
 def main():
@@ -1099,10 +1121,10 @@ def main():
     if not args.no_e2e:
         r = e2e_run(pipe, wl, max(3, args.steps // 2), 2, rank, world)
         if r is not None:
-            e_ms, h2d, d2h = r
+            e_ms, h2d, d2h, e_input = r
             e_max = replicas.max_over_ranks(e_ms, dist, dev)
             e2e = {"value": cells_all / (e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h), "ms_per_step": e_max}
+                   "d2h_bytes_per_step": int(d2h), "ms_per_step": e_max, "input": e_input}
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_sample_realizations)

@@ -91,6 +91,20 @@ __global__ void __launch_bounds__(SRowsCfg<T, L>::THREADS, SRowsCfg<T, L>::MINB)
                 v[q] = cscale(lo, sa[q] * amp_scale);
                 v[q + E / 2] = cscale(hi, sb[q] * amp_scale);
             }
+        } else if constexpr (E >= 4) {
+            // two cell pairs of this thread at once: the paired Box-Muller
+            // (the same draws, its polynomials in f32x2 instructions)
+#pragma unroll
+            for (int q = 0; q < E / 2; q += 2) {
+                const int ca = j + q * STEP, cb = ca + STEP;
+                CP lo, hi;
+                noise_pair_f32x2((unsigned long long)rw * (L / 2) + ca, r, key0, key1,
+                                 (unsigned long long)rw * (L / 2) + cb, r, key0, key1, lo, hi);
+                v[q] = cscale(mk(lo.re.x, lo.im.x), srow[ca] * amp_scale);
+                v[q + 1] = cscale(mk(lo.re.y, lo.im.y), srow[cb] * amp_scale);
+                v[q + E / 2] = cscale(mk(hi.re.x, hi.im.x), srow[ca + L / 2] * amp_scale);
+                v[q + 1 + E / 2] = cscale(mk(hi.re.y, hi.im.y), srow[cb + L / 2] * amp_scale);
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < E / 2; ++q) {
@@ -135,6 +149,19 @@ cf_status launch_sample_persistent(const GridInfo& g, const float* s, float amp_
                                    int nr, C2<float>* buf1, C2<float>* buf2, const FieldEpi<float>& epi,
                                    const PoissonDefer& defer, const RealDesc* desc, cudaStream_t st);
 
+// Binary32 row pass of 1024-point rows with one warp per row
+// (cf_sample_warp.cu; CF_SROWS_WARP=0 in the environment turns it off).
+cf_status launch_rows_warp(long long L, int keep, const float* s, float amp_scale, uint64_t seed, uint32_t r0,
+                           int chunk, long long nrows, C2<float>* out, cudaStream_t st, const RealDesc* desc,
+                           int shape);
+static bool warp_rows() {
+    static const bool on = [] {
+        const char* e = getenv("CF_SROWS_WARP");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 // Binary32 row pass with two realizations per thread (CF_SROWS_PAIR=0 in the
 // environment turns it off).
 static bool pair_rows() {
@@ -177,6 +204,8 @@ static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_sca
                                     int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
                                     cudaStream_t st, const RealDesc* desc = nullptr, int shape = 0) {
     if constexpr (sizeof(T) == 4) {
+        if (mode == 0 && L == 1024 && warp_rows())
+            return launch_rows_warp(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc, shape);
         if (mode == 0 && L >= 16 && pair_rows())
             return launch_rows_pair(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc, shape);
     }

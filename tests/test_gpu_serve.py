@@ -146,7 +146,10 @@ def test_batched_mixed_stream_matches_the_oracle(orc):
              ((64, 64), cf.CF_XI_GAUSSIAN, 0.80, 3.0, 0.0, 0xABCDEF0123, 2**32 - 9, 4, 0.80, 0.5),
              ((16, 16, 16), cf.CF_XI_EXPONENTIAL, 0.9, 2.0, 0.0, 504, 3, 2, 0.9, 3.0),
              ((16, 16, 16), cf.CF_XI_EXPONENTIAL, 0.4, 2.0, 0.0, 505, 9, 3, 0.4, 1.0),
-             ((64, 64), cf.CF_XI_GEN_CAUCHY, 0.6, 4.0, 0.4, 506, 1, 2, 0.6, 2.0)]
+             ((64, 64), cf.CF_XI_GEN_CAUCHY, 0.6, 4.0, 0.4, 506, 1, 2, 0.6, 2.0),
+             # rows of 1024 points (the warp row pass with descriptors)
+             ((512, 512), cf.CF_XI_GEN_CAUCHY, 0.8, 8.0, 0.4, 507, 4, 2, 0.8, 2.0),
+             ((512, 512), cf.CF_XI_GEN_CAUCHY, 0.5, 8.0, 0.4, 508, 0, 1, 0.5, 1.0)]
     sv = cf.cf_serve_create(cf.make_serve_cfg(max_inflight=1, max_batch_realizations=64))
     big = cf.make_request((1024, 1024), cf.CF_XI_GAUSSIAN, 1.0, 4.0, R=64)
     t_big = cf.cf_serve_submit(sv, big)
