@@ -149,8 +149,9 @@ cf_status launch_sample_persistent(const GridInfo& g, const float* s, float amp_
                                    int nr, C2<float>* buf1, C2<float>* buf2, const FieldEpi<float>& epi,
                                    const PoissonDefer& defer, const RealDesc* desc, cudaStream_t st);
 
-// Binary32 row pass of 1024-point rows with one warp per row
-// (cf_sample_warp.cu; CF_SROWS_WARP=0 in the environment turns it off).
+// Binary32 row pass of 256- and 1024-point rows with P = sqrt(L) lanes per
+// row (cf_sample_warp.cu; CF_SROWS_WARP=0 in the environment turns it off).
+bool warp_rows_len(long long L);
 cf_status launch_rows_warp(long long L, int keep, const float* s, float amp_scale, uint64_t seed, uint32_t r0,
                            int chunk, long long nrows, C2<float>* out, cudaStream_t st, const RealDesc* desc,
                            int shape);
@@ -204,7 +205,7 @@ static cf_status launch_sample_rows(long long L, int keep, const T* s, T amp_sca
                                     int chunk, long long nrows, C2<T>* out, int mode, const FieldEpi<T>& epi,
                                     cudaStream_t st, const RealDesc* desc = nullptr, int shape = 0) {
     if constexpr (sizeof(T) == 4) {
-        if (mode == 0 && L == 1024 && warp_rows())
+        if (mode == 0 && warp_rows_len(L) && warp_rows())
             return launch_rows_warp(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc, shape);
         if (mode == 0 && L >= 16 && pair_rows())
             return launch_rows_pair(L, keep, s, amp_scale, seed, r0, chunk, nrows, out, st, desc, shape);

@@ -59,9 +59,13 @@ def test_plan_replays_match_eager_calls(n, kind, scale):
         assert torch.equal(fields, ef), k
         assert torch.equal(counts, ec), k
         # bin sums use binary32 partial sums and atomic additions: the spectra agree
-        # to rounding order (other realizations would differ at order one)
-        for a, b in ((pk, epk), (pkc, epkc), (mean, emean), (cov, ecov)):
+        # to rounding order (other realizations would differ at order one).  The
+        # covariance's small entries are differences of products of spectra
+        # that agree to about 1e-7, so they are compared against its largest
+        # entry.
+        for a, b in ((pk, epk), (pkc, epkc), (mean, emean)):
             assert torch.allclose(a, b, rtol=1e-6, atol=1e-9 * float(b.abs().max())), k
+        assert torch.allclose(cov, ecov, rtol=1e-5, atol=1e-6 * float(ecov.abs().max())), k
     plan.seek(13)
     plan.launch()
     torch.cuda.synchronize()
