@@ -208,6 +208,19 @@ CF_API cf_status cf_embedding_info(const cf_embedding* e, cf_grid* g, cf_embed_r
 CF_API cf_status cf_draw_noise(uint64_t seed, uint64_t r0, int32_t R, int64_t ncells, int64_t m_last,
                         cf_dtype dt, void* out, cf_stream_t s);
 
+/* Self-check of the binary32 noise arithmetic (section 2, eq. (Papos2): the
+ * draws are the specification's only if every operation rounds as it
+ * specifies).  The noise kernels form the logarithm's quotient
+ * (m - 1) / (m + 1) and the Box-Muller square root with short sequences; this
+ * call compares them with the IEEE correctly rounded quotient and square root
+ * over every binary32 input of their domains (m from sqrt(1/2) to sqrt(2):
+ * 8.4 M inputs; x = +-0 and x from 2^-24 to 34: 0.24 G inputs) on the current
+ * device, synchronously.  mismatches (host, 2 entries): quotient, square root
+ * (both 0: the draws are the specification's).  examples (host, 2 entries,
+ * may be NULL): the bit pattern of the first mismatching m and x found (0
+ * where none).  Allocates 24 bytes of device memory for the call. */
+CF_API cf_status cf_noise_selfcheck(uint64_t* mismatches, uint32_t* examples);
+
 /* Workspace (bytes, device) that cf_sample / cf_sample_lp need for R
  * realizations; realizations are processed in chunks whose intermediate
  * fits 1 GiB (or the chunk cf_tune_sample recorded for this grid), so the size

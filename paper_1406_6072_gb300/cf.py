@@ -117,6 +117,7 @@ _sigs = {
     "cf_embedding_sqrt_lambda": [_P, _P, _S],
     "cf_embedding_info": [_P, C.POINTER(cf_grid), C.POINTER(cf_embed_report)],
     "cf_draw_noise": [C.c_uint64, C.c_uint64, C.c_int32, C.c_int64, C.c_int64, C.c_int32, _P, _S],
+    "cf_noise_selfcheck": [C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)],
     "cf_sample_workspace_size": [_P, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "cf_sample": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, _P, C.c_size_t, _S],
     "cf_sample_lp": [_P, C.c_uint64, C.c_uint64, C.c_int32, C.c_int32, _P, C.POINTER(cf_lp_params), _P,
@@ -318,6 +319,16 @@ def cf_embedding_info(emb):
 
 def cf_draw_noise(seed, r0, R, ncells, m_last, dtype, out, stream=None):
     _check(_lib.cf_draw_noise(seed, r0, R, ncells, m_last, dtype, _ptr(out), _stream(stream)), "cf_draw_noise")
+
+
+def cf_noise_selfcheck():
+    """Mismatches of the noise's quotient and square-root sequences against
+    the IEEE operations over their whole input domains, and the first
+    mismatching inputs' bit patterns: ((nq, ns), (mq, xs))."""
+    mism = (C.c_uint64 * 2)()
+    ex = (C.c_uint32 * 2)()
+    _check(_lib.cf_noise_selfcheck(mism, ex), "cf_noise_selfcheck")
+    return (int(mism[0]), int(mism[1])), (int(ex[0]), int(ex[1]))
 
 
 def cf_sample_workspace_size(emb, R, dtype):

@@ -65,6 +65,7 @@ def test_argument_errors_before_any_cuda_call(cfmod):
     assert lib.cf_embed(C.byref(g), C.byref(bad), 0, None, C.byref(h), C.byref(rep)) == cfmod.CF_ERR_ARG
     assert lib.cf_sample(None, 0, 0, 1, cfmod.CF_F32, None, None, 0, None) == cfmod.CF_ERR_ARG
     assert lib.cf_draw_noise(0, 0, 1, 16, 3, cfmod.CF_F32, C.c_void_p(8), None) == cfmod.CF_ERR_ARG
+    assert lib.cf_noise_selfcheck(None, None) == cfmod.CF_ERR_ARG
     assert lib.cf_draw_noise(0, 2**32 - 1, 2, 16, 4, cfmod.CF_F32, C.c_void_p(8), None) == cfmod.CF_ERR_ARG
     n = C.c_size_t()
     b = cfmod.make_bins(8)
