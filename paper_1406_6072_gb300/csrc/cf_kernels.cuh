@@ -196,14 +196,27 @@ __device__ __forceinline__ void cols_block(long long bx, long long o, const C2<T
     C2<T> v[G::E];
 #pragma unroll
     for (int q = 0; q < G::E; ++q) v[q] = src[(size_t)(j + q * (L / G::E)) * (size_t)inner];
-    auto sink = [&](int, int p, C2<T> val) {
-        if (!valid || p >= keep) return;
-        if (mode == 0)
-            out[((size_t)o * keep + p) * (size_t)inner + i] = val;
-        else
-            epi((int)o, (long long)p * inner + i, val);
+    const ColLayout<G::E, Cfg::C> lay;
+    if (mode == 0) {
+        auto sink = [&](int, int p, C2<T> val) {
+            if (valid && p < keep) out[((size_t)o * keep + p) * (size_t)inner + i] = val;
+        };
+        line_fft<T, L, SIGN, KEEP>(sm, lay, ln, j, v, tw, sink);
+        return;
+    }
+    // field epilogue: the kept outputs go to shared memory first, and the
+    // epilogue (split, lognormal, Poisson) runs after the transform, when
+    // the line's registers are free again
+    auto to_smem = [&](int, int p, C2<T> val) {
+        if (p < keep) sm[lay(ln, p)] = val;
     };
-    line_fft<T, L, SIGN, KEEP>(sm, ColLayout<G::E, Cfg::C>(), ln, j, v, tw, sink);
+    line_fft<T, L, SIGN, KEEP, true>(sm, lay, ln, j, v, tw, to_smem);
+    __syncthreads();
+    if (valid) {
+#pragma unroll 1
+        for (int p = j; p < keep; p += G::TL) epi((int)o, (long long)p * inner + i, sm[lay(ln, p)]);
+    }
+    __syncthreads();  // the exchange buffer is free for the next tile
 }
 
 template <typename T, int L, int SIGN, int KEEP_HALF>
