@@ -271,8 +271,8 @@ CF_API cf_status cf_sample_noalloc(const cf_embedding* e, uint64_t seed, uint64_
 /* Autotuner of the sampler's schedule.  Times cf_sample on R realizations of
  * e for each candidate chunk that fits ws_bytes (realizations per launch of
  * the transform passes: 1, 2, 4, ... up to R), then, in binary32 on grids
- * with a side of 256 or more, each of the 3 CTA shapes of the paired row
- * pass (and of the paired column pass, where it is enabled) at the best
+ * with a side of 256 or more, each of the 3 CTA shapes of the row pass
+ * (and of the paired column pass, where it is enabled) at the best
  * chunk, writing into fields_scratch
  * ([R][2][n...] of dt), and records the fastest for this device, grid shape
  * and dtype (on small binary32 grids also the persistent single launch);
@@ -286,7 +286,9 @@ CF_API cf_status cf_tune_sample(const cf_embedding* e, cf_dtype dt, int32_t R, v
 /* The sampler schedule recorded for e's grid and dt on the current device:
  * realizations per launch (0: the default, chunks of up to 1 GiB of
  * intermediate), the CTA shapes (0, 1, 2; 0 the default) of the binary32
- * passes with two realizations per thread, and whether each chunk runs as one
+ * row pass (rows of 256 or 1024 points: 8, 4 or 16 warps per block; other
+ * rows: 128, 256 or 512 threads) and of the paired column pass (where it is
+ * enabled), and whether each chunk runs as one
  * persistent cooperative launch (1; binary32 grids whose embedded sides are
  * all 64 or 128, else CF_ERR_UNSUPPORTED) instead of one launch per pass (0).
  * cf_tune_sample records the fastest; cf_tune_set records a given one (all
