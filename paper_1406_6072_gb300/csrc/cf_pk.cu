@@ -383,7 +383,8 @@ template <int L>
 __global__ void __launch_bounds__(PkPairCfg<L, CF_PKC2_THREADS>::THREADS, PkPairCfg<L, CF_PKC2_THREADS>::MINB)
     k_pk_cols_pair(const C2<float>* __restrict__ in, long long inner, long long H, long long n_mid, long long n_last,
                    const int16_t* __restrict__ bin_of, long long k2max, int nbins, long long nchunk,
-                   double* __restrict__ acc, long long f0, const float4* __restrict__ tw) {
+                   double* __restrict__ acc, long long f0, const float4* __restrict__ tw,
+                   const int16_t* __restrict__ pbin) {
     using Cfg = PkPairCfg<L, CF_PKC2_THREADS>;
     constexpr int E = Cfg::E;
     constexpr int C = Cfg::LINES;
@@ -413,7 +414,36 @@ __global__ void __launch_bounds__(PkPairCfg<L, CF_PKC2_THREADS>::THREADS, PkPair
     auto to_smem = [&](int lnn, int p, CP val) { sm[lay(lnn, p)] = val; };
     line_fft_pair<L, -1, L, true>(sm, lay, ln, j, v, tw, to_smem);
     __syncthreads();
-    if (valid) {
+    if (valid && pbin) {
+        // this thread's eight consecutive modes p = j E .. j E + 7: their bins
+        // in one 16-byte load from the per-mode table
+        static_assert(E == 8, "one 16-byte load holds the eight bins of a thread");
+        const int il = (int)(i % H);
+        const float w = (il == 0 || 2 * (long long)il == n_last) ? 1.0f : 2.0f;
+        const float2 ww = make_float2(w, w);
+        const uint4 packed = *reinterpret_cast<const uint4*>(pbin + (size_t)i * L + (size_t)j * E);
+        const uint32_t words[4] = {packed.x, packed.y, packed.z, packed.w};
+        int cur = -1;
+        float2 run = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int b = (int)(int16_t)(words[t >> 1] >> (16 * (t & 1)));
+            const CP x = sm[lay(ln, j * E + t)];
+            if (b != cur) {
+                if (cur >= 0) {
+                    atomicAdd(&sbin[cur], run.x);
+                    atomicAdd(&sbin[nbins + cur], run.y);
+                }
+                cur = b;
+                run = make_float2(0.0f, 0.0f);
+            }
+            if (b >= 0) run = f2fma(ww, f2fma(x.re, x.re, f2mul(x.im, x.im)), run);
+        }
+        if (cur >= 0) {
+            atomicAdd(&sbin[cur], run.x);
+            atomicAdd(&sbin[nbins + cur], run.y);
+        }
+    } else if (valid) {
         const int il = (int)(i % H);
         const int smid = (int)signed_mode(i / H, n_mid);
         const int c2 = smid * smid + il * il;
@@ -805,6 +835,7 @@ struct BinCacheEntry {
     std::vector<double> edges;
     int16_t* bin_of;
     unsigned long long* nmodes;
+    int16_t* pbin;  // bin of every (half-spectrum column, axis-0 mode), or null
     cudaEvent_t ready;
 };
 constexpr size_t kBinCacheMax = 32;
@@ -827,10 +858,31 @@ static cf_status build_bins(const PkPlan& P, int16_t* bin_of, unsigned long long
     return CF_OK;
 }
 
+// The bin of every mode the paired binning pass visits: pbin[i n0 + p] for
+// half-spectrum column i (3D: axis-1 mode i / H, last-axis mode i % H) and
+// axis-0 mode p, from bin_of (-1: no bin).  The pass then reads a thread's
+// eight bins with one 16-byte load instead of searching the thresholds per
+// mode.
+__global__ void k_pk_pbin(long long n0, long long n_mid, long long H, const int16_t* __restrict__ bin_of,
+                          long long k2max, int16_t* __restrict__ pbin) {
+    const long long total = n_mid * H * n0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / n0, p = e - i * n0;
+        const long long il = i % H, sm = signed_mode(i / H, n_mid), s0 = signed_mode(p, n0);
+        const long long k2 = s0 * s0 + sm * sm + il * il;
+        pbin[e] = k2 <= k2max ? bin_of[k2] : (int16_t)-1;
+    }
+}
+
+// pbin tables up to this size (bytes) are kept with the cached bins
+constexpr size_t kPbinMaxBytes = (size_t)32 << 20;
+
 // Returns the cached tables for P (building them on stream s if needed), or
-// the workspace copies when the cache is full.
+// the workspace copies when the cache is full (then without pbin).
 static cf_status get_bins(const PkPlan& P, char* ws, cudaStream_t s, const int16_t** bin_of,
-                          const unsigned long long** nmodes) {
+                          const unsigned long long** nmodes, const int16_t** pbin = nullptr) {
+    if (pbin) *pbin = nullptr;
     int dev = 0;
     CF_CUDA(cudaGetDevice(&dev));
     std::vector<double> edges(P.edges.e, P.edges.e + P.nbins + 1);
@@ -844,6 +896,7 @@ static cf_status get_bins(const PkPlan& P, char* ws, cudaStream_t s, const int16
             CF_CUDA(cudaStreamWaitEvent(s, c.ready, cs == cudaStreamCaptureStatusNone ? 0 : cudaEventWaitExternal));
             *bin_of = c.bin_of;
             *nmodes = c.nmodes;
+            if (pbin) *pbin = c.pbin;
             return CF_OK;
         }
     }
@@ -855,15 +908,24 @@ static cf_status get_bins(const PkPlan& P, char* ws, cudaStream_t s, const int16
         *nmodes = nm;
         return CF_OK;
     }
-    BinCacheEntry c{dev, P.g.ndim, P.g.n[0], P.nbins, edges, nullptr, nullptr, nullptr};
+    BinCacheEntry c{dev, P.g.ndim, P.g.n[0], P.nbins, edges, nullptr, nullptr, nullptr, nullptr};
     CF_CUDA(cudaMalloc((void**)&c.bin_of, bin_table_bytes(P.k2max)));
     CF_CUDA(cudaMalloc((void**)&c.nmodes, sizeof(unsigned long long) * P.nbins));
     CF_CUDA(cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming));
     CF_TRY(build_bins(P, c.bin_of, c.nmodes, s));
+    const long long n_mid = P.g.ndim == 3 ? P.g.n[1] : 1;
+    const size_t pbin_bytes = sizeof(int16_t) * (size_t)n_mid * (size_t)P.H * (size_t)P.g.n[0];
+    if (P.g.ndim >= 2 && pbin_bytes <= kPbinMaxBytes) {
+        CF_CUDA(cudaMalloc((void**)&c.pbin, pbin_bytes));
+        k_pk_pbin<<<grid_blocks((long long)(pbin_bytes / sizeof(int16_t)), 256, 2048), 256, 0, s>>>(
+            P.g.n[0], n_mid, P.H, c.bin_of, P.k2max, c.pbin);
+        CF_CHECK_LAUNCH();
+    }
     CF_CUDA(cudaEventRecord(c.ready, s));
     g_bin_cache.push_back(c);
     *bin_of = c.bin_of;
     *nmodes = c.nmodes;
+    if (pbin) *pbin = c.pbin;
     return CF_OK;
 }
 
@@ -935,7 +997,7 @@ static cf_status launch_pk_rows_pair(const void* fields, int kind, const float* 
 template <int L>
 static cf_status launch_pk_cols_pair(const C2<float>* in, long long inner, long long n_mid, const PkPlan& P,
                                      const int16_t* bin_of, double* acc, long long f0, long long nchunk,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, const int16_t* pbin) {
     using Cfg = PkPairCfg<L, CF_PKC2_THREADS>;
     auto kern = k_pk_cols_pair<L>;
     const size_t smem = Cfg::SMEM + 2 * sizeof(float) * (size_t)P.nbins + sizeof(int) * (size_t)(P.nbins + 1);
@@ -943,7 +1005,7 @@ static cf_status launch_pk_cols_pair(const C2<float>* in, long long inner, long 
     dim3 grid((unsigned)((inner + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((nchunk + 1) / 2));
     ScopedKernelTimer kt(s, "pk_cols_f32", L);
     kern<<<grid, Cfg::THREADS, smem, s>>>(in, inner, P.H, n_mid, P.g.n[P.g.ndim - 1], bin_of, P.k2max, P.nbins,
-                                          nchunk, acc, f0, twiddles_f32x2());
+                                          nchunk, acc, f0, twiddles_f32x2(), pbin);
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
@@ -962,6 +1024,7 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
                          double* pk_out, int64_t* nmodes_out, double* mean, double* cov, char* ws, cudaStream_t s) {
     const GridInfo& g = P.g;
     const int16_t* bin_of = nullptr;
+    const int16_t* pbin = nullptr;
     const unsigned long long* nmodes = nullptr;
     double* acc = (double*)(ws + P.off_acc);
     double* cross = (double*)(ws + P.off_cross);
@@ -978,7 +1041,7 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
     const long long n_mid = d == 3 ? g.n[1] : 1;
     {
         ScopedKernelTimer kt(s, "pk_setup");
-        CF_TRY(get_bins(P, ws, s, &bin_of, &nmodes));
+        CF_TRY(get_bins(P, ws, s, &bin_of, &nmodes, &pbin));
         // zero the accumulators (acc .. mask spectrum)
         CF_CUDA(cudaMemsetAsync(ws + P.off_acc, 0, P.off_half - P.off_acc, s));
     }
@@ -1015,7 +1078,8 @@ static cf_status pk_impl(const void* fields, int kind, const float* f, const PkP
             constexpr int LL = decltype(Lc)::value;
             if constexpr (sizeof(T) == 4 && LL >= 16) {
                 if (paired && !masked)
-                    return launch_pk_cols_pair<LL>((const C2<float>*)half, inner, n_mid, P, bin_of, acc, f0, nc, s);
+                    return launch_pk_cols_pair<LL>((const C2<float>*)half, inner, n_mid, P, bin_of, acc, f0, nc, s,
+                                                   LL == g.n[0] ? pbin : nullptr);
             }
             return launch_pk_cols<T, LL>(half, inner, n_mid, P, bin_of, acc, masked ? cross : nullptr,
                                          masked ? mask_spec : nullptr, f0, nc, s);
