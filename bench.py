@@ -190,6 +190,28 @@ def recorded_traffic(kernel, workload):
     return None
 
 
+def step_bytes(wl, R):
+    """The scope table's per-realization byte counts of the sampler path
+    (steps b1-c2): floor = the outputs (2 fields, and 2 count maps when the
+    lognormal + Poisson step runs) plus the amplitudes sqrt(lambda+) read
+    once per batch of R; plan = floor plus the pruned intermediates written
+    and read once (2D: M0 x n1 complex; 3D: M0 x M1 x n2 and M0 x n1 x n2)."""
+    import numpy as np
+    n, m = [int(v) for v in wl.n], [int(v) for v in wl.m]
+    real = 4 if wl.dtype == "f32" else 8
+    cells = int(np.prod(n))
+    out = 2 * cells * (real + (4 if wl.nbar is not None and wl.dtype == "f32" else 0))
+    amp = int(np.prod(m)) * real / R
+    if len(n) == 1:
+        inter = 0
+    elif len(n) == 2:
+        inter = m[0] * n[1]
+    else:
+        inter = m[0] * m[1] * n[2] + m[0] * n[1] * n[2]
+    floor = out + amp
+    return floor, floor + 2 * inter * 2 * real
+
+
 def roofline(wl, R, timing, steps, hbm_peak, peak_kind, sm_mhz):
     per_kernel = {}
     for name, (launches, ms) in timing.items():
@@ -1115,6 +1137,14 @@ def main():
                           "on one stream, nothing else on the device); in_step: its launches inside the timed "
                           "region, overlapped with the other streams' kernels" % n_alone)
         roof["in_step"] = {k: roof_step[k] for k in ("achieved", "frac", "avg_launch_ms", "launches")}
+    if roof is not None:
+        # the whole step against the scope table's byte counts (the step also
+        # embeds and computes both spectra, which these counts leave out)
+        floor, plan = step_bytes(wl, R)
+        gbs = lambda b: b * R * world / (ms_max * 1e-3) / 1e9
+        roof["step"] = {"floor_bytes_per_realization": int(floor), "plan_bytes_per_realization": int(plan),
+                        "floor_gbs": round(gbs(floor), 1), "plan_gbs": round(gbs(plan), 1),
+                        "floor_frac": round(gbs(floor) / hbm_peak, 4), "plan_frac": round(gbs(plan) / hbm_peak, 4)}
     launches = sum(v[0] for v in per_kernel.values())
 
     e2e = None
