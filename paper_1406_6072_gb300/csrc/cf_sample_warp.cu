@@ -41,14 +41,18 @@ struct WarpRowsCfg {
     static constexpr size_t SMEM = sizeof(C2<float>) * ((size_t)P * P + (size_t)W * RPW * P * PAD);
 };
 
-// Lane group `lane / P` of warp `threadIdx.x / 32` of block (bx, rl)
-// transforms row (bx W + warp) RPW + lane / P of realization rl of the chunk:
-// intermediate out[chunk][nrows][keep], keep <= L/2.
+// Block b of the one-dimensional grid covers realization rl = b mod chunk
+// and row block bx = b / chunk (realizations adjacent, so that the blocks
+// resident together read the same rows of sqrt(lambda+) and a 3D amplitude
+// array larger than L2 leaves DRAM once per launch, not once per
+// realization); lane group `lane / P` of warp `threadIdx.x / 32` transforms
+// row (bx W + warp) RPW + lane / P of realization rl: intermediate
+// out[chunk][nrows][keep], keep <= L/2.
 template <int P, bool DESC, int W>
 __global__ void __launch_bounds__(WarpRowsCfg<P, W>::THREADS, WarpRowsCfg<P, W>::MINB)
     k_sample_rows_warp(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
-                       long long nrows, int keep, C2<float>* __restrict__ out, const C2<float>* __restrict__ tw,
-                       const RealDesc* __restrict__ desc) {
+                       long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
+                       const C2<float>* __restrict__ tw, const RealDesc* __restrict__ desc) {
     using Cfg = WarpRowsCfg<P, W>;
     constexpr int L = Cfg::L;
     constexpr int PAD = Cfg::PAD;
@@ -62,13 +66,14 @@ __global__ void __launch_bounds__(WarpRowsCfg<P, W>::THREADS, WarpRowsCfg<P, W>:
         twl[i] = tw[((l * k2) & (L - 1)) * (TWN / L)];
     }
     __syncthreads();
-    const long long row = ((long long)blockIdx.x * W + warp) * Cfg::RPW + sub;
+    const int rl = (int)(blockIdx.x % (unsigned)chunk);
+    const long long bx = blockIdx.x / (unsigned)chunk;
+    const long long row = (bx * W + warp) * Cfg::RPW + sub;
     // the warp's lane groups stay together to the end (warp-wide exchange);
     // a group past the last row works on row 0 and stores nothing
-    if (((long long)blockIdx.x * W + warp) * Cfg::RPW >= nrows) return;
+    if ((bx * W + warp) * Cfg::RPW >= nrows) return;
     const bool valid = row < nrows;
     const long long rw = valid ? row : 0;
-    const int rl = blockIdx.y;
     const float* srow = s + (size_t)rw * L;
     float amp = amp_scale;
     uint32_t k0 = key0, k1 = key1, r = r0 + (uint32_t)rl;
@@ -134,10 +139,11 @@ cf_status launch_rows_warp(long long L, int keep, const float* s, float amp_scal
         auto kern = desc ? k_sample_rows_warp<P, true, W> : k_sample_rows_warp<P, false, W>;
         CF_TRY(prepare_smem(kern, Cfg::SMEM));
         const long long per_block = (long long)W * Cfg::RPW;
-        dim3 grid((unsigned)((nrows + per_block - 1) / per_block), (unsigned)chunk);
+        const long long blocks = (nrows + per_block - 1) / per_block * (long long)chunk;
+        if (blocks > 0x7fffffffll) return fail(CF_ERR_UNSUPPORTED, "row pass of %lld blocks", blocks);
         ScopedKernelTimer kt(st, "sample_rows_f32", Cfg::L);
-        kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0, nrows,
-                                                     keep, out, twiddles_f32(), desc);
+        kern<<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                                r0, nrows, keep, chunk, out, twiddles_f32(), desc);
         CF_CHECK_LAUNCH();
         return CF_OK;
     };
