@@ -111,8 +111,12 @@ __global__ void __launch_bounds__(PairCfg<L, LW>::THREADS, PairCfg<L, LW>::MINB)
     k_sample_rows_pair(const float* __restrict__ s, float amp_scale, uint32_t key0, uint32_t key1, uint32_t r0,
                        long long nrows, int keep, int chunk, C2<float>* __restrict__ out,
                        const float4* __restrict__ tw, const RealDesc* __restrict__ desc) {
-    rows_pair_block<L, DESC, LW>(blockIdx.x, blockIdx.y, s, amp_scale, key0, key1, r0, nrows, keep, chunk, out, tw,
-                                 desc);
+    // one-dimensional grid, the realization pairs of a row block adjacent:
+    // blocks resident together read the same rows of sqrt(lambda+), so an
+    // amplitude array larger than L2 leaves DRAM once per launch
+    const unsigned pairs = (unsigned)(chunk + 1) / 2;
+    rows_pair_block<L, DESC, LW>(blockIdx.x / pairs, blockIdx.x % pairs, s, amp_scale, key0, key1, r0, nrows, keep,
+                                 chunk, out, tw, desc);
 }
 
 // Column pass: lines o = 2 blockIdx.y and o + 1 of in[outer][L][inner], the
@@ -187,10 +191,12 @@ cf_status launch_rows_pair(long long L, int keep, const float* s, float amp_scal
                 using Cfg = PairCfg<LL, LW>;
                 auto kern = desc ? k_sample_rows_pair<LL, true, LW> : k_sample_rows_pair<LL, false, LW>;
                 CF_TRY(prepare_smem(kern, Cfg::SMEM));
-                dim3 grid((unsigned)((nrows + Cfg::LINES - 1) / Cfg::LINES), (unsigned)((chunk + 1) / 2));
+                const long long blocks = (nrows + Cfg::LINES - 1) / Cfg::LINES * (long long)((chunk + 1) / 2);
+                if (blocks > 0x7fffffffll) return fail(CF_ERR_UNSUPPORTED, "row pass of %lld blocks", blocks);
                 ScopedKernelTimer kt(st, "sample_rows_f32", LL);
-                kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed, (uint32_t)(seed >> 32), r0,
-                                                            nrows, keep, chunk, out, twiddles_f32x2(), desc);
+                kern<<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, st>>>(s, amp_scale, (uint32_t)seed,
+                                                                        (uint32_t)(seed >> 32), r0, nrows, keep,
+                                                                        chunk, out, twiddles_f32x2(), desc);
                 CF_CHECK_LAUNCH();
                 return CF_OK;
             });
