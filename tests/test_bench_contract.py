@@ -58,3 +58,25 @@ def test_reference_arm_other_ranks_exit_without_work():
                        capture_output=True, text=True, timeout=300, env=env)
     assert p.returncode == 0
     assert not _lines(p.stdout)
+
+
+def test_step_byte_counts_follow_the_scope_table():
+    """Floor = outputs + amplitudes once per batch; plan = floor + the pruned
+    intermediates written and read once.  The 512^2 workload: 2 fields and 2
+    count maps of 512^2 cells (4 MiB) + 1024^2 amplitudes / 64 realizations
+    (64 KiB); plan + 1024 x 512 complex written and read (8 MiB).  The
+    binary64 64^2 workload: 2 fields of 8 bytes (64 KiB) + 128^2 amplitudes of
+    8 bytes / 16 realizations; plan + 128 x 64 complex of 16 bytes twice."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1406_6072_gb300 import workloads as W
+    mib = float(1 << 20)
+    wl = W.CONFIGS["cauchy2d_n512_f32"]
+    floor, plan = bench.step_bytes(wl, wl.R)
+    assert floor == 4 * (1 << 20) + 64 * 1024
+    assert plan == floor + 8 * (1 << 20)
+    wl = W.CONFIGS["gauss2d_n64_f64"]
+    floor, plan = bench.step_bytes(wl, wl.R)
+    assert floor == 2 * 64 * 64 * 8 + 128 * 128 * 8 / 16
+    assert plan == floor + 2 * 128 * 64 * 16
+    assert round(floor / mib, 2) == 0.07 and round(plan / mib, 2) == 0.32
