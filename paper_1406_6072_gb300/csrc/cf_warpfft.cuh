@@ -23,15 +23,24 @@ __host__ __device__ constexpr double cos_pi16_base(int m) {
 __host__ __device__ constexpr double cos_pi16(int m) { return m <= 8 ? cos_pi16_base(m) : -cos_pi16_base(16 - m); }
 __host__ __device__ constexpr double sin_pi16(int m) { return m <= 8 ? cos_pi16_base(8 - m) : cos_pi16_base(m - 8); }
 
-// w_N^(SIGN k) o for N dividing 32 and k < N/2 (compile-time after unrolling):
-// the trivial factors 1 and SIGN i without multiplications
-template <int N, int SIGN>
-__device__ __forceinline__ C2<float> rot_const(int k, C2<float> o) {
+// One radix-2 butterfly with the twiddle w_N^(SIGN k): y0 = e + w o and, when
+// y1 is wanted, y1 = e - w o.  A non-trivial twiddle is folded into two fused
+// multiply-adds per component, e.x + o.x c - o.y s, and the difference is
+// formed as 2 e - y0 (one fused multiply-add, exact product), six
+// instructions where a separate product and two sums take eight; the trivial
+// twiddles 1 and SIGN i take additions only.
+template <int N, int SIGN, bool Y1>
+__device__ __forceinline__ void butterfly_const(int k, C2<float> e, C2<float> o, C2<float>& y0, C2<float>& y1) {
     const int m = (32 / N) * k;  // w_N^k = w_32^m
-    if (m == 0) return o;
-    if (m == 8) return mul_si<SIGN>(o);
+    if (m == 0 || m == 8) {
+        const C2<float> t = m == 0 ? o : mul_si<SIGN>(o);
+        y0 = e + t;
+        if constexpr (Y1) y1 = e - t;
+        return;
+    }
     const float c = (float)cos_pi16(m), s = SIGN > 0 ? (float)sin_pi16(m) : -(float)sin_pi16(m);
-    return mk(o.x * c - o.y * s, o.x * s + o.y * c);
+    y0 = mk(__fmaf_rn(o.x, c, __fmaf_rn(-o.y, s, e.x)), __fmaf_rn(o.x, s, __fmaf_rn(o.y, c, e.y)));
+    if constexpr (Y1) y1 = mk(__fmaf_rn(2.0f, e.x, -y0.x), __fmaf_rn(2.0f, e.y, -y0.y));
 }
 
 // Radix-2 decimation-in-time transform of N points x[0], x[S], ..., x[(N-1) S]
@@ -48,9 +57,12 @@ struct RegFft {
             RegFft<N / 2, SIGN, false>::template run<2 * S>(x + S, o);
 #pragma unroll
             for (int k = 0; k < N / 2; ++k) {
-                const C2<float> t = rot_const<N, SIGN>(k, o[k]);
-                y[k] = e[k] + t;
-                if constexpr (!HALF) y[k + N / 2] = e[k] - t;
+                if constexpr (HALF) {
+                    C2<float> unused;
+                    butterfly_const<N, SIGN, false>(k, e[k], o[k], y[k], unused);
+                } else {
+                    butterfly_const<N, SIGN, true>(k, e[k], o[k], y[k], y[k + N / 2]);
+                }
             }
         }
     }
