@@ -419,10 +419,16 @@ static PoissonDefer defer_list(const GridInfo& g, size_t elem, int chunk, void* 
     return d;
 }
 
-// Decides the listed counts in binary64 (one thread per entry).
-__global__ void __launch_bounds__(128) k_poisson_fixup(PoissonDefer d) {
+// Decides the listed counts in binary64 (one thread per entry).  One warp per
+// block, up to eight blocks per SM: the walks are bound by the binary64 pipe,
+// which the warps of an SM share, so the entries are spread over as many SMs
+// as they fill instead of four warps to each.
+constexpr int kFixupThreads = 32;
+constexpr int kFixupBlocks = 152 * 8;
+__global__ void __launch_bounds__(kFixupThreads) k_poisson_fixup(PoissonDefer d) {
     const unsigned int n = *d.count < d.capacity ? *d.count : d.capacity;
-    for (unsigned int i = blockIdx.x * 128u + threadIdx.x; i < n; i += gridDim.x * 128u) {
+    for (unsigned int i = blockIdx.x * (unsigned)kFixupThreads + threadIdx.x; i < n;
+         i += gridDim.x * (unsigned)kFixupThreads) {
         const PoissonTodo t = d.items[i];
         *t.dst = poisson_count_f64(t.G, t.half_sigma2, t.nbar, t.f, t.ubits);
     }
@@ -436,7 +442,7 @@ static cf_status defer_begin(const PoissonDefer& d, cudaStream_t st) {
 static cf_status defer_end(const PoissonDefer& d, cudaStream_t st) {
     if (!d.items) return CF_OK;
     ScopedKernelTimer kt(st, "poisson_fixup");
-    k_poisson_fixup<<<256, 128, 0, st>>>(d);
+    k_poisson_fixup<<<kFixupBlocks, kFixupThreads, 0, st>>>(d);
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
