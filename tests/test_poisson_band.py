@@ -8,7 +8,10 @@ and quotient pushed to the edge of its documented error (2 ulp) in a random
 direction, and places U adversarially close to the CDF values: every count
 the model accepts must equal the exact decision.  The same model with a bound
 fifty times smaller must accept wrong counts, which shows the cases reach the
-band's edge.
+band's edge.  A last test runs the binary64 walk that decides the remaining
+counts with its term tests in floating point and in the integer form the
+kernel uses (j > floor(mu), U < F and F + p == F on the bit patterns): the
+same counts.
 """
 import numpy as np
 import pytest
@@ -103,3 +106,45 @@ def test_a_smaller_bound_accepts_wrong_counts():
     j = _fast_path(G, 0.4, 2.0, f, ubits, rng, tol_scale=1.0 / 50.0)
     acc = j >= 0
     assert np.count_nonzero(j[acc] != jtrue[acc]) > 0
+
+
+def _walk_float_tests(U, mu, inv):
+    """The binary64 walk with its tests in floating point (j > mu, U < F,
+    F + p == F)."""
+    j, p = 0, np.exp(-mu)
+    F = p
+    while not (U < F):
+        j += 1
+        p = p * (mu * inv[j])
+        Fn = F + p
+        if Fn == F and float(j) > mu:
+            break
+        F = Fn
+    return j
+
+
+def _walk_integer_tests(U, mu, inv):
+    """The same walk with the tests the kernel makes in integers: j > floor(mu)
+    and the comparisons on the doubles' bit patterns."""
+    bits = lambda x: int(np.float64(x).view(np.int64))
+    jm, Ub = int(np.floor(mu)), bits(U)
+    j, p = 0, np.exp(-mu)
+    F = p
+    while not (Ub < bits(F)):
+        j += 1
+        p = p * (mu * inv[j])
+        Fn = F + p
+        if j > jm and bits(Fn) == bits(F):
+            break
+        F = Fn
+    return j
+
+
+def test_walk_integer_tests_match_float_tests():
+    rng = np.random.default_rng(5)
+    inv = np.array([0.0] + [1.0 / i for i in range(1, 2048)])
+    mus = np.concatenate([rng.uniform(0.01, 30.0, 300), rng.uniform(30.0, 700.0, 60),
+                          np.arange(1.0, 40.0), [700.0, 699.5, 1e-3]])
+    for mu in mus:
+        for U in (rng.random(), 0.0, 1.0 - 2.0 ** -53, rng.random() ** 8, 1.0 - rng.random() ** 8):
+            assert _walk_integer_tests(U, float(mu), inv) == _walk_float_tests(U, float(mu), inv)
