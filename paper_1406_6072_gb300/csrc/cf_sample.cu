@@ -420,11 +420,11 @@ static PoissonDefer defer_list(const GridInfo& g, size_t elem, int chunk, void* 
 }
 
 // Decides the listed counts in binary64 (one thread per entry).  One warp per
-// block, up to eight blocks per SM: the walks are bound by the binary64 pipe,
-// which the warps of an SM share, so the entries are spread over as many SMs
-// as they fill instead of four warps to each.
+// block, eight blocks per SM: the walks are bound by the binary64 pipe, which
+// the warps of an SM share, so the entries are spread over as many SMs as they
+// fill instead of four warps to each.
 constexpr int kFixupThreads = 32;
-constexpr int kFixupBlocks = 152 * 8;
+constexpr int kFixupBlocksPerSm = 8;
 __global__ void __launch_bounds__(kFixupThreads) k_poisson_fixup(PoissonDefer d) {
     const unsigned int n = *d.count < d.capacity ? *d.count : d.capacity;
     for (unsigned int i = blockIdx.x * (unsigned)kFixupThreads + threadIdx.x; i < n;
@@ -441,8 +441,11 @@ static cf_status defer_begin(const PoissonDefer& d, cudaStream_t st) {
 
 static cf_status defer_end(const PoissonDefer& d, cudaStream_t st) {
     if (!d.items) return CF_OK;
+    int dev = 0, sms = 0;
+    CF_CUDA(cudaGetDevice(&dev));
+    CF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     ScopedKernelTimer kt(st, "poisson_fixup");
-    k_poisson_fixup<<<kFixupBlocks, kFixupThreads, 0, st>>>(d);
+    k_poisson_fixup<<<(sms > 0 ? sms : 1) * kFixupBlocksPerSm, kFixupThreads, 0, st>>>(d);
     CF_CHECK_LAUNCH();
     return CF_OK;
 }
